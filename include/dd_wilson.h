@@ -1,0 +1,251 @@
+/*
+ * dd_wilson.h — C ABI of the GB300 (sm_103a) Wilson-clover library.
+ *
+ * The library applies the Wilson-clover Dirac operator of lattice QCD and
+ * solves D x = b with FGMRES.  Operator and algorithms follow "Accelerating
+ * Lattice QCD Simulations using GPUs" (T. Matthaei, 2023):
+ *   D (Eq. 1.13 with a = 1)          (D psi)(x) = A(x) psi(x)
+ *                                     - 1/2 sum_mu ((I - gamma_mu) (x) U_mu(x)) psi(x + mu)
+ *                                     - 1/2 sum_mu ((I + gamma_mu) (x) U_mu^H(x - mu)) psi(x - mu)
+ *   self coupling A(x) (Eq. 1.11, 1.12, 2.5)
+ *                                     = (m0 + 4) I - (c_sw/32) sum_{mu,nu} gamma_mu gamma_nu (x) (Q_munu - Q_numu)
+ *   FGMRES (Section 1.2, Algorithm 2).
+ * Additions that the thesis does not have: the even-odd Schur operator,
+ * FP32 / FP16-storage arithmetic with FP64 iterative refinement, multiple
+ * right-hand sides, batched uneven lattices and the link derivative.
+ *
+ * Conventions
+ *   dims = {nT, nZ, nY, nX}; every extent must be even and >= 2.
+ *   site index (lexicographic, X fastest) = ((t*nZ + z)*nY + y)*nX + x.
+ *   direction mu = 0..3 for T, Z, Y, X (Eq. 1.7, 1.8).
+ *   spinor component = 3*spin + colour (Eq. 1.2).
+ *   gamma matrices: Euclidean chiral basis,
+ *     gamma_X,Y,Z = [[0, -i sigma_1,2,3], [i sigma_1,2,3, 0]], gamma_T = [[0, I], [I, 0]],
+ *     gamma_5 = gamma_X gamma_Y gamma_Z gamma_T = diag(1, 1, -1, -1).
+ *   time boundary: the fermion hop across t = nT-1 <-> 0 is multiplied by
+ *     t_bc (-1 antiperiodic, +1 periodic); Z, Y, X are periodic.
+ *   parity of a site = (t + z + y + x) mod 2 (0 even, 1 odd).
+ *
+ * Field layouts (argument `layout`)
+ *   DD_LAYOUT_CANONICAL       device memory, complex double interleaved,
+ *                             [nrhs][nsites][4 spin][3 colour].
+ *   DD_LAYOUT_CANONICAL_HOST  the same shape in host memory (pinned memory is
+ *                             faster); the call copies in and out itself and
+ *                             returns after the result has reached the host.
+ *   DD_LAYOUT_NATIVE          device memory in the library's native layout for
+ *                             the precision (see dd_field_bytes).
+ *   For the full-lattice operators (DD_OP_D, DD_OP_DH) nsites = V.  For the
+ *   even-odd operators (DD_OP_DHAT, DD_OP_DHAT_H) fields live on odd sites
+ *   only: nsites = V/2, in increasing lexicographic order.
+ *
+ * Native layout (all device memory; Vh = V/2; N = nrhs; a "half field" holds
+ * the sites of one parity, site k of parity p being the k-th site of that
+ * parity in lexicographic order):
+ *   FP64 half field: [12 components][Vh][N] of complex double (16 B).
+ *   FP32 half field: [6 component pairs][Vh][N] of float4 (re, im of
+ *                    components 2c and 2c + 1).
+ *   FP16 half field: [3 component quads][Vh][N] of 8 halves (re, im of
+ *                    components 4c .. 4c + 3, divided by the site scale),
+ *                    then [Vh][N] float scales (max |re|, |im| over the 24 reals).
+ *   A full field is the even half field followed by the odd half field.
+ *
+ * Ownership: handles own the device memory they allocate.  Field pointers
+ * passed to calls belong to the caller and are never freed or retained.
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ * stream).  Calls on device layouts only enqueue work and return; calls on
+ * DD_LAYOUT_CANONICAL_HOST and dd_solve synchronise the stream.
+ * Errors: every call returns a status (DD_OK = 0, negative on error); it never
+ * aborts.  dd_last_error_detail() describes the last error of the calling
+ * thread.
+ */
+#ifndef DD_WILSON_H
+#define DD_WILSON_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define DD_OK 0
+#define DD_ERR_ARG (-1)            /* bad argument (null pointer, size, enum) */
+#define DD_ERR_OOM (-2)            /* device or host allocation failed */
+#define DD_ERR_CUDA (-3)           /* a CUDA call failed */
+#define DD_ERR_SINGULAR (-4)       /* a self-coupling block could not be inverted */
+#define DD_ERR_NOT_CONVERGED (-5)  /* solver hit its iteration limit; x holds the best iterate */
+#define DD_ERR_TIMEOUT (-6)        /* a bounded device wait gave up */
+#define DD_ERR_UNSUPPORTED (-7)    /* combination not built (e.g. precision not created) */
+
+/* ---- precisions (bit flags for masks) ---- */
+#define DD_PREC_F64 1  /* FP64 storage and arithmetic */
+#define DD_PREC_F32 2  /* FP32 storage and arithmetic */
+#define DD_PREC_F16 4  /* FP16 storage (spinors with a per-site FP32 scale), FP32 arithmetic */
+
+/* ---- operators ---- */
+#define DD_OP_D 0       /* D, Eq. 1.13 */
+#define DD_OP_DH 1      /* D^H = gamma5 D gamma5 */
+#define DD_OP_DHAT 2    /* Dhat = A_oo - D_oe A_ee^{-1} D_eo on odd sites */
+#define DD_OP_DHAT_H 3  /* Dhat^H = gamma5 Dhat gamma5 */
+#define DD_OP_SC 4      /* D_sc alone (Eq. 2.5): the self coupling A(x) psi(x) */
+
+/* ---- layouts ---- */
+#define DD_LAYOUT_CANONICAL 0
+#define DD_LAYOUT_CANONICAL_HOST 1
+#define DD_LAYOUT_NATIVE 2
+
+typedef struct dd_lattice dd_lattice;
+typedef struct dd_gauge dd_gauge;
+typedef struct dd_clover dd_clover;
+typedef struct dd_batch dd_batch;
+
+/* Human-readable name of a status code (static string). */
+const char* dd_error_string(int status);
+/* Detail of the calling thread's last error (static per thread, never NULL). */
+const char* dd_last_error_detail(void);
+/* Library version, major * 10000 + minor * 100 + patch. */
+int dd_version(void);
+
+/*
+ * Lattice of dims[4] = {nT, nZ, nY, nX} (Eq. 1.9), all even and >= 2, with
+ * V = nT nZ nY nX < 2^31.  t_bc = -1 (antiperiodic in time) or +1.
+ * Host-only object; DD_ERR_ARG on bad sizes.
+ */
+int dd_lattice_create(const int dims[4], int t_bc, dd_lattice** out);
+int dd_lattice_destroy(dd_lattice* lat);
+int64_t dd_lattice_volume(const dd_lattice* lat);
+
+/*
+ * Gauge field U_mu(x) in SU(3) (Section 1.1), given as complex double
+ * [V][4 mu][3][3] (row-major colour matrices; U_mu(x) links x to x + mu).
+ * `location` 0 = host pointer, 1 = device pointer.  The library copies the
+ * links into its native layout in every precision of `prec_mask` (FP64 is
+ * always kept).  The caller keeps ownership of U.  The lattice must outlive
+ * the gauge handle.
+ */
+int dd_gauge_create(const dd_lattice* lat, const double* U, int location, unsigned prec_mask, dd_gauge** out);
+int dd_gauge_destroy(dd_gauge* g);
+/* Copy the FP64 links back out as complex double [V][4][3][3] to host (location 0) or device (1). */
+int dd_gauge_download(const dd_gauge* g, double* U, int location);
+
+/*
+ * Operator handle: builds the self coupling A(x) of Eq. 2.5 from the links on
+ * the device (Q_munu per Eq. 1.12, clover term per Eq. 1.11, mass term m0 + 4)
+ * as two Hermitian 6x6 blocks per site (upper and lower chirality; the
+ * clover term commutes with gamma5 in the chiral basis), and A_ee^{-1} on even
+ * sites in FP64.  Lower-precision copies are made for `prec_mask`.
+ * DD_ERR_SINGULAR if an even-site block has no inverse.  The gauge handle must
+ * outlive the operator.
+ */
+int dd_clover_create(const dd_gauge* g, double m0, double csw, unsigned prec_mask, dd_clover** out);
+int dd_clover_destroy(dd_clover* op);
+/* Self coupling of every site as dense 12x12 complex double [V][12][12] in
+ * host memory (for checking). */
+int dd_clover_download(const dd_clover* op, double* A_host);
+
+/*
+ * Bytes of one native field: subset 0 = full lattice, 1 = one parity (V/2
+ * sites), for `nrhs` right-hand sides in precision `prec`.
+ */
+size_t dd_field_bytes(const dd_clover* op, int prec, int subset, int nrhs);
+
+/*
+ * Convert between the canonical layout (device, complex double) and the
+ * native layout of precision `prec`.  subset 0: full field ([nrhs][V][12]
+ * canonical); 1: odd sites ([nrhs][V/2][12]); 2: even sites.
+ * Enqueued on `stream`.
+ */
+int dd_pack(const dd_clover* op, int prec, int subset, const double* canon, void* native, int nrhs, void* stream);
+int dd_unpack(const dd_clover* op, int prec, int subset, const void* native, double* canon, int nrhs, void* stream);
+
+/*
+ * out = OP in for `nrhs` right-hand sides at precision `prec` (the precision
+ * must have been created in both the gauge and the operator handle).
+ * op: DD_OP_D, DD_OP_DH, DD_OP_SC (full lattice) or DD_OP_DHAT, DD_OP_DHAT_H
+ * (odd sites).  in and out must not overlap.  Canonical layouts are converted
+ * to and from the native layout inside the call, using workspace owned by the
+ * operator handle (allocated on first use and kept).
+ * Enqueued on `stream`; DD_LAYOUT_CANONICAL_HOST synchronises it.
+ */
+int dd_apply(dd_clover* op, int which, int prec, const void* in, void* out, int nrhs, int layout, void* stream);
+
+/* ---- solver (Algorithm 2 inside FP64 iterative refinement) ---- */
+typedef struct {
+  double tol;          /* stop when ||b - D x|| < tol ||b|| (full-system FP64 residual), e.g. 1e-10 */
+  int restart;         /* Krylov dimension m of FGMRES(m), e.g. 30 */
+  int max_restarts;    /* restart cycles allowed per inner solve */
+  int max_outer;       /* refinement steps allowed (1 with inner_prec = F64 means a plain FP64 solve) */
+  int inner_prec;      /* DD_PREC_F64, DD_PREC_F32 or DD_PREC_F16 (FP16 links/clover, FP32 vectors) */
+  double inner_tol;    /* relative residual reduction asked of each inner solve, e.g. 1e-6 */
+  int even_odd;        /* 1: inner solves use Dhat on odd sites; 0: D on the full lattice */
+  int verbose;         /* 1: print one line per refinement step to stderr */
+} dd_solve_params;
+
+typedef struct {
+  int converged;             /* 1 if every right-hand side met tol */
+  int outer_iterations;      /* refinement steps */
+  int inner_iterations;      /* Arnoldi steps summed over inner solves (max over RHS) */
+  int restarts;              /* restart cycles summed over inner solves */
+  int applies_inner;         /* operator applications inside inner solves */
+  int applies_fp64;          /* FP64 operator applications (true residuals) */
+  double true_residual;      /* max over RHS of ||b - D x|| / ||b|| in FP64 */
+  double seconds;            /* wall time of the call */
+} dd_stats;
+
+/* Fill `p` with defaults: tol 1e-10, restart 30, max_restarts 100,
+ * max_outer 30, inner_prec F32, inner_tol 1e-6, even_odd 1. */
+void dd_solve_params_default(dd_solve_params* p);
+
+/*
+ * Solve D x = b for `nrhs` right-hand sides.  b and x use `layout`
+ * (canonical device or host; full lattice); x holds the initial guess on
+ * entry and the solution on exit.  Convergence is judged on the FP64 true
+ * residual of the full system.  Returns DD_ERR_NOT_CONVERGED (with x = best
+ * iterate and stats filled) when limits are hit.  Synchronises `stream`.
+ * `stats` may be NULL.
+ */
+int dd_solve(dd_clover* op, const dd_solve_params* params, const void* b, void* x, int nrhs, int layout,
+             void* stream, dd_stats* stats);
+
+/* ---- link derivative (not in the thesis) ----
+ * For L = Re <phi, D psi> = Re sum_x phi(x)^H (D psi)(x), writes per link
+ *   G_mu(x) = dL/dRe U_mu(x) + i dL/dIm U_mu(x)           (if G != NULL)
+ *   F_mu(x) = P(G_mu(x) U_mu(x)^H), P(M) = (M - M^H)/2 - tr(M - M^H)/6 I
+ *                                                          (if F != NULL)
+ * as complex double [V][4][3][3] on the device.  phi, psi: canonical device
+ * fields [nrhs][V][12]; contributions of all right-hand sides are summed.
+ * with_clover = 0 holds the self coupling fixed (hopping terms only); 1 also
+ * differentiates A(x) through Q_munu (Eq. 1.11, 1.12).  prec: DD_PREC_F64 or
+ * DD_PREC_F32 (arithmetic precision; outputs are FP64).  Enqueued on stream.
+ */
+int dd_force(dd_clover* op, int prec, const double* phi, const double* psi, int nrhs, int with_clover, double* G,
+             double* F, void* stream);
+
+/* ---- batched uneven lattices ----
+ * A batch groups operator handles of different lattices (FP32 or FP16
+ * precision) and applies D to all of them in one persistent kernel launch.
+ * Work items are (lattice, site tile, RHS block) triples; the tile and RHS
+ * block shapes come from the autotuner (dd_batch_tune) or defaults.
+ */
+int dd_batch_create(dd_clover* const* ops, int count, int prec, const int* nrhs, dd_batch** out);
+int dd_batch_destroy(dd_batch* b);
+/* ins[i], outs[i]: native device fields of operator i (full lattice, nrhs[i] RHS). */
+int dd_apply_batched(dd_batch* b, const void* const* ins, void* const* outs, void* stream);
+/* Time candidate launch shapes on `stream` and keep the fastest; optional
+ * report of the chosen shape (tile sites, threads per block, CTAs per SM). */
+int dd_batch_tune(dd_batch* b, const void* const* ins, void* const* outs, void* stream, int* chosen3);
+/* Capture the batched launch in a CUDA graph on first call and replay it
+ * afterwards (same pointers required; DD_ERR_ARG otherwise). */
+int dd_apply_batched_graph(dd_batch* b, const void* const* ins, void* const* outs, void* stream);
+
+/* ---- vector operations on canonical device fields (FP64) ----
+ * dots[r] = <a_r, b_r> = sum a_r^H b_r over `nsites` sites, for r < nrhs;
+ * written to host memory after synchronising the stream. */
+int dd_dot(const double* a, const double* b, int64_t nsites, int nrhs, double* dots_host /*[nrhs][2]*/, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DD_WILSON_H */

@@ -1,0 +1,10 @@
+"""GB300 (sm_103a) Wilson-clover Dirac operator and FGMRES solver.
+
+The compute path is ``libddwilson.so`` (hand-written CUDA, C ABI declared in
+``include/dd_wilson.h``); this package is its thin Python binding.  Importing
+it loads the library and fails loudly if it cannot be built or loaded.
+"""
+from .binding import *  # noqa: F401,F403
+from .binding import load, Lattice, Gauge, Operator, SolveParams, Stats, DDError  # noqa: F401
+
+lib = load()

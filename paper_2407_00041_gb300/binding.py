@@ -1,0 +1,209 @@
+"""ctypes binding of the C ABI in ``include/dd_wilson.h``.
+
+Argument marshalling only: every computation runs in ``libddwilson.so``.
+PyTorch supplies device memory and streams.  The functions keep the C names
+(``dd_apply``, ``dd_solve`` ...); the small classes below own the handles.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import _build
+
+DD_OK = 0
+DD_ERR_ARG, DD_ERR_OOM, DD_ERR_CUDA, DD_ERR_SINGULAR = -1, -2, -3, -4
+DD_ERR_NOT_CONVERGED, DD_ERR_TIMEOUT, DD_ERR_UNSUPPORTED = -5, -6, -7
+DD_PREC_F64, DD_PREC_F32, DD_PREC_F16 = 1, 2, 4
+DD_OP_D, DD_OP_DH, DD_OP_DHAT, DD_OP_DHAT_H, DD_OP_SC = 0, 1, 2, 3, 4
+DD_LAYOUT_CANONICAL, DD_LAYOUT_CANONICAL_HOST, DD_LAYOUT_NATIVE = 0, 1, 2
+
+PREC = {"f64": DD_PREC_F64, "f32": DD_PREC_F32, "f16": DD_PREC_F16}
+OPS = {"D": DD_OP_D, "DH": DD_OP_DH, "DHAT": DD_OP_DHAT, "DHAT_H": DD_OP_DHAT_H, "SC": DD_OP_SC}
+
+
+class DDError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {_lib.dd_error_string(status).decode()} "
+                         f"({_lib.dd_last_error_detail().decode()})")
+
+
+class SolveParams(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("max_restarts", ctypes.c_int),
+                ("max_outer", ctypes.c_int), ("inner_prec", ctypes.c_int), ("inner_tol", ctypes.c_double),
+                ("even_odd", ctypes.c_int), ("verbose", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("converged", ctypes.c_int), ("outer_iterations", ctypes.c_int),
+                ("inner_iterations", ctypes.c_int), ("restarts", ctypes.c_int),
+                ("applies_inner", ctypes.c_int), ("applies_fp64", ctypes.c_int),
+                ("true_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# name -> (restype, argtypes)
+_P, _I, _D, _L, _U, _S = (ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64, ctypes.c_uint,
+                          ctypes.c_size_t)
+SIGNATURES = {
+    "dd_error_string": (ctypes.c_char_p, [_I]),
+    "dd_last_error_detail": (ctypes.c_char_p, []),
+    "dd_version": (_I, []),
+    "dd_lattice_create": (_I, [_P, _I, _P]),
+    "dd_lattice_destroy": (_I, [_P]),
+    "dd_lattice_volume": (_L, [_P]),
+    "dd_gauge_create": (_I, [_P, _P, _I, _U, _P]),
+    "dd_gauge_destroy": (_I, [_P]),
+    "dd_gauge_download": (_I, [_P, _P, _I]),
+    "dd_clover_create": (_I, [_P, _D, _D, _U, _P]),
+    "dd_clover_destroy": (_I, [_P]),
+    "dd_clover_download": (_I, [_P, _P]),
+    "dd_field_bytes": (_S, [_P, _I, _I, _I]),
+    "dd_pack": (_I, [_P, _I, _I, _P, _P, _I, _P]),
+    "dd_unpack": (_I, [_P, _I, _I, _P, _P, _I, _P]),
+    "dd_apply": (_I, [_P, _I, _I, _P, _P, _I, _I, _P]),
+    "dd_solve_params_default": (None, [_P]),
+    "dd_solve": (_I, [_P, _P, _P, _P, _I, _I, _P, _P]),
+    "dd_force": (_I, [_P, _I, _P, _P, _I, _I, _P, _P, _P]),
+    "dd_batch_create": (_I, [_P, _I, _I, _P, _P]),
+    "dd_batch_destroy": (_I, [_P]),
+    "dd_apply_batched": (_I, [_P, _P, _P, _P]),
+    "dd_batch_tune": (_I, [_P, _P, _P, _P, _P]),
+    "dd_apply_batched_graph": (_I, [_P, _P, _P, _P]),
+    "dd_dot": (_I, [_P, _P, _L, _I, _P, _P]),
+}
+
+_lib = None
+
+
+def load(build_if_missing: bool = True):
+    """Load ``libddwilson.so`` (building it in-tree first when it is missing or
+    stale).  Raises when the library cannot be built or loaded: there is no
+    CPU fallback."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise ImportError(f"CUDA library {_build.LIB} is missing; run __graft_entry__.build()")
+    lib = ctypes.CDLL(_build.LIB)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def check(status, where):
+    if status != DD_OK:
+        raise DDError(status, where)
+    return status
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+def _ptr(t):
+    return t.data_ptr() if hasattr(t, "data_ptr") else t.ctypes.data
+
+
+class Lattice:
+    def __init__(self, dims, t_bc=-1):
+        lib = load()
+        self.dims = tuple(int(d) for d in dims)
+        arr = (ctypes.c_int * 4)(*self.dims)
+        h = ctypes.c_void_p()
+        check(lib.dd_lattice_create(arr, t_bc, ctypes.byref(h)), "dd_lattice_create")
+        self.h, self.t_bc = h, t_bc
+        self.V = int(lib.dd_lattice_volume(h))
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.dd_lattice_destroy(self.h)
+            self.h = None
+
+
+class Gauge:
+    """Links U as complex128 [V, 4, 3, 3] (numpy on the host or a torch tensor)."""
+
+    def __init__(self, lattice, U, precisions=DD_PREC_F64 | DD_PREC_F32 | DD_PREC_F16):
+        lib = load()
+        self.lattice = lattice
+        loc = 1 if (hasattr(U, "is_cuda") and U.is_cuda) else 0
+        if hasattr(U, "contiguous"):
+            U = U.contiguous()
+        else:
+            import numpy as np
+            U = np.ascontiguousarray(U, dtype=np.complex128)
+        h = ctypes.c_void_p()
+        check(lib.dd_gauge_create(lattice.h, _ptr(U), loc, precisions, ctypes.byref(h)), "dd_gauge_create")
+        self.h = h
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.dd_gauge_destroy(self.h)
+            self.h = None
+
+
+class Operator:
+    """Wilson-clover operator handle (dd_clover)."""
+
+    def __init__(self, gauge, m0, csw, precisions=DD_PREC_F64 | DD_PREC_F32 | DD_PREC_F16):
+        lib = load()
+        self.gauge, self.lattice = gauge, gauge.lattice
+        self.m0, self.csw = m0, csw
+        h = ctypes.c_void_p()
+        check(lib.dd_clover_create(gauge.h, m0, csw, precisions, ctypes.byref(h)), "dd_clover_create")
+        self.h = h
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.dd_clover_destroy(self.h)
+            self.h = None
+
+    # -- fields
+    def field_bytes(self, prec, subset=0, nrhs=1):
+        return int(_lib.dd_field_bytes(self.h, prec, subset, nrhs))
+
+    def pack(self, prec, subset, canon, native, nrhs, stream=None):
+        check(_lib.dd_pack(self.h, prec, subset, _ptr(canon), _ptr(native), nrhs, _stream(stream)), "dd_pack")
+
+    def unpack(self, prec, subset, native, canon, nrhs, stream=None):
+        check(_lib.dd_unpack(self.h, prec, subset, _ptr(native), _ptr(canon), nrhs, _stream(stream)), "dd_unpack")
+
+    # -- operators
+    def apply(self, which, prec, inp, out, nrhs, layout=DD_LAYOUT_CANONICAL, stream=None):
+        s = 0 if layout == DD_LAYOUT_CANONICAL_HOST and stream is None else _stream(stream)
+        check(_lib.dd_apply(self.h, which, prec, _ptr(inp), _ptr(out), nrhs, layout, s), "dd_apply")
+
+    def solve(self, b, x, nrhs, layout=DD_LAYOUT_CANONICAL, stream=None, **kw):
+        p = SolveParams()
+        _lib.dd_solve_params_default(ctypes.byref(p))
+        for k, v in kw.items():
+            setattr(p, k, v)
+        st = Stats()
+        s = 0 if layout == DD_LAYOUT_CANONICAL_HOST and stream is None else _stream(stream)
+        status = _lib.dd_solve(self.h, ctypes.byref(p), _ptr(b), _ptr(x), nrhs, layout, s, ctypes.byref(st))
+        if status not in (DD_OK, DD_ERR_NOT_CONVERGED):
+            check(status, "dd_solve")
+        return status, st.as_dict()
+
+    def force(self, prec, phi, psi, nrhs, with_clover, G=None, F=None, stream=None):
+        check(_lib.dd_force(self.h, prec, _ptr(phi), _ptr(psi), nrhs, int(with_clover),
+                            _ptr(G) if G is not None else None, _ptr(F) if F is not None else None,
+                            _stream(stream)), "dd_force")
+
+    def clover_dense(self):
+        import numpy as np
+        A = np.empty((self.lattice.V, 12, 12), dtype=np.complex128)
+        check(_lib.dd_clover_download(self.h, A.ctypes.data), "dd_clover_download")
+        return A

@@ -1,0 +1,307 @@
+// C ABI entry points (declared in include/dd_wilson.h).
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "dd_blas.h"
+#include "dd_internal.h"
+
+namespace dd {
+const char* last_error();
+int solve(dd_clover* op, const dd_solve_params* prm, const double* b, double* x, int N, cudaStream_t st,
+          dd_stats* stats);
+int force(dd_clover* op, int prec, const double* phi, const double* psi, int nrhs, int with_clover, double* G,
+          double* F, cudaStream_t st);
+}  // namespace dd
+
+using namespace dd;
+
+namespace {
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+bool valid_prec(int p) { return p == DD_PREC_F64 || p == DD_PREC_F32 || p == DD_PREC_F16; }
+
+// Copy a canonical field into device memory when it lives on the host.
+int stage_in(DevBuf& buf, const void* src, size_t bytes, int layout, const double** dev, cudaStream_t st) {
+  if (layout == DD_LAYOUT_CANONICAL_HOST) {
+    DD_TRY(buf.ensure(bytes));
+    DD_CUDA(cudaMemcpyAsync(buf.ptr, src, bytes, cudaMemcpyHostToDevice, st));
+    *dev = reinterpret_cast<const double*>(buf.ptr);
+  } else {
+    *dev = reinterpret_cast<const double*>(src);
+  }
+  return DD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* dd_error_string(int status) {
+  switch (status) {
+    case DD_OK: return "DD_OK";
+    case DD_ERR_ARG: return "DD_ERR_ARG";
+    case DD_ERR_OOM: return "DD_ERR_OOM";
+    case DD_ERR_CUDA: return "DD_ERR_CUDA";
+    case DD_ERR_SINGULAR: return "DD_ERR_SINGULAR";
+    case DD_ERR_NOT_CONVERGED: return "DD_ERR_NOT_CONVERGED";
+    case DD_ERR_TIMEOUT: return "DD_ERR_TIMEOUT";
+    case DD_ERR_UNSUPPORTED: return "DD_ERR_UNSUPPORTED";
+    default: return "unknown status";
+  }
+}
+
+const char* dd_last_error_detail(void) { return last_error(); }
+
+int dd_version(void) { return 100; }
+
+int dd_lattice_create(const int dims[4], int t_bc, dd_lattice** out) {
+  if (!dims || !out) return fail(DD_ERR_ARG, "null argument");
+  int64_t V = 1;
+  for (int i = 0; i < 4; ++i) {
+    if (dims[i] < 2 || dims[i] % 2) return fail(DD_ERR_ARG, "every lattice extent must be even and >= 2");
+    V *= dims[i];
+  }
+  if (V >= (int64_t(1) << 31)) return fail(DD_ERR_ARG, "lattice volume must be below 2^31");
+  if (t_bc != 1 && t_bc != -1) return fail(DD_ERR_ARG, "t_bc must be +1 or -1");
+  dd_lattice* l = new (std::nothrow) dd_lattice;
+  if (!l) return fail(DD_ERR_OOM, "host allocation failed");
+  for (int i = 0; i < 4; ++i) l->dims[i] = dims[i];
+  l->t_bc = t_bc;
+  l->V = V;
+  l->Vh = V / 2;
+  *out = l;
+  return DD_OK;
+}
+
+int dd_lattice_destroy(dd_lattice* lat) {
+  delete lat;
+  return DD_OK;
+}
+
+int64_t dd_lattice_volume(const dd_lattice* lat) { return lat ? lat->V : 0; }
+
+int dd_gauge_create(const dd_lattice* lat, const double* U, int location, unsigned prec_mask, dd_gauge** out) {
+  if (!lat || !U || !out) return fail(DD_ERR_ARG, "null argument");
+  if (location != 0 && location != 1) return fail(DD_ERR_ARG, "location must be 0 (host) or 1 (device)");
+  if (prec_mask & ~7u) return fail(DD_ERR_ARG, "bad precision mask");
+  dd_gauge* g = new (std::nothrow) dd_gauge;
+  if (!g) return fail(DD_ERR_OOM, "host allocation failed");
+  g->lat = lat;
+  g->prec_mask = prec_mask | DD_PREC_F64;
+  const size_t bytes = (size_t)lat->V * 4 * 9 * 16;
+  const int64_t nel = lat->V * 4 * 9;
+  int s = g->links[0].alloc(nel * 16);
+  if (s == DD_OK && (g->prec_mask & DD_PREC_F32)) s = g->links[1].alloc(nel * 8);
+  if (s == DD_OK && (g->prec_mask & DD_PREC_F16)) s = g->links[2].alloc(nel * 4);
+  DevBuf staging;
+  const double* Ud = U;
+  if (s == DD_OK && location == 0) {
+    s = staging.alloc(bytes);
+    if (s == DD_OK && cudaMemcpy(staging.ptr, U, bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+      s = cuda_fail(cudaGetLastError(), "cudaMemcpy of the links");
+    Ud = reinterpret_cast<const double*>(staging.ptr);
+  }
+  if (s == DD_OK) s = links_to_native(lat, Ud, g, 0);
+  if (s == DD_OK && cudaDeviceSynchronize() != cudaSuccess) s = cuda_fail(cudaGetLastError(), "link conversion");
+  if (s != DD_OK) {
+    delete g;
+    return s;
+  }
+  *out = g;
+  return DD_OK;
+}
+
+int dd_gauge_destroy(dd_gauge* g) {
+  delete g;
+  return DD_OK;
+}
+
+int dd_gauge_download(const dd_gauge* g, double* U, int location) {
+  if (!g || !U) return fail(DD_ERR_ARG, "null argument");
+  const size_t bytes = (size_t)g->lat->V * 4 * 9 * 16;
+  if (location == 1) {
+    DD_TRY(links_to_canonical(g, U, 0));
+    DD_CUDA(cudaDeviceSynchronize());
+    return DD_OK;
+  }
+  DevBuf tmp;
+  DD_TRY(tmp.alloc(bytes));
+  DD_TRY(links_to_canonical(g, reinterpret_cast<double*>(tmp.ptr), 0));
+  DD_CUDA(cudaMemcpy(U, tmp.ptr, bytes, cudaMemcpyDeviceToHost));
+  return DD_OK;
+}
+
+int dd_clover_create(const dd_gauge* g, double m0, double csw, unsigned prec_mask, dd_clover** out) {
+  if (!g || !out) return fail(DD_ERR_ARG, "null argument");
+  if (prec_mask & ~7u) return fail(DD_ERR_ARG, "bad precision mask");
+  dd_clover* op = new (std::nothrow) dd_clover;
+  if (!op) return fail(DD_ERR_OOM, "host allocation failed");
+  op->gauge = g;
+  op->lat = g->lat;
+  op->m0 = m0;
+  op->csw = csw;
+  op->prec_mask = (prec_mask | DD_PREC_F64) & g->prec_mask;
+  int s = clover_build(op, 0);
+  if (s == DD_OK && cudaDeviceSynchronize() != cudaSuccess) s = cuda_fail(cudaGetLastError(), "clover build");
+  if (s != DD_OK) {
+    delete op;
+    return s;
+  }
+  *out = op;
+  return DD_OK;
+}
+
+int dd_clover_destroy(dd_clover* op) {
+  delete op;
+  return DD_OK;
+}
+
+int dd_clover_download(const dd_clover* op, double* A_host) {
+  if (!op || !A_host) return fail(DD_ERR_ARG, "null argument");
+  const size_t bytes = (size_t)op->lat->V * 144 * 16;
+  DevBuf tmp;
+  DD_TRY(tmp.alloc(bytes));
+  DD_TRY(clover_to_dense(op, reinterpret_cast<double*>(tmp.ptr), 0));
+  DD_CUDA(cudaMemcpy(A_host, tmp.ptr, bytes, cudaMemcpyDeviceToHost));
+  return DD_OK;
+}
+
+size_t dd_field_bytes(const dd_clover* op, int prec, int subset, int nrhs) {
+  if (!op || !valid_prec(prec) || nrhs < 1 || (subset != 0 && subset != 1)) return 0;
+  return field_bytes(op->lat, prec, subset, nrhs);
+}
+
+int dd_pack(const dd_clover* op, int prec, int subset, const double* canon, void* native, int nrhs, void* stream) {
+  if (!op || !canon || !native || nrhs < 1) return fail(DD_ERR_ARG, "null argument or nrhs < 1");
+  if (!valid_prec(prec) || subset < 0 || subset > 2) return fail(DD_ERR_ARG, "bad precision or subset");
+  Field f = field_view(op->lat, prec, subset, native, nrhs);
+  return pack(op->lat, prec, subset, canon, f, as_stream(stream));
+}
+
+int dd_unpack(const dd_clover* op, int prec, int subset, const void* native, double* canon, int nrhs, void* stream) {
+  if (!op || !canon || !native || nrhs < 1) return fail(DD_ERR_ARG, "null argument or nrhs < 1");
+  if (!valid_prec(prec) || subset < 0 || subset > 2) return fail(DD_ERR_ARG, "bad precision or subset");
+  Field f = field_view(op->lat, prec, subset, const_cast<void*>(native), nrhs);
+  return unpack(op->lat, prec, subset, f, canon, as_stream(stream));
+}
+
+int dd_apply(dd_clover* op, int which, int prec, const void* in, void* out, int nrhs, int layout, void* stream) {
+  if (!op || !in || !out || nrhs < 1) return fail(DD_ERR_ARG, "null argument or nrhs < 1");
+  if (!valid_prec(prec)) return fail(DD_ERR_ARG, "bad precision");
+  if (which < DD_OP_D || which > DD_OP_SC) return fail(DD_ERR_ARG, "bad operator");
+  if (layout < DD_LAYOUT_CANONICAL || layout > DD_LAYOUT_NATIVE) return fail(DD_ERR_ARG, "bad layout");
+  const int pi = prec_index(prec);
+  if (!op->gauge->links[pi].ptr || !op->clov[pi].ptr)
+    return fail(DD_ERR_UNSUPPORTED, "precision not created in the gauge/operator handles");
+  cudaStream_t st = as_stream(stream);
+  const dd_lattice* lat = op->lat;
+  const bool half = which == DD_OP_DHAT || which == DD_OP_DHAT_H;
+  const int subset = half ? 1 : 0;
+  const size_t nb = field_bytes(lat, prec, subset, nrhs);
+  const size_t cb = (size_t)(half ? lat->Vh : lat->V) * 12 * 16 * nrhs;
+  Field fin, fout;
+  const double* cin = nullptr;
+  if (layout == DD_LAYOUT_NATIVE) {
+    fin = field_view(lat, prec, subset, const_cast<void*>(in), nrhs);
+    fout = field_view(lat, prec, subset, out, nrhs);
+  } else {
+    DD_TRY(stage_in(op->ws_canon_in, in, cb, layout, &cin, st));
+    DD_TRY(op->ws_in.ensure(nb));
+    DD_TRY(op->ws_out.ensure(nb));
+    fin = field_view(lat, prec, subset, op->ws_in.ptr, nrhs);
+    fout = field_view(lat, prec, subset, op->ws_out.ptr, nrhs);
+    DD_TRY(pack(lat, prec, subset, cin, fin, st));
+  }
+  switch (which) {
+    case DD_OP_D:
+    case DD_OP_DH:
+      DD_TRY(op_D(op, prec, prec, which == DD_OP_DH, fin, fout, st));
+      break;
+    case DD_OP_SC:
+      DD_TRY(op_SC(op, prec, prec, fin, fout, st));
+      break;
+    default: {
+      DD_TRY(op->ws_tmp.ensure(field_bytes(lat, prec, 2, nrhs)));
+      Field tmp = field_view(lat, prec, 2, op->ws_tmp.ptr, nrhs);
+      DD_TRY(op_Dhat(op, prec, prec, which == DD_OP_DHAT_H, fin, fout, tmp, st));
+    }
+  }
+  if (layout != DD_LAYOUT_NATIVE) {
+    double* cout = reinterpret_cast<double*>(out);
+    if (layout == DD_LAYOUT_CANONICAL_HOST) {
+      DD_TRY(op->ws_canon_out.ensure(cb));
+      cout = reinterpret_cast<double*>(op->ws_canon_out.ptr);
+    }
+    DD_TRY(unpack(lat, prec, subset, fout, cout, st));
+    if (layout == DD_LAYOUT_CANONICAL_HOST) {
+      DD_CUDA(cudaMemcpyAsync(out, cout, cb, cudaMemcpyDeviceToHost, st));
+      DD_CUDA(cudaStreamSynchronize(st));
+    }
+  }
+  DD_CUDA(cudaGetLastError());
+  return DD_OK;
+}
+
+void dd_solve_params_default(dd_solve_params* p) {
+  if (!p) return;
+  p->tol = 1e-10;
+  p->restart = 30;
+  p->max_restarts = 100;
+  p->max_outer = 30;
+  p->inner_prec = DD_PREC_F32;
+  p->inner_tol = 1e-6;
+  p->even_odd = 1;
+  p->verbose = 0;
+}
+
+int dd_solve(dd_clover* op, const dd_solve_params* params, const void* b, void* x, int nrhs, int layout,
+             void* stream, dd_stats* stats) {
+  if (!op || !params || !b || !x || nrhs < 1) return fail(DD_ERR_ARG, "null argument or nrhs < 1");
+  if (layout != DD_LAYOUT_CANONICAL && layout != DD_LAYOUT_CANONICAL_HOST)
+    return fail(DD_ERR_ARG, "dd_solve takes canonical fields");
+  if (!(params->tol > 0) || params->max_restarts < 1 || params->max_outer < 0)
+    return fail(DD_ERR_ARG, "bad solver parameters");
+  cudaStream_t st = as_stream(stream);
+  const size_t cb = (size_t)op->lat->V * 12 * 16 * nrhs;
+  if (layout == DD_LAYOUT_CANONICAL) return solve(op, params, (const double*)b, (double*)x, nrhs, st, stats);
+  DevBuf bd, xd;
+  DD_TRY(bd.alloc(cb));
+  DD_TRY(xd.alloc(cb));
+  DD_CUDA(cudaMemcpyAsync(bd.ptr, b, cb, cudaMemcpyHostToDevice, st));
+  DD_CUDA(cudaMemcpyAsync(xd.ptr, x, cb, cudaMemcpyHostToDevice, st));
+  int s = solve(op, params, (const double*)bd.ptr, (double*)xd.ptr, nrhs, st, stats);
+  if (s == DD_OK || s == DD_ERR_NOT_CONVERGED) {
+    DD_CUDA(cudaMemcpyAsync(x, xd.ptr, cb, cudaMemcpyDeviceToHost, st));
+    DD_CUDA(cudaStreamSynchronize(st));
+  }
+  return s;
+}
+
+int dd_force(dd_clover* op, int prec, const double* phi, const double* psi, int nrhs, int with_clover, double* G,
+             double* F, void* stream) {
+  if (!op || !phi || !psi || nrhs < 1 || (!G && !F)) return fail(DD_ERR_ARG, "null argument or nrhs < 1");
+  if (prec != DD_PREC_F64 && prec != DD_PREC_F32) return fail(DD_ERR_ARG, "force precision must be F64 or F32");
+  return force(op, prec, phi, psi, nrhs, with_clover, G, F, as_stream(stream));
+}
+
+int dd_dot(const double* a, const double* b, int64_t nsites, int nrhs, double* dots_host, void* stream) {
+  if (!a || !b || !dots_host || nsites < 1 || nrhs < 1) return fail(DD_ERR_ARG, "null argument or empty field");
+  cudaStream_t st = as_stream(stream);
+  // canonical [nrhs][nsites][12] complex: per-RHS contiguous blocks
+  DevBuf partials, out;
+  DD_TRY(partials.alloc((size_t)blas_partials_len(1) * sizeof(double2)));
+  DD_TRY(out.alloc((size_t)nrhs * sizeof(double2)));
+  const int64_t L = nsites * 12;
+  for (int r = 0; r < nrhs; ++r) {
+    VecList vs;
+    vs.p[0] = a + 2 * r * L;
+    DD_TRY(blas_multidot<P64>(vs, 1, b + 2 * r * L, L, 1, (double2*)out.ptr + r, 0, (double2*)partials.ptr, st));
+  }
+  DD_CUDA(cudaMemcpyAsync(dots_host, out.ptr, (size_t)nrhs * sizeof(double2), cudaMemcpyDeviceToHost, st));
+  DD_CUDA(cudaStreamSynchronize(st));
+  return DD_OK;
+}
+
+}  // extern "C"

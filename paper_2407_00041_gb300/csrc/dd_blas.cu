@@ -1,0 +1,295 @@
+// Vector kernels for the Krylov solver on native fields.
+//
+// A native FP64 or FP32 field of N right-hand sides is a flat array of
+// 16-byte groups whose RHS index is (group index mod N) (see the layout in
+// dd_wilson.h): FP64 groups hold one complex number, FP32 groups two.
+// Every kernel runs with a block size that is a multiple of N and a
+// grid-stride loop, so a thread always sees the same right-hand side.
+//
+// Inner products accumulate in FP64 (warp shuffles inside a block, then a
+// fixed-order pass over per-block partials, so results are reproducible).
+// FP32 data is summed in FP32 over short runs of 16 groups per thread
+// before entering the FP64 accumulator.
+#include "dd_blas.h"
+#include "dd_internal.h"
+
+namespace dd {
+
+namespace {
+
+template <int PV>
+struct G;
+template <>
+struct G<P64> {
+  using group = double2;
+  using real = double;
+};
+template <>
+struct G<P32> {
+  using group = float4;
+  using real = float;
+};
+
+__device__ __forceinline__ void acc_dot(double2 v, double2 w, double& re, double& im) {
+  re = fma(v.x, w.x, re);
+  re = fma(v.y, w.y, re);
+  im = fma(v.x, w.y, im);
+  im = fma(-v.y, w.x, im);
+}
+__device__ __forceinline__ void acc_dot(float4 v, float4 w, float& re, float& im) {
+  re = fmaf(v.x, w.x, re);
+  re = fmaf(v.y, w.y, re);
+  re = fmaf(v.z, w.z, re);
+  re = fmaf(v.w, w.w, re);
+  im = fmaf(v.x, w.y, im);
+  im = fmaf(-v.y, w.x, im);
+  im = fmaf(v.z, w.w, im);
+  im = fmaf(-v.w, w.z, im);
+}
+
+// w += c * v with complex c
+__device__ __forceinline__ void caxpy(double cr, double ci, double2 v, double2& w) {
+  w.x = fma(cr, v.x, fma(-ci, v.y, w.x));
+  w.y = fma(cr, v.y, fma(ci, v.x, w.y));
+}
+__device__ __forceinline__ void caxpy(float cr, float ci, float4 v, float4& w) {
+  w.x = fmaf(cr, v.x, fmaf(-ci, v.y, w.x));
+  w.y = fmaf(cr, v.y, fmaf(ci, v.x, w.y));
+  w.z = fmaf(cr, v.z, fmaf(-ci, v.w, w.z));
+  w.w = fmaf(cr, v.w, fmaf(ci, v.z, w.w));
+}
+
+constexpr int MAXJ = 8;
+
+// partials[block][j][r] = sum over this block's groups of <V_j, w> for RHS r.
+template <int PV>
+__global__ void __launch_bounds__(256) k_multidot(VecList vs, int J, const void* __restrict__ wp, int64_t L, int N,
+                                                  double2* partials) {
+  using T = typename G<PV>::group;
+  using R = typename G<PV>::real;
+  __shared__ double sre[256], sim[256];
+  const T* w = reinterpret_cast<const T*>(wp);
+  double are[MAXJ], aim[MAXJ];
+  R fre[MAXJ], fim[MAXJ];
+#pragma unroll
+  for (int j = 0; j < MAXJ; ++j) are[j] = aim[j] = 0.0, fre[j] = fim[j] = R(0);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int run = 0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < L; e += stride) {
+    const T we = w[e];
+#pragma unroll
+    for (int j = 0; j < MAXJ; ++j)
+      if (j < J) acc_dot(reinterpret_cast<const T*>(vs.p[j])[e], we, fre[j], fim[j]);
+    if (PV == P32 && ++run == 16) {
+      run = 0;
+#pragma unroll
+      for (int j = 0; j < MAXJ; ++j) are[j] += (double)fre[j], aim[j] += (double)fim[j], fre[j] = fim[j] = R(0);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < MAXJ; ++j) are[j] += (double)fre[j], aim[j] += (double)fim[j];
+  const int t = threadIdx.x;
+  const int per = blockDim.x / N;  // threads per RHS in this block
+  for (int j = 0; j < J; ++j) {
+    sre[t] = are[j];
+    sim[t] = aim[j];
+    __syncthreads();
+    if (t < N) {
+      double re = 0.0, im = 0.0;
+      for (int k = 0; k < per; ++k) re += sre[t + k * N], im += sim[t + k * N];
+      partials[((int64_t)blockIdx.x * J + j) * N + t] = make_double2(re, im);
+    }
+    __syncthreads();
+  }
+}
+
+// out[j][r] (+)= sum over blocks of partials[block][j][r], fixed order.
+__global__ void k_reduce_partials(const double2* __restrict__ partials, int nblocks, int JN, double2* out, int add) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= JN) return;
+  double re = 0.0, im = 0.0;
+  for (int b = 0; b < nblocks; ++b) {
+    double2 v = partials[(int64_t)b * JN + i];
+    re += v.x;
+    im += v.y;
+  }
+  if (add) {
+    re += out[i].x;
+    im += out[i].y;
+  }
+  out[i] = make_double2(re, im);
+}
+
+// w = alpha_r * w + sum_j c[j][r] * V_j   (c, alpha complex double [.][N])
+template <int PV>
+__global__ void __launch_bounds__(256) k_multiaxpy(VecList vs, int J, const double2* __restrict__ c, double csign,
+                                                   void* wp, int64_t L, int N) {
+  using T = typename G<PV>::group;
+  using R = typename G<PV>::real;
+  T* w = reinterpret_cast<T*>(wp);
+  const int r = threadIdx.x % N;
+  R cr[32], ci[32];
+  for (int j = 0; j < J; ++j) {
+    double2 cc = c[(int64_t)j * N + r];
+    cr[j] = (R)(csign * cc.x);
+    ci[j] = (R)(csign * cc.y);
+  }
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < L; e += stride) {
+    T we = w[e];
+    for (int j = 0; j < J; ++j) caxpy(cr[j], ci[j], reinterpret_cast<const T*>(vs.p[j])[e], we);
+    w[e] = we;
+  }
+}
+
+// out = c[r] * in  (complex c [N])
+template <int PV>
+__global__ void __launch_bounds__(256) k_scale(const double2* __restrict__ c, const void* inp, void* outp, int64_t L,
+                                               int N) {
+  using T = typename G<PV>::group;
+  using R = typename G<PV>::real;
+  const T* in = reinterpret_cast<const T*>(inp);
+  T* out = reinterpret_cast<T*>(outp);
+  const int r = threadIdx.x % N;
+  const R cr = (R)c[r].x, ci = (R)c[r].y;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < L; e += stride) {
+    T v = in[e], o;
+    if constexpr (PV == P64) {
+      o.x = cr * v.x - ci * v.y;
+      o.y = cr * v.y + ci * v.x;
+    } else {
+      o.x = cr * v.x - ci * v.y;
+      o.y = cr * v.y + ci * v.x;
+      o.z = cr * v.z - ci * v.w;
+      o.w = cr * v.w + ci * v.z;
+    }
+    out[e] = o;
+  }
+}
+
+// FP64 field (L64 double2 groups) -> FP32 field (L64 / 2 float4 groups).
+// Group g of an FP32 half field holds components 2g, 2g+1; group c of an FP64
+// half field holds component c.  Index maps: FP32 group (h, g, i) with
+// i = site * N + r <- FP64 groups (h, 2g, i) and (h, 2g + 1, i).
+__global__ void k_demote(const double2* __restrict__ in, float4* out, int64_t nhalf, int64_t VN) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // over nhalf * 6 * VN
+  if (t >= nhalf * 6 * VN) return;
+  const int64_t i = t % VN;
+  const int64_t hg = t / VN;
+  const int64_t h = hg / 6, g = hg % 6;
+  const double2 a = in[(h * 12 + 2 * g) * VN + i];
+  const double2 b = in[(h * 12 + 2 * g + 1) * VN + i];
+  out[t] = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
+}
+
+// x64 += e32 with the same index map
+__global__ void k_promote_add(const float4* __restrict__ in, double2* out, int64_t nhalf, int64_t VN) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nhalf * 6 * VN) return;
+  const int64_t i = t % VN;
+  const int64_t hg = t / VN;
+  const int64_t h = hg / 6, g = hg % 6;
+  const float4 v = in[t];
+  double2* a = out + (h * 12 + 2 * g) * VN + i;
+  double2* b = out + (h * 12 + 2 * g + 1) * VN + i;
+  a->x += (double)v.x;
+  a->y += (double)v.y;
+  b->x += (double)v.z;
+  b->y += (double)v.w;
+}
+
+__global__ void k_add64(const double2* __restrict__ in, double2* out, int64_t n) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  out[t].x += in[t].x;
+  out[t].y += in[t].y;
+}
+
+int block_for(int N) {
+  if (N > 256) return -1;
+  return (256 / N) * N;
+}
+
+}  // namespace
+
+int blas_grid(int64_t L, int block) {
+  const int64_t want = (L + block - 1) / block;
+  const int64_t cap = 152 * 8;
+  return (int)(want < cap ? (want < 1 ? 1 : want) : cap);
+}
+
+template <int PV>
+int blas_multidot(const VecList& vs, int J, const void* w, int64_t L, int N, double2* dots_dev, int add,
+                  double2* partials, cudaStream_t st) {
+  const int block = block_for(N);
+  if (block <= 0) return fail(DD_ERR_ARG, "too many right-hand sides for the vector kernels");
+  const int grid = blas_grid(L, block);
+  for (int j0 = 0; j0 < J; j0 += MAXJ) {
+    const int Jc = J - j0 < MAXJ ? J - j0 : MAXJ;
+    VecList sub;
+    for (int j = 0; j < Jc; ++j) sub.p[j] = vs.p[j0 + j];
+    k_multidot<PV><<<grid, block, 0, st>>>(sub, Jc, w, L, N, partials);
+    const int JN = Jc * N;
+    k_reduce_partials<<<(JN + 127) / 128, 128, 0, st>>>(partials, grid, JN, dots_dev + (int64_t)j0 * N, add);
+  }
+  DD_CUDA(cudaGetLastError());
+  return DD_OK;
+}
+
+template <int PV>
+int blas_multiaxpy(const VecList& vs, int J, const double2* c_dev, double csign, void* w, int64_t L, int N,
+                   cudaStream_t st) {
+  const int block = block_for(N);
+  if (block <= 0) return fail(DD_ERR_ARG, "too many right-hand sides for the vector kernels");
+  const int grid = blas_grid(L, block);
+  for (int j0 = 0; j0 < J; j0 += 32) {
+    const int Jc = J - j0 < 32 ? J - j0 : 32;
+    VecList sub;
+    for (int j = 0; j < Jc; ++j) sub.p[j] = vs.p[j0 + j];
+    k_multiaxpy<PV><<<grid, block, 0, st>>>(sub, Jc, c_dev + (int64_t)j0 * N, csign, w, L, N);
+  }
+  DD_CUDA(cudaGetLastError());
+  return DD_OK;
+}
+
+template <int PV>
+int blas_scale(const double2* c_dev, const void* in, void* out, int64_t L, int N, cudaStream_t st) {
+  const int block = block_for(N);
+  if (block <= 0) return fail(DD_ERR_ARG, "too many right-hand sides for the vector kernels");
+  k_scale<PV><<<blas_grid(L, block), block, 0, st>>>(c_dev, in, out, L, N);
+  DD_CUDA(cudaGetLastError());
+  return DD_OK;
+}
+
+int blas_demote(const void* in64, void* out32, int64_t nhalf, int64_t VN, cudaStream_t st) {
+  const int64_t n = nhalf * 6 * VN;
+  k_demote<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(reinterpret_cast<const double2*>(in64),
+                                                       reinterpret_cast<float4*>(out32), nhalf, VN);
+  DD_CUDA(cudaGetLastError());
+  return DD_OK;
+}
+
+int blas_promote_add(const void* in32, void* out64, int64_t nhalf, int64_t VN, cudaStream_t st) {
+  const int64_t n = nhalf * 6 * VN;
+  k_promote_add<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(reinterpret_cast<const float4*>(in32),
+                                                            reinterpret_cast<double2*>(out64), nhalf, VN);
+  DD_CUDA(cudaGetLastError());
+  return DD_OK;
+}
+
+int blas_add64(const void* in, void* out, int64_t n, cudaStream_t st) {
+  k_add64<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(reinterpret_cast<const double2*>(in),
+                                                      reinterpret_cast<double2*>(out), n);
+  DD_CUDA(cudaGetLastError());
+  return DD_OK;
+}
+
+template int blas_multidot<P64>(const VecList&, int, const void*, int64_t, int, double2*, int, double2*, cudaStream_t);
+template int blas_multidot<P32>(const VecList&, int, const void*, int64_t, int, double2*, int, double2*, cudaStream_t);
+template int blas_multiaxpy<P64>(const VecList&, int, const double2*, double, void*, int64_t, int, cudaStream_t);
+template int blas_multiaxpy<P32>(const VecList&, int, const double2*, double, void*, int64_t, int, cudaStream_t);
+template int blas_scale<P64>(const double2*, const void*, void*, int64_t, int, cudaStream_t);
+template int blas_scale<P32>(const double2*, const void*, void*, int64_t, int, cudaStream_t);
+
+}  // namespace dd

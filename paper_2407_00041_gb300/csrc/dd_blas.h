@@ -1,0 +1,36 @@
+// Vector kernels of the Krylov solver (see dd_blas.cu for the conventions).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dd {
+
+struct VecList {
+  const void* p[32];
+};
+
+int blas_grid(int64_t L, int block);
+// dots[j][r] (+)= <V_j, w>_r for j < J; partials: scratch of
+// blas_grid(L, block) * min(J, 8) * N complex doubles.
+template <int PV>
+int blas_multidot(const VecList& vs, int J, const void* w, int64_t L, int N, double2* dots_dev, int add,
+                  double2* partials, cudaStream_t st);
+// w += csign * sum_j c[j][r] V_j
+template <int PV>
+int blas_multiaxpy(const VecList& vs, int J, const double2* c_dev, double csign, void* w, int64_t L, int N,
+                   cudaStream_t st);
+// out = c[r] * in
+template <int PV>
+int blas_scale(const double2* c_dev, const void* in, void* out, int64_t L, int N, cudaStream_t st);
+// FP64 native field -> FP32 native field (nhalf half fields, VN = Vh * N)
+int blas_demote(const void* in64, void* out32, int64_t nhalf, int64_t VN, cudaStream_t st);
+// FP64 native field += FP32 native field
+int blas_promote_add(const void* in32, void* out64, int64_t nhalf, int64_t VN, cudaStream_t st);
+// out += in over n complex doubles
+int blas_add64(const void* in, void* out, int64_t n, cudaStream_t st);
+
+// Largest number of partial sums blas_multidot needs per RHS and vector chunk.
+inline int64_t blas_partials_len(int N) { return (int64_t)152 * 8 * 8 * N; }
+
+}  // namespace dd

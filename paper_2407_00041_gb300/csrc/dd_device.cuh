@@ -1,0 +1,288 @@
+// Device-side types shared by the library's kernels: complex arithmetic,
+// precision traits, native field accessors and even-odd lattice geometry.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dd {
+
+// ---------------------------------------------------------------- complex
+template <typename R>
+struct cx {
+  R re, im;
+};
+
+template <typename R>
+__device__ __forceinline__ cx<R> mk(R a, R b) {
+  cx<R> c;
+  c.re = a;
+  c.im = b;
+  return c;
+}
+template <typename R>
+__device__ __forceinline__ cx<R> operator+(cx<R> a, cx<R> b) {
+  return mk(a.re + b.re, a.im + b.im);
+}
+template <typename R>
+__device__ __forceinline__ cx<R> operator-(cx<R> a, cx<R> b) {
+  return mk(a.re - b.re, a.im - b.im);
+}
+template <typename R>
+__device__ __forceinline__ cx<R> operator*(R s, cx<R> a) {
+  return mk(s * a.re, s * a.im);
+}
+// a * b
+template <typename R>
+__device__ __forceinline__ cx<R> cmul(cx<R> a, cx<R> b) {
+  return mk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+// acc + a * b
+template <typename R>
+__device__ __forceinline__ cx<R> cfma(cx<R> a, cx<R> b, cx<R> acc) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(-a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(a.im, b.re, acc.im);
+  return acc;
+}
+// acc + conj(a) * b
+template <typename R>
+__device__ __forceinline__ cx<R> cfmac(cx<R> a, cx<R> b, cx<R> acc) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(-a.im, b.re, acc.im);
+  return acc;
+}
+// i * a, -i * a
+template <typename R>
+__device__ __forceinline__ cx<R> mul_i(cx<R> a) {
+  return mk(-a.im, a.re);
+}
+template <typename R>
+__device__ __forceinline__ cx<R> mul_mi(cx<R> a) {
+  return mk(a.im, -a.re);
+}
+template <typename R>
+__device__ __forceinline__ cx<R> neg(cx<R> a) {
+  return mk(-a.re, -a.im);
+}
+template <typename R>
+__device__ __forceinline__ cx<R> zero() {
+  return mk(R(0), R(0));
+}
+
+// ---------------------------------------------------------------- precisions
+enum { P64 = 1, P32 = 2, P16 = 4 };
+
+// Storage of links and self-coupling blocks: one complex (or one pair of
+// reals) per element.
+template <int P>
+struct Store;
+template <>
+struct Store<P64> {
+  using real = double;
+  using elem = double2;  // complex
+};
+template <>
+struct Store<P32> {
+  using real = float;
+  using elem = float2;
+};
+template <>
+struct Store<P16> {
+  using real = float;
+  using elem = __half2;
+};
+
+template <int P>
+__device__ __forceinline__ cx<typename Store<P>::real> ld_elem(const typename Store<P>::elem* p) {
+  if constexpr (P == P64) {
+    double2 v = __ldg(p);
+    return mk(v.x, v.y);
+  } else if constexpr (P == P32) {
+    float2 v = __ldg(p);
+    return mk(v.x, v.y);
+  } else {
+    unsigned int u = __ldg(reinterpret_cast<const unsigned int*>(p));
+    __half2 h = *reinterpret_cast<__half2*>(&u);
+    float2 f = __half22float2(h);
+    return mk(f.x, f.y);
+  }
+}
+
+// Streaming load (data touched once per apply: self-coupling blocks).
+template <int P>
+__device__ __forceinline__ cx<typename Store<P>::real> ld_elem_stream(const typename Store<P>::elem* p) {
+  if constexpr (P == P64) {
+    double2 v = __ldcs(p);
+    return mk(v.x, v.y);
+  } else if constexpr (P == P32) {
+    float2 v = __ldcs(p);
+    return mk(v.x, v.y);
+  } else {
+    unsigned int u = __ldcs(reinterpret_cast<const unsigned int*>(p));
+    __half2 h = *reinterpret_cast<__half2*>(&u);
+    float2 f = __half22float2(h);
+    return mk(f.x, f.y);
+  }
+}
+
+template <int P>
+__device__ __forceinline__ void st_elem(typename Store<P>::elem* p, cx<typename Store<P>::real> v) {
+  if constexpr (P == P64) {
+    *p = make_double2(v.re, v.im);
+  } else if constexpr (P == P32) {
+    *p = make_float2(v.re, v.im);
+  } else {
+    *p = __floats2half2_rn(v.re, v.im);
+  }
+}
+
+// ---------------------------------------------------------------- spinor fields
+// A half field (sites of one parity, Vh sites, N right-hand sides) in native
+// layout.  `base` points at the first component group; `gstride` is the
+// distance between component groups in group units (= Vh * N); FP16 fields
+// carry `scale` [Vh][N].
+struct HalfField {
+  void* base;
+  float* scale;
+};
+
+template <int P>
+struct SpinorStore;
+template <>
+struct SpinorStore<P64> {
+  static constexpr int GROUPS = 12;
+  using group = double2;
+  using real = double;
+};
+template <>
+struct SpinorStore<P32> {
+  static constexpr int GROUPS = 6;
+  using group = float4;
+  using real = float;
+};
+template <>
+struct SpinorStore<P16> {
+  static constexpr int GROUPS = 3;
+  using group = uint4;
+  using real = float;
+};
+
+template <int P>
+__host__ __device__ inline size_t half_field_bytes(int64_t Vh, int nrhs) {
+  size_t n = (size_t)Vh * (size_t)nrhs;
+  if (P == P64) return n * 12 * 16;
+  if (P == P32) return n * 6 * 16;
+  return n * 3 * 16 + n * 4;
+}
+
+// Load the 12 components of site-rhs index `i` (= site * N + r).
+template <int P, typename R>
+__device__ __forceinline__ void load_spinor(const HalfField& f, int64_t gstride, int64_t i, cx<R> v[12]) {
+  if constexpr (P == P64) {
+    const double2* b = reinterpret_cast<const double2*>(f.base) + i;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      double2 t = __ldg(b + c * gstride);
+      v[c] = mk<R>(t.x, t.y);
+    }
+  } else if constexpr (P == P32) {
+    const float4* b = reinterpret_cast<const float4*>(f.base) + i;
+#pragma unroll
+    for (int g = 0; g < 6; ++g) {
+      float4 t = __ldg(b + g * gstride);
+      v[2 * g] = mk<R>(t.x, t.y);
+      v[2 * g + 1] = mk<R>(t.z, t.w);
+    }
+  } else {
+    const uint4* b = reinterpret_cast<const uint4*>(f.base) + i;
+    const float s = __ldg(f.scale + i);
+#pragma unroll
+    for (int g = 0; g < 3; ++g) {
+      uint4 t = __ldg(b + g * gstride);
+      unsigned int w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        __half2 h = *reinterpret_cast<__half2*>(&w[k]);
+        float2 ff = __half22float2(h);
+        v[4 * g + k] = mk<R>(ff.x * s, ff.y * s);
+      }
+    }
+  }
+}
+
+template <int P, typename R>
+__device__ __forceinline__ void store_spinor(const HalfField& f, int64_t gstride, int64_t i, const cx<R> v[12]) {
+  if constexpr (P == P64) {
+    double2* b = reinterpret_cast<double2*>(f.base) + i;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) b[c * gstride] = make_double2(v[c].re, v[c].im);
+  } else if constexpr (P == P32) {
+    float4* b = reinterpret_cast<float4*>(f.base) + i;
+#pragma unroll
+    for (int g = 0; g < 6; ++g)
+      b[g * gstride] = make_float4((float)v[2 * g].re, (float)v[2 * g].im, (float)v[2 * g + 1].re,
+                                   (float)v[2 * g + 1].im);
+  } else {
+    float m = 0.f;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) m = fmaxf(m, fmaxf(fabsf((float)v[c].re), fabsf((float)v[c].im)));
+    const float inv = m > 0.f ? 1.f / m : 0.f;
+    uint4* b = reinterpret_cast<uint4*>(f.base) + i;
+#pragma unroll
+    for (int g = 0; g < 3; ++g) {
+      unsigned int w[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        __half2 h = __floats2half2_rn((float)v[4 * g + k].re * inv, (float)v[4 * g + k].im * inv);
+        w[k] = *reinterpret_cast<unsigned int*>(&h);
+      }
+      b[g * gstride] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    f.scale[i] = m;
+  }
+}
+
+// ---------------------------------------------------------------- geometry
+// Even-odd geometry.  A site of parity p has compact index s = lex / 2
+// (valid because nX is even), so the sites of one parity keep their
+// lexicographic order.
+struct Geom {
+  int n[4];       // nT, nZ, nY, nX
+  int stride[4];  // lexicographic strides of T, Z, Y, X
+  int Vh;         // sites per parity
+  float t_bc;     // sign of hops across the time boundary
+};
+
+struct SiteCoord {
+  int c[4];  // t, z, y, x
+  int lex;
+};
+
+__device__ __forceinline__ SiteCoord site_coords(const Geom& g, int s, int p) {
+  SiteCoord sc;
+  const int lex2 = 2 * s;
+  const int r1 = lex2 / g.n[3];
+  const int x0 = lex2 - r1 * g.n[3];
+  const int r2 = r1 / g.n[2];
+  sc.c[2] = r1 - r2 * g.n[2];
+  sc.c[0] = r2 / g.n[1];
+  sc.c[1] = r2 - sc.c[0] * g.n[1];
+  sc.c[3] = x0 + ((p ^ (sc.c[0] + sc.c[1] + sc.c[2])) & 1);
+  sc.lex = r1 * g.n[3] + sc.c[3];
+  return sc;
+}
+
+// lexicographic index of the neighbour x + mu (fwd) or x - mu (bwd)
+__device__ __forceinline__ int nb_fwd(const Geom& g, const SiteCoord& sc, int mu) {
+  return sc.c[mu] == g.n[mu] - 1 ? sc.lex - (g.n[mu] - 1) * g.stride[mu] : sc.lex + g.stride[mu];
+}
+__device__ __forceinline__ int nb_bwd(const Geom& g, const SiteCoord& sc, int mu) {
+  return sc.c[mu] == 0 ? sc.lex + (g.n[mu] - 1) * g.stride[mu] : sc.lex - g.stride[mu];
+}
+
+}  // namespace dd

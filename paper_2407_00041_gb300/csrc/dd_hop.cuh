@@ -1,0 +1,304 @@
+// Fused Wilson-clover stencil kernel.
+//
+// One thread computes one (output site, right-hand side) pair of one parity:
+//   acc(x) = sum_mu (I + s gamma_mu) (x) U_mu(x)       psi(x + mu)
+//          + sum_mu (I - s gamma_mu) (x) U_mu^H(x - mu) psi(x - mu)
+// with s = -1 for D (the hopping sum of Eq. 1.13 / Eq. 2.6, without the
+// factor 1/2) and s = +1 for D^H = gamma5 D gamma5.  The sum is formed the
+// way the back-substitution after Algorithm 3 of the thesis shows: each
+// neighbour spinor is projected to two independent spin components
+// (6 complex), multiplied by the link, and reconstructed.  Nothing is staged
+// through memory: projection, SU(3) products, reconstruction and the
+// self-coupling epilogue (Eq. 2.5, 2.7) run in registers in one pass.
+//
+// In the chiral basis gamma_mu = [[0, B_mu], [B_mu^H, 0]] with
+//   B_T = I, B_Z = -i sigma_3, B_Y = -i sigma_2, B_X = -i sigma_1,
+// so for psi = (u, l) (upper and lower spin pairs)
+//   (I + t gamma_mu) psi = (h, t B_mu^H h),  h = u + t B_mu l,  t = +-1.
+#pragma once
+
+#include "dd_ops.h"
+
+namespace dd {
+
+__device__ __forceinline__ float ffma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double ffma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// (B_mu l) for spin component 0 / 1 of the lower pair
+template <int MU, typename R>
+__device__ __forceinline__ void b_times(cx<R> l0, cx<R> l1, cx<R>& b0, cx<R>& b1) {
+  if constexpr (MU == 0) {
+    b0 = l0;
+    b1 = l1;
+  } else if constexpr (MU == 1) {  // -i sigma_3
+    b0 = mul_mi(l0);
+    b1 = mul_i(l1);
+  } else if constexpr (MU == 2) {  // -i sigma_2 = [[0, -1], [1, 0]]
+    b0 = neg(l1);
+    b1 = l0;
+  } else {  // -i sigma_1 = [[0, -i], [-i, 0]]
+    b0 = mul_mi(l1);
+    b1 = mul_mi(l0);
+  }
+}
+
+// (B_mu^H g)
+template <int MU, typename R>
+__device__ __forceinline__ void bh_times(cx<R> g0, cx<R> g1, cx<R>& b0, cx<R>& b1) {
+  if constexpr (MU == 0) {
+    b0 = g0;
+    b1 = g1;
+  } else if constexpr (MU == 1) {  // i sigma_3
+    b0 = mul_i(g0);
+    b1 = mul_mi(g1);
+  } else if constexpr (MU == 2) {  // i sigma_2 = [[0, 1], [-1, 0]]
+    b0 = g1;
+    b1 = neg(g0);
+  } else {  // i sigma_1
+    b0 = mul_i(g1);
+    b1 = mul_i(g0);
+  }
+}
+
+// acc += (I + T gamma_mu) (x) W psi, W = U (ADJ = false) or U^H (ADJ = true),
+// scaled by `sign` (+-1, the time-boundary sign).
+template <int PG, int MU, int T, bool ADJ, typename R>
+__device__ __forceinline__ void hop(cx<R> acc[12], const cx<R> psi[12], const typename Store<PG>::elem* U,
+                                    int64_t Vh, R sign) {
+  cx<R> h0[3], h1[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    cx<R> b0, b1;
+    b_times<MU>(psi[6 + c], psi[9 + c], b0, b1);
+    if constexpr (T > 0) {
+      h0[c] = psi[c] + b0;
+      h1[c] = psi[3 + c] + b1;
+    } else {
+      h0[c] = psi[c] - b0;
+      h1[c] = psi[3 + c] - b1;
+    }
+    h0[c] = sign * h0[c];
+    h1[c] = sign * h1[c];
+  }
+  cx<R> u[9];
+#pragma unroll
+  for (int e = 0; e < 9; ++e) u[e] = ld_elem<PG>(U + e * Vh);
+  cx<R> g0[3], g1[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    g0[a] = zero<R>();
+    g1[a] = zero<R>();
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      if constexpr (ADJ) {
+        g0[a] = cfmac(u[3 * b + a], h0[b], g0[a]);
+        g1[a] = cfmac(u[3 * b + a], h1[b], g1[a]);
+      } else {
+        g0[a] = cfma(u[3 * a + b], h0[b], g0[a]);
+        g1[a] = cfma(u[3 * a + b], h1[b], g1[a]);
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    acc[c] = acc[c] + g0[c];
+    acc[3 + c] = acc[3 + c] + g1[c];
+    cx<R> b0, b1;
+    bh_times<MU>(g0[c], g1[c], b0, b1);
+    if constexpr (T > 0) {
+      acc[6 + c] = acc[6 + c] + b0;
+      acc[9 + c] = acc[9 + c] + b1;
+    } else {
+      acc[6 + c] = acc[6 + c] - b0;
+      acc[9 + c] = acc[9 + c] - b1;
+    }
+  }
+}
+
+// out = M x for the two Hermitian 6x6 blocks stored as 18 elements each:
+// elements 0..2 hold the real diagonal in pairs (d0, d1), (d2, d3), (d4, d5);
+// elements 3..17 the strict upper triangle row by row.
+template <int PG, typename R>
+__device__ __forceinline__ void block_apply(const typename Store<PG>::elem* M, int64_t Vh, const cx<R> x[12],
+                                            cx<R> out[12]) {
+#pragma unroll
+  for (int b = 0; b < 2; ++b) {
+    const typename Store<PG>::elem* m = M + (int64_t)18 * b * Vh;
+    cx<R> d01 = ld_elem_stream<PG>(m), d23 = ld_elem_stream<PG>(m + Vh), d45 = ld_elem_stream<PG>(m + 2 * Vh);
+    const R d[6] = {d01.re, d01.im, d23.re, d23.im, d45.re, d45.im};
+#pragma unroll
+    for (int i = 0; i < 6; ++i) out[6 * b + i] = d[i] * x[6 * b + i];
+    int k = 3;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = i + 1; j < 6; ++j) {
+        cx<R> a = ld_elem_stream<PG>(m + k * Vh);
+        ++k;
+        out[6 * b + i] = cfma(a, x[6 * b + j], out[6 * b + i]);
+        out[6 * b + j] = cfmac(a, x[6 * b + i], out[6 * b + j]);
+      }
+  }
+}
+
+template <int PG, int PIN, int POUT, bool DAG, int EPI>
+__global__ void __launch_bounds__(128) k_hop(const HopArgs a) {
+  using R = typename Store<PG>::real;
+  using E = typename Store<PG>::elem;
+  const int64_t nper = (int64_t)a.g.Vh * a.nrhs;
+  int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= nper * a.npar) return;
+  int p = a.p0;
+  if (tid >= nper) {
+    tid -= nper;
+    p ^= 1;
+  }
+  const int s = (int)(tid / a.nrhs);
+  const int r = (int)(tid - (int64_t)s * a.nrhs);
+  const int q = p ^ 1;
+  const int64_t Vh = a.g.Vh;
+  const SiteCoord sc = site_coords(a.g, s, p);
+  // forward hop: (I - gamma) for D, (I + gamma) for D^H; backward the opposite
+  constexpr int TF = DAG ? +1 : -1;
+  constexpr int TB = -TF;
+
+  cx<R> acc[12];
+#pragma unroll
+  for (int c = 0; c < 12; ++c) acc[c] = zero<R>();
+
+  const E* Up = reinterpret_cast<const E*>(a.U[p]);
+  const E* Uq = reinterpret_cast<const E*>(a.U[q]);
+
+#define DD_HOP_DIR(MU)                                                                     \
+  {                                                                                        \
+    cx<R> psi[12];                                                                         \
+    int nl = nb_fwd(a.g, sc, MU);                                                          \
+    R sg = (MU == 0 && sc.c[0] == a.g.n[0] - 1) ? (R)a.g.t_bc : (R)1;                      \
+    load_spinor<PIN, R>(a.in[q], a.gstride, (int64_t)(nl >> 1) * a.nrhs + r, psi);         \
+    hop<PG, MU, TF, false, R>(acc, psi, Up + (int64_t)(MU * 9) * Vh + s, Vh, sg);          \
+    nl = nb_bwd(a.g, sc, MU);                                                              \
+    sg = (MU == 0 && sc.c[0] == 0) ? (R)a.g.t_bc : (R)1;                                   \
+    load_spinor<PIN, R>(a.in[q], a.gstride, (int64_t)(nl >> 1) * a.nrhs + r, psi);         \
+    hop<PG, MU, TB, true, R>(acc, psi, Uq + (int64_t)(MU * 9) * Vh + (nl >> 1), Vh, sg);   \
+  }
+  DD_HOP_DIR(0)
+  DD_HOP_DIR(1)
+  DD_HOP_DIR(2)
+  DD_HOP_DIR(3)
+#undef DD_HOP_DIR
+
+  const R beta = (R)a.beta;
+  const int64_t i = tid;  // == s * nrhs + r
+  const E* M = reinterpret_cast<const E*>(a.M[p]);
+  cx<R> res[12];
+  if constexpr (EPI == EPI_D || EPI == EPI_RESID) {
+    cx<R> y[12];
+    if constexpr (EPI == EPI_D)
+      load_spinor<PIN, R>(a.y[p], a.gstride, i, y);
+    else
+      load_spinor<POUT, R>(a.y[p], a.gstride, i, y);
+    block_apply<PG, R>(M + s, Vh, y, res);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      res[c].re = ffma(beta, acc[c].re, res[c].re);
+      res[c].im = ffma(beta, acc[c].im, res[c].im);
+    }
+    if constexpr (EPI == EPI_RESID) {
+      cx<R> z[12];
+      load_spinor<POUT, R>(a.z[p], a.gstride, i, z);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) res[c] = z[c] - res[c];
+    }
+  } else if constexpr (EPI == EPI_AINV) {
+#pragma unroll
+    for (int c = 0; c < 12; ++c) acc[c] = beta * acc[c];
+    block_apply<PG, R>(M + s, Vh, acc, res);
+  } else if constexpr (EPI == EPI_ADD) {
+    load_spinor<POUT, R>(a.y[p], a.gstride, i, res);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      res[c].re = ffma(beta, acc[c].re, res[c].re);
+      res[c].im = ffma(beta, acc[c].im, res[c].im);
+    }
+  } else {  // EPI_AINV_ADD
+    cx<R> y[12];
+    load_spinor<POUT, R>(a.y[p], a.gstride, i, y);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      y[c].re = ffma(beta, acc[c].re, y[c].re);
+      y[c].im = ffma(beta, acc[c].im, y[c].im);
+    }
+    block_apply<PG, R>(M + s, Vh, y, res);
+  }
+  store_spinor<POUT, R>(a.out[p], a.gstride, i, res);
+}
+
+template <int PG, int PIN, int POUT>
+__global__ void __launch_bounds__(128) k_block(const BlockArgs a) {
+  using R = typename Store<PG>::real;
+  using E = typename Store<PG>::elem;
+  const int64_t nper = a.Vh * a.nrhs;
+  int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= nper * a.npar) return;
+  int p = a.p0;
+  if (tid >= nper) {
+    tid -= nper;
+    p ^= 1;
+  }
+  const int s = (int)(tid / a.nrhs);
+  cx<R> y[12], res[12];
+  load_spinor<PIN, R>(a.y[p], a.gstride, tid, y);
+  block_apply<PG, R>(reinterpret_cast<const E*>(a.M[p]) + s, a.Vh, y, res);
+  store_spinor<POUT, R>(a.out[p], a.gstride, tid, res);
+}
+
+// Host launchers; the instantiation units explicitly instantiate one
+// precision triple each, other units only see the declarations in dd_ops.h.
+template <int PG, int PIN, int POUT>
+cudaError_t launch_hop(const HopArgs& a, bool dagger, int epi, cudaStream_t st) {
+  const int64_t n = (int64_t)a.g.Vh * a.nrhs * a.npar;
+  if (n == 0) return cudaSuccess;
+  const int threads = 128;
+  const unsigned blocks = (unsigned)((n + threads - 1) / threads);
+  switch (epi * 2 + (dagger ? 1 : 0)) {
+    case EPI_D * 2:
+      k_hop<PG, PIN, POUT, false, EPI_D><<<blocks, threads, 0, st>>>(a);
+      break;
+    case EPI_D * 2 + 1:
+      k_hop<PG, PIN, POUT, true, EPI_D><<<blocks, threads, 0, st>>>(a);
+      break;
+    case EPI_AINV * 2:
+      k_hop<PG, PIN, POUT, false, EPI_AINV><<<blocks, threads, 0, st>>>(a);
+      break;
+    case EPI_AINV * 2 + 1:
+      k_hop<PG, PIN, POUT, true, EPI_AINV><<<blocks, threads, 0, st>>>(a);
+      break;
+    case EPI_RESID * 2:
+      k_hop<PG, PIN, POUT, false, EPI_RESID><<<blocks, threads, 0, st>>>(a);
+      break;
+    case EPI_ADD * 2:
+      k_hop<PG, PIN, POUT, false, EPI_ADD><<<blocks, threads, 0, st>>>(a);
+      break;
+    case EPI_AINV_ADD * 2:
+      k_hop<PG, PIN, POUT, false, EPI_AINV_ADD><<<blocks, threads, 0, st>>>(a);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <int PG, int PIN, int POUT>
+cudaError_t launch_block(const BlockArgs& a, cudaStream_t st) {
+  const int64_t n = a.Vh * a.nrhs * a.npar;
+  if (n == 0) return cudaSuccess;
+  const int threads = 128;
+  k_block<PG, PIN, POUT><<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+#define DD_INSTANTIATE_HOP(PG, PIN, POUT)                                                                  \
+  template cudaError_t launch_hop<PG, PIN, POUT>(const HopArgs&, bool, int, cudaStream_t);                \
+  template cudaError_t launch_block<PG, PIN, POUT>(const BlockArgs&, cudaStream_t);
+
+}  // namespace dd

@@ -1,0 +1,131 @@
+// Host-side internals of the library: handle structures, error reporting and
+// the operator layer that the C ABI, the solver and the batch path share.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/dd_wilson.h"
+#include "dd_device.cuh"
+
+namespace dd {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+int fail(int status, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* where);
+
+#define DD_CUDA(call)                                       \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return ::dd::cuda_fail(e_, #call); \
+  } while (0)
+
+#define DD_TRY(call)          \
+  do {                        \
+    int s_ = (call);          \
+    if (s_ != DD_OK) return s_; \
+  } while (0)
+
+inline int prec_index(int prec) { return prec == P64 ? 0 : prec == P32 ? 1 : prec == P16 ? 2 : -1; }
+
+// Device buffer owned by a handle.
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  int alloc(size_t n);
+  int ensure(size_t n);  // grow-only
+  void release();
+};
+
+}  // namespace dd
+
+struct dd_lattice {
+  int dims[4];
+  int t_bc;
+  int64_t V, Vh;
+  dd::Geom geom() const;
+};
+
+struct dd_gauge {
+  const dd_lattice* lat;
+  unsigned prec_mask;
+  // native links per precision (index 0: F64, 1: F32, 2: F16):
+  // [parity][mu][9][Vh] complex elements
+  dd::DevBuf links[3];
+  const void* U(int pi, int parity) const;
+};
+
+struct dd_clover {
+  const dd_gauge* gauge;
+  const dd_lattice* lat;
+  double m0, csw;
+  unsigned prec_mask;
+  // self-coupling blocks per precision: [parity][36][Vh] elements
+  dd::DevBuf clov[3];
+  // A_ee^{-1} per precision: [36][Vh] elements (even sites)
+  dd::DevBuf ainv[3];
+  // workspace for canonical-layout calls and operator intermediates
+  dd::DevBuf ws_in, ws_out, ws_tmp, ws_canon_in, ws_canon_out;
+  const void* M(int pi, int parity) const;  // A of a parity
+  const void* Ainv(int pi) const;
+};
+
+namespace dd {
+
+// A native field: two half fields (parity 0 and 1; a half-lattice field sets
+// only one of them).
+struct Field {
+  HalfField h[2];
+  int prec = 0;
+  int nrhs = 1;
+};
+
+// Build a Field view of a native buffer.  subset: 0 full (even then odd),
+// 1 odd sites only, 2 even sites only.
+Field field_view(const dd_lattice* lat, int prec, int subset, void* base, int nrhs);
+size_t field_bytes(const dd_lattice* lat, int prec, int subset, int nrhs);
+
+// ---- operator layer (all enqueue on `st`) ----
+// Precision of the operator handle to use (pg) and of the vectors (pv):
+// (F64, F64), (F32, F32), (F16, F16) or (F16, F32).
+int op_D(const dd_clover* op, int pg, int pv, bool dagger, const Field& in, const Field& out, cudaStream_t st);
+int op_SC(const dd_clover* op, int pg, int pv, const Field& in, const Field& out, cudaStream_t st);
+// out_o = Dhat in_o (odd half fields); tmp_e: even half-field workspace
+int op_Dhat(const dd_clover* op, int pg, int pv, bool dagger, const Field& in, const Field& out, const Field& tmp,
+            cudaStream_t st);
+// r = b - D x (full fields)
+int op_residual(const dd_clover* op, int pg, int pv, const Field& b, const Field& x, const Field& r,
+                cudaStream_t st);
+// bhat_o = b_o - D_oe A_ee^{-1} b_e   (b full, bhat odd, tmp even)
+int op_prepare(const dd_clover* op, int pg, int pv, const Field& b, const Field& bhat, const Field& tmp,
+               cudaStream_t st);
+// x_e = A_ee^{-1} (b_e - D_eo x_o)   (b full; x full with its odd half given)
+int op_reconstruct(const dd_clover* op, int pg, int pv, const Field& b, const Field& x, cudaStream_t st);
+
+// ---- setup kernels (dd_setup.cu) ----
+int links_to_native(const dd_lattice* lat, const double* U_canon_dev, dd_gauge* g, cudaStream_t st);
+int links_to_canonical(const dd_gauge* g, double* U_canon_dev, cudaStream_t st);
+int clover_build(dd_clover* op, cudaStream_t st);  // FP64 blocks, A_ee^{-1}, demoted copies
+int clover_to_dense(const dd_clover* op, double* A_dev /*[V][144] complex*/, cudaStream_t st);
+int pack(const dd_lattice* lat, int prec, int subset, const double* canon, const Field& f, cudaStream_t st);
+int unpack(const dd_lattice* lat, int prec, int subset, const Field& f, double* canon, cudaStream_t st);
+
+// ---- vector kernels on native half fields (dd_blas.cu) ----
+// Each works on `nh` consecutive half fields of a Field (nh = 1 or 2).
+struct Vec {
+  Field f;
+  int npar;   // 1: h[p0] only, 2: both halves
+  int p0;
+};
+int64_t vec_len(const dd_lattice* lat, const Vec& v);  // sites*nrhs
+
+}  // namespace dd

@@ -1,0 +1,48 @@
+// Argument blocks of the stencil and self-coupling kernels and the
+// declarations of their host launchers (defined in dd_hop.cuh, instantiated
+// once per precision triple in dd_hop_*.cu).
+#pragma once
+
+#include "dd_device.cuh"
+
+namespace dd {
+
+enum Epi {
+  EPI_D = 0,        // out = M y + beta acc            (D, D^H; Dhat second step)
+  EPI_AINV = 1,     // out = M (beta acc)              (Dhat first step)
+  EPI_RESID = 2,    // out = z - (M y + beta acc)      (r = b - D x)
+  EPI_ADD = 3,      // out = y + beta acc              (right-hand side preparation)
+  EPI_AINV_ADD = 4  // out = M (y + beta acc)          (even-site reconstruction)
+};
+
+struct HopArgs {
+  Geom g;
+  int nrhs;
+  int p0;            // output parity of the first part of the grid
+  int npar;          // number of output parities in this launch (1 or 2)
+  int64_t gstride;   // component-group stride of a half field = Vh * nrhs
+  HalfField in[2];   // input field by parity (parity 1 - p is read for output parity p)
+  HalfField out[2];  // output by parity
+  HalfField y[2];    // per output parity: self term (EPI_D: the input's own parity)
+  HalfField z[2];    // per output parity: residual base (EPI_RESID)
+  const void* U[2];  // links by parity of their site: [mu][9][Vh] complex elements
+  const void* M[2];  // 6x6 Hermitian blocks by output parity: [36][Vh] elements
+  double beta;
+};
+
+// Self-coupling apply without hopping: out = M y on npar parities.
+struct BlockArgs {
+  int64_t Vh;
+  int nrhs;
+  int p0, npar;
+  int64_t gstride;
+  HalfField y[2], out[2];
+  const void* M[2];
+};
+
+template <int PG, int PIN, int POUT>
+cudaError_t launch_hop(const HopArgs& a, bool dagger, int epi, cudaStream_t st);
+template <int PG, int PIN, int POUT>
+cudaError_t launch_block(const BlockArgs& a, cudaStream_t st);
+
+}  // namespace dd

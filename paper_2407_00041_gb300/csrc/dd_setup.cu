@@ -1,0 +1,500 @@
+// Setup kernels: native link layout, self-coupling construction (Eq. 1.11,
+// 1.12, 2.5) and inversion, precision copies, and canonical <-> native field
+// conversion.
+#include "dd_internal.h"
+
+namespace dd {
+
+namespace {
+
+struct LexGeom {
+  int n[4];
+  int stride[4];
+  int64_t Vh;
+};
+
+LexGeom lex_geom(const dd_lattice* lat) {
+  LexGeom g;
+  for (int i = 0; i < 4; ++i) g.n[i] = lat->dims[i];
+  g.stride[3] = 1;
+  g.stride[2] = g.n[3];
+  g.stride[1] = g.n[3] * g.n[2];
+  g.stride[0] = g.n[3] * g.n[2] * g.n[1];
+  g.Vh = lat->Vh;
+  return g;
+}
+
+__device__ __forceinline__ void lex_to_coords(const LexGeom& g, int lex, int c[4]) {
+  c[3] = lex % g.n[3];
+  int r = lex / g.n[3];
+  c[2] = r % g.n[2];
+  r /= g.n[2];
+  c[1] = r % g.n[1];
+  c[0] = r / g.n[1];
+}
+
+__device__ __forceinline__ int coords_to_lex(const LexGeom& g, const int c[4]) {
+  return ((c[0] * g.n[1] + c[1]) * g.n[2] + c[2]) * g.n[3] + c[3];
+}
+
+// ---------------------------------------------------------------- links
+__global__ void k_links_to_native(LexGeom g, const double2* __restrict__ Uc, double2* U64, float2* U32,
+                                  __half2* U16) {
+  const int64_t V = 2 * g.Vh;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= V * 4) return;
+  const int lex = (int)(t >> 2), mu = (int)(t & 3);
+  int c[4];
+  lex_to_coords(g, lex, c);
+  const int p = (c[0] + c[1] + c[2] + c[3]) & 1;
+  const int64_t s = lex >> 1;
+  const int64_t base = (int64_t)p * 36 * g.Vh + (int64_t)mu * 9 * g.Vh + s;
+#pragma unroll
+  for (int e = 0; e < 9; ++e) {
+    double2 v = Uc[t * 9 + e];
+    U64[base + e * g.Vh] = v;
+    if (U32) U32[base + e * g.Vh] = make_float2((float)v.x, (float)v.y);
+    if (U16) U16[base + e * g.Vh] = __floats2half2_rn((float)v.x, (float)v.y);
+  }
+}
+
+__global__ void k_links_to_canonical(LexGeom g, const double2* __restrict__ U64, double2* Uc) {
+  const int64_t V = 2 * g.Vh;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= V * 4) return;
+  const int lex = (int)(t >> 2), mu = (int)(t & 3);
+  int c[4];
+  lex_to_coords(g, lex, c);
+  const int p = (c[0] + c[1] + c[2] + c[3]) & 1;
+  const int64_t base = (int64_t)p * 36 * g.Vh + (int64_t)mu * 9 * g.Vh + (lex >> 1);
+  for (int e = 0; e < 9; ++e) Uc[t * 9 + e] = U64[base + e * g.Vh];
+}
+
+// ---------------------------------------------------------------- 3x3 algebra (FP64)
+struct M3 {
+  cx<double> m[9];
+};
+
+__device__ __forceinline__ M3 m3_load(const LexGeom& g, const double2* U64, const int c[4], int mu) {
+  const int lex = coords_to_lex(g, c);
+  const int p = (c[0] + c[1] + c[2] + c[3]) & 1;
+  const double2* b = U64 + (int64_t)p * 36 * g.Vh + (int64_t)mu * 9 * g.Vh + (lex >> 1);
+  M3 r;
+#pragma unroll
+  for (int e = 0; e < 9; ++e) {
+    double2 v = b[e * g.Vh];
+    r.m[e] = mk(v.x, v.y);
+  }
+  return r;
+}
+
+__device__ __forceinline__ M3 m3_dag(const M3& a) {
+  M3 r;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) r.m[3 * i + j] = mk(a.m[3 * j + i].re, -a.m[3 * j + i].im);
+  return r;
+}
+
+__device__ __forceinline__ M3 m3_mul(const M3& a, const M3& b) {
+  M3 r;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      cx<double> acc = zero<double>();
+#pragma unroll
+      for (int k = 0; k < 3; ++k) acc = cfma(a.m[3 * i + k], b.m[3 * k + j], acc);
+      r.m[3 * i + j] = acc;
+    }
+  return r;
+}
+
+__device__ __forceinline__ void shifted(const LexGeom& g, const int c[4], int mu, int d, int out[4]) {
+  for (int i = 0; i < 4; ++i) out[i] = c[i];
+  out[mu] = (c[mu] + d + g.n[mu]) % g.n[mu];
+}
+
+// Q_munu(x), Eq. 1.12: the four plaquettes in the mu-nu plane that start and
+// end at x (gauge links are periodic).
+__device__ M3 clover_leaves(const LexGeom& g, const double2* U, const int x[4], int mu, int nu) {
+  int xpm[4], xpn[4], xmm[4], xmn[4], xmm_pn[4], xmm_mn[4], xmn_pm[4];
+  shifted(g, x, mu, +1, xpm);
+  shifted(g, x, nu, +1, xpn);
+  shifted(g, x, mu, -1, xmm);
+  shifted(g, x, nu, -1, xmn);
+  shifted(g, xmm, nu, +1, xmm_pn);
+  shifted(g, xmm, nu, -1, xmm_mn);
+  shifted(g, xmn, mu, +1, xmn_pm);
+  // U_mu(x) U_nu(x+mu) U_mu(x+nu)^H U_nu(x)^H
+  M3 l = m3_mul(m3_mul(m3_load(g, U, x, mu), m3_load(g, U, xpm, nu)),
+                m3_mul(m3_dag(m3_load(g, U, xpn, mu)), m3_dag(m3_load(g, U, x, nu))));
+  M3 q = l;
+  // U_nu(x) U_mu(x-mu+nu)^H U_nu(x-mu)^H U_mu(x-mu)
+  l = m3_mul(m3_mul(m3_load(g, U, x, nu), m3_dag(m3_load(g, U, xmm_pn, mu))),
+             m3_mul(m3_dag(m3_load(g, U, xmm, nu)), m3_load(g, U, xmm, mu)));
+  for (int e = 0; e < 9; ++e) q.m[e] = q.m[e] + l.m[e];
+  // U_mu(x-mu)^H U_nu(x-mu-nu)^H U_mu(x-mu-nu) U_nu(x-nu)
+  l = m3_mul(m3_mul(m3_dag(m3_load(g, U, xmm, mu)), m3_dag(m3_load(g, U, xmm_mn, nu))),
+             m3_mul(m3_load(g, U, xmm_mn, mu), m3_load(g, U, xmn, nu)));
+  for (int e = 0; e < 9; ++e) q.m[e] = q.m[e] + l.m[e];
+  // U_nu(x-nu)^H U_mu(x-nu) U_nu(x-nu+mu) U_mu(x)^H
+  l = m3_mul(m3_mul(m3_dag(m3_load(g, U, xmn, nu)), m3_load(g, U, xmn, mu)),
+             m3_mul(m3_load(g, U, xmn_pm, nu), m3_dag(m3_load(g, U, x, mu))));
+  for (int e = 0; e < 9; ++e) q.m[e] = q.m[e] + l.m[e];
+  return q;
+}
+
+// 2x2 spin blocks of the chiral basis: gamma_mu = [[0, B_mu], [B_mu^H, 0]]
+__device__ __forceinline__ cx<double> Bmat(int mu, int i, int j) {
+  // B_T = I, B_Z = diag(-i, i), B_Y = [[0, -1], [1, 0]], B_X = [[0, -i], [-i, 0]]
+  if (mu == 0) return mk(i == j ? 1.0 : 0.0, 0.0);
+  if (mu == 1) return i != j ? mk(0.0, 0.0) : mk(0.0, i == 0 ? -1.0 : 1.0);
+  if (mu == 2) return i == j ? mk(0.0, 0.0) : mk(i == 0 ? -1.0 : 1.0, 0.0);
+  return i == j ? mk(0.0, 0.0) : mk(0.0, -1.0);
+}
+
+// Element (i, j) of gamma_mu gamma_nu restricted to chirality block b:
+// b = 0: B_mu B_nu^H, b = 1: B_mu^H B_nu.
+__device__ __forceinline__ cx<double> gg_block(int b, int mu, int nu, int i, int j) {
+  cx<double> acc = zero<double>();
+  for (int k = 0; k < 2; ++k) {
+    cx<double> x, y;
+    if (b == 0) {
+      x = Bmat(mu, i, k);
+      cx<double> t = Bmat(nu, j, k);
+      y = mk(t.re, -t.im);
+    } else {
+      cx<double> t = Bmat(mu, k, i);
+      x = mk(t.re, -t.im);
+      y = Bmat(nu, k, j);
+    }
+    acc = cfma(x, y, acc);
+  }
+  return acc;
+}
+
+// One thread per site: both 6x6 blocks of A(x) = (m0 + 4) I
+//   - (c_sw / 16) sum_{mu < nu} (gamma_mu gamma_nu) (x) (Q_munu - Q_munu^H).
+__global__ void k_clover_build(LexGeom g, const double2* __restrict__ U, double m0, double csw, double2* clov) {
+  const int64_t V = 2 * g.Vh;
+  const int lex = blockIdx.x * blockDim.x + threadIdx.x;
+  if (lex >= V) return;
+  int x[4];
+  lex_to_coords(g, lex, x);
+  const int p = (x[0] + x[1] + x[2] + x[3]) & 1;
+  const int64_t s = lex >> 1;
+  cx<double> A[2][6][6];
+  for (int b = 0; b < 2; ++b)
+    for (int i = 0; i < 6; ++i)
+      for (int j = 0; j < 6; ++j) A[b][i][j] = mk(i == j ? m0 + 4.0 : 0.0, 0.0);
+  for (int mu = 0; mu < 4; ++mu)
+    for (int nu = mu + 1; nu < 4; ++nu) {
+      M3 Q = clover_leaves(g, U, x, mu, nu);
+      M3 F;
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+          F.m[3 * i + j] = mk(Q.m[3 * i + j].re - Q.m[3 * j + i].re, Q.m[3 * i + j].im + Q.m[3 * j + i].im);
+      for (int b = 0; b < 2; ++b)
+        for (int si = 0; si < 2; ++si)
+          for (int sj = 0; sj < 2; ++sj) {
+            cx<double> gg = gg_block(b, mu, nu, si, sj);
+            if (gg.re == 0.0 && gg.im == 0.0) continue;
+            for (int a = 0; a < 3; ++a)
+              for (int c = 0; c < 3; ++c) {
+                cx<double> t = cmul(gg, F.m[3 * a + c]);
+                A[b][3 * si + a][3 * sj + c] = A[b][3 * si + a][3 * sj + c] - (csw / 16.0) * t;
+              }
+          }
+    }
+  double2* out = clov + (int64_t)p * 36 * g.Vh + s;
+  for (int b = 0; b < 2; ++b) {
+    double2* o = out + (int64_t)18 * b * g.Vh;
+    for (int k = 0; k < 3; ++k) o[k * g.Vh] = make_double2(A[b][2 * k][2 * k].re, A[b][2 * k + 1][2 * k + 1].re);
+    int k = 3;
+    for (int i = 0; i < 6; ++i)
+      for (int j = i + 1; j < 6; ++j, ++k) o[k * g.Vh] = make_double2(A[b][i][j].re, A[b][i][j].im);
+  }
+}
+
+__device__ void unpack_block(const double2* m, int64_t Vh, cx<double> A[6][6]) {
+  for (int k = 0; k < 3; ++k) {
+    double2 d = m[k * Vh];
+    A[2 * k][2 * k] = mk(d.x, 0.0);
+    A[2 * k + 1][2 * k + 1] = mk(d.y, 0.0);
+  }
+  int k = 3;
+  for (int i = 0; i < 6; ++i)
+    for (int j = i + 1; j < 6; ++j, ++k) {
+      double2 v = m[k * Vh];
+      A[i][j] = mk(v.x, v.y);
+      A[j][i] = mk(v.x, -v.y);
+    }
+}
+
+// A_ee^{-1}: Gauss-Jordan elimination with partial pivoting on each 6x6 block
+// of every even site.  A block whose pivot falls below 1e-12 of the block's
+// largest entry raises `flag`.
+__global__ void k_clover_invert(int64_t Vh, const double2* __restrict__ clov_even, double2* ainv, int* flag) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= Vh) return;
+  for (int b = 0; b < 2; ++b) {
+    cx<double> A[6][6], X[6][6];
+    unpack_block(clov_even + (int64_t)18 * b * Vh + s, Vh, A);
+    double amax = 0.0;
+    for (int i = 0; i < 6; ++i)
+      for (int j = 0; j < 6; ++j) {
+        X[i][j] = mk(i == j ? 1.0 : 0.0, 0.0);
+        amax = fmax(amax, fabs(A[i][j].re) + fabs(A[i][j].im));
+      }
+    for (int col = 0; col < 6; ++col) {
+      int piv = col;
+      double best = -1.0;
+      for (int r = col; r < 6; ++r) {
+        double m = A[r][col].re * A[r][col].re + A[r][col].im * A[r][col].im;
+        if (m > best) {
+          best = m;
+          piv = r;
+        }
+      }
+      if (!(sqrt(best) > 1e-12 * amax)) {
+        atomicExch(flag, 1);
+        return;
+      }
+      if (piv != col)
+        for (int j = 0; j < 6; ++j) {
+          cx<double> t = A[col][j];
+          A[col][j] = A[piv][j];
+          A[piv][j] = t;
+          t = X[col][j];
+          X[col][j] = X[piv][j];
+          X[piv][j] = t;
+        }
+      const cx<double> d = A[col][col];
+      const double dn = d.re * d.re + d.im * d.im;
+      const cx<double> inv = mk(d.re / dn, -d.im / dn);
+      for (int j = 0; j < 6; ++j) {
+        A[col][j] = cmul(inv, A[col][j]);
+        X[col][j] = cmul(inv, X[col][j]);
+      }
+      for (int r = 0; r < 6; ++r) {
+        if (r == col) continue;
+        const cx<double> f = A[r][col];
+        for (int j = 0; j < 6; ++j) {
+          A[r][j] = A[r][j] - cmul(f, A[col][j]);
+          X[r][j] = X[r][j] - cmul(f, X[col][j]);
+        }
+      }
+    }
+    double2* o = ainv + (int64_t)18 * b * Vh + s;
+    for (int k = 0; k < 3; ++k) o[k * Vh] = make_double2(X[2 * k][2 * k].re, X[2 * k + 1][2 * k + 1].re);
+    int k = 3;
+    for (int i = 0; i < 6; ++i)
+      for (int j = i + 1; j < 6; ++j, ++k) o[k * Vh] = make_double2(X[i][j].re, X[i][j].im);
+  }
+}
+
+__global__ void k_demote32(const double2* __restrict__ in, float2* out, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = make_float2((float)in[i].x, (float)in[i].y);
+}
+__global__ void k_demote16(const double2* __restrict__ in, __half2* out, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = __floats2half2_rn((float)in[i].x, (float)in[i].y);
+}
+
+__global__ void k_clover_dense(LexGeom g, const double2* __restrict__ clov, double2* A) {
+  const int64_t V = 2 * g.Vh;
+  const int lex = blockIdx.x * blockDim.x + threadIdx.x;
+  if (lex >= V) return;
+  int x[4];
+  lex_to_coords(g, lex, x);
+  const int p = (x[0] + x[1] + x[2] + x[3]) & 1;
+  double2* o = A + (int64_t)lex * 144;
+  for (int i = 0; i < 144; ++i) o[i] = make_double2(0.0, 0.0);
+  for (int b = 0; b < 2; ++b) {
+    cx<double> B[6][6];
+    unpack_block(clov + (int64_t)p * 36 * g.Vh + (int64_t)18 * b * g.Vh + (lex >> 1), g.Vh, B);
+    for (int i = 0; i < 6; ++i)
+      for (int j = 0; j < 6; ++j) o[(6 * b + i) * 12 + 6 * b + j] = make_double2(B[i][j].re, B[i][j].im);
+  }
+}
+
+// ---------------------------------------------------------------- fields
+struct PackArgs {
+  LexGeom g;
+  int nrhs;
+  int subset;  // 0 full, 1 odd, 2 even
+  int p0, npar;
+  int64_t gstride;
+  HalfField h[2];
+};
+
+__device__ __forceinline__ int64_t canon_offset(const PackArgs& a, int p, int64_t s, int r) {
+  if (a.subset == 0) {
+    // lexicographic index of compact site s of parity p
+    const int lex2 = (int)(2 * s);
+    const int r1 = lex2 / a.g.n[3];
+    const int x0 = lex2 - r1 * a.g.n[3];
+    const int r2 = r1 / a.g.n[2];
+    const int y = r1 - r2 * a.g.n[2];
+    const int t = r2 / a.g.n[1];
+    const int z = r2 - t * a.g.n[1];
+    const int lex = r1 * a.g.n[3] + x0 + ((p ^ (t + z + y)) & 1);
+    return ((int64_t)r * 2 * a.g.Vh + lex) * 12;
+  }
+  return ((int64_t)r * a.g.Vh + s) * 12;
+}
+
+template <int P>
+__global__ void k_pack(PackArgs a, const double2* __restrict__ canon) {
+  using R = typename SpinorStore<P>::real;
+  const int64_t nper = a.g.Vh * a.nrhs;
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nper * a.npar) return;
+  int p = a.p0;
+  if (t >= nper) {
+    t -= nper;
+    p ^= 1;
+  }
+  const int64_t s = t / a.nrhs;
+  const int r = (int)(t - s * a.nrhs);
+  const double2* src = canon + canon_offset(a, p, s, r);
+  cx<R> v[12];
+#pragma unroll
+  for (int c = 0; c < 12; ++c) {
+    double2 d = src[c];
+    v[c] = mk<R>((R)d.x, (R)d.y);
+  }
+  store_spinor<P, R>(a.h[p], a.gstride, t, v);
+}
+
+template <int P>
+__global__ void k_unpack(PackArgs a, double2* canon) {
+  using R = typename SpinorStore<P>::real;
+  const int64_t nper = a.g.Vh * a.nrhs;
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nper * a.npar) return;
+  int p = a.p0;
+  if (t >= nper) {
+    t -= nper;
+    p ^= 1;
+  }
+  const int64_t s = t / a.nrhs;
+  const int r = (int)(t - s * a.nrhs);
+  cx<R> v[12];
+  load_spinor<P, R>(a.h[p], a.gstride, t, v);
+  double2* dst = canon + canon_offset(a, p, s, r);
+#pragma unroll
+  for (int c = 0; c < 12; ++c) dst[c] = make_double2((double)v[c].re, (double)v[c].im);
+}
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+PackArgs pack_args(const dd_lattice* lat, int subset, const Field& f) {
+  PackArgs a;
+  a.g = lex_geom(lat);
+  a.nrhs = f.nrhs;
+  a.subset = subset;
+  a.p0 = subset == 2 ? 0 : (subset == 1 ? 1 : 0);
+  a.npar = subset == 0 ? 2 : 1;
+  a.gstride = lat->Vh * f.nrhs;
+  a.h[0] = f.h[0];
+  a.h[1] = f.h[1];
+  return a;
+}
+
+}  // namespace
+
+int links_to_native(const dd_lattice* lat, const double* Uc, dd_gauge* g, cudaStream_t st) {
+  const int64_t n = lat->V * 4;
+  k_links_to_native<<<nblk(n, 128), 128, 0, st>>>(
+      lex_geom(lat), reinterpret_cast<const double2*>(Uc), reinterpret_cast<double2*>(g->links[0].ptr),
+      reinterpret_cast<float2*>(g->links[1].ptr), reinterpret_cast<__half2*>(g->links[2].ptr));
+  DD_CUDA(cudaGetLastError());
+  return DD_OK;
+}
+
+int links_to_canonical(const dd_gauge* g, double* Uc, cudaStream_t st) {
+  const int64_t n = g->lat->V * 4;
+  k_links_to_canonical<<<nblk(n, 128), 128, 0, st>>>(lex_geom(g->lat),
+                                                     reinterpret_cast<const double2*>(g->links[0].ptr),
+                                                     reinterpret_cast<double2*>(Uc));
+  DD_CUDA(cudaGetLastError());
+  return DD_OK;
+}
+
+int clover_build(dd_clover* op, cudaStream_t st) {
+  const dd_lattice* lat = op->lat;
+  const int64_t Vh = lat->Vh;
+  const int64_t nclov = 2 * 36 * Vh, nainv = 36 * Vh;
+  DD_TRY(op->clov[0].alloc(nclov * sizeof(double2)));
+  DD_TRY(op->ainv[0].alloc(nainv * sizeof(double2)));
+  k_clover_build<<<nblk(lat->V, 64), 64, 0, st>>>(lex_geom(lat),
+                                                  reinterpret_cast<const double2*>(op->gauge->links[0].ptr), op->m0,
+                                                  op->csw, reinterpret_cast<double2*>(op->clov[0].ptr));
+  DD_CUDA(cudaGetLastError());
+  DevBuf flag;
+  DD_TRY(flag.alloc(sizeof(int)));
+  DD_CUDA(cudaMemsetAsync(flag.ptr, 0, sizeof(int), st));
+  k_clover_invert<<<nblk(Vh, 64), 64, 0, st>>>(Vh, reinterpret_cast<const double2*>(op->clov[0].ptr),
+                                                reinterpret_cast<double2*>(op->ainv[0].ptr),
+                                                reinterpret_cast<int*>(flag.ptr));
+  DD_CUDA(cudaGetLastError());
+  int hflag = 0;
+  DD_CUDA(cudaMemcpyAsync(&hflag, flag.ptr, sizeof(int), cudaMemcpyDeviceToHost, st));
+  DD_CUDA(cudaStreamSynchronize(st));
+  if (hflag) return fail(DD_ERR_SINGULAR, "an even-site self-coupling block is singular");
+  if (op->prec_mask & P32) {
+    DD_TRY(op->clov[1].alloc(nclov * sizeof(float2)));
+    DD_TRY(op->ainv[1].alloc(nainv * sizeof(float2)));
+    k_demote32<<<nblk(nclov, 256), 256, 0, st>>>((const double2*)op->clov[0].ptr, (float2*)op->clov[1].ptr, nclov);
+    k_demote32<<<nblk(nainv, 256), 256, 0, st>>>((const double2*)op->ainv[0].ptr, (float2*)op->ainv[1].ptr, nainv);
+  }
+  if (op->prec_mask & P16) {
+    DD_TRY(op->clov[2].alloc(nclov * sizeof(__half2)));
+    DD_TRY(op->ainv[2].alloc(nainv * sizeof(__half2)));
+    k_demote16<<<nblk(nclov, 256), 256, 0, st>>>((const double2*)op->clov[0].ptr, (__half2*)op->clov[2].ptr, nclov);
+    k_demote16<<<nblk(nainv, 256), 256, 0, st>>>((const double2*)op->ainv[0].ptr, (__half2*)op->ainv[2].ptr, nainv);
+  }
+  DD_CUDA(cudaGetLastError());
+  return DD_OK;
+}
+
+int clover_to_dense(const dd_clover* op, double* A_dev, cudaStream_t st) {
+  k_clover_dense<<<nblk(op->lat->V, 64), 64, 0, st>>>(lex_geom(op->lat), (const double2*)op->clov[0].ptr,
+                                                      reinterpret_cast<double2*>(A_dev));
+  DD_CUDA(cudaGetLastError());
+  return DD_OK;
+}
+
+int pack(const dd_lattice* lat, int prec, int subset, const double* canon, const Field& f, cudaStream_t st) {
+  PackArgs a = pack_args(lat, subset, f);
+  const int64_t n = lat->Vh * f.nrhs * a.npar;
+  const double2* c = reinterpret_cast<const double2*>(canon);
+  if (prec == P64)
+    k_pack<P64><<<nblk(n, 128), 128, 0, st>>>(a, c);
+  else if (prec == P32)
+    k_pack<P32><<<nblk(n, 128), 128, 0, st>>>(a, c);
+  else
+    k_pack<P16><<<nblk(n, 128), 128, 0, st>>>(a, c);
+  DD_CUDA(cudaGetLastError());
+  return DD_OK;
+}
+
+int unpack(const dd_lattice* lat, int prec, int subset, const Field& f, double* canon, cudaStream_t st) {
+  PackArgs a = pack_args(lat, subset, f);
+  const int64_t n = lat->Vh * f.nrhs * a.npar;
+  double2* c = reinterpret_cast<double2*>(canon);
+  if (prec == P64)
+    k_unpack<P64><<<nblk(n, 128), 128, 0, st>>>(a, c);
+  else if (prec == P32)
+    k_unpack<P32><<<nblk(n, 128), 128, 0, st>>>(a, c);
+  else
+    k_unpack<P16><<<nblk(n, 128), 128, 0, st>>>(a, c);
+  DD_CUDA(cudaGetLastError());
+  return DD_OK;
+}
+
+}  // namespace dd

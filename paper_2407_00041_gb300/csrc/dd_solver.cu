@@ -1,0 +1,388 @@
+// FGMRES (Algorithm 2 of the thesis) inside an FP64 iterative-refinement
+// loop, for several right-hand sides at once.
+//
+// Outer loop (FP64): r = b - D x with the full FP64 operator; stop when
+// ||r_k|| < tol ||b_k|| for every right-hand side k.  Otherwise solve
+// D e = r approximately (inner solve) and update x += e in FP64.
+//
+// Inner solve: FGMRES(m) with M_j = I (so z_j = v_j) on the even-odd Schur
+// operator Dhat (odd sites) or on D, in the inner precision.  Each Arnoldi
+// step applies the operator once (Algorithm 2, line 9) and orthogonalises
+// with classical Gram-Schmidt applied twice (an equivalent of the modified
+// Gram-Schmidt of lines 10-13 that reads every basis vector in one pass),
+// inner products accumulated in FP64.  The small least-squares problem of
+// line 18 is solved on the host with complex Givens rotations, whose
+// residual estimate is checked after every step; a cycle also ends when
+// |h_{j+1,j}| falls below tol / 10 of ||f|| (the breakdown rule after
+// Algorithm 1).  Right-hand sides that have converged are masked out (their
+// new basis vectors are scaled by zero).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <vector>
+
+#include "dd_blas.h"
+#include "dd_internal.h"
+
+namespace dd {
+
+namespace {
+
+using cd = std::complex<double>;
+
+struct Pinned {
+  void* p = nullptr;
+  ~Pinned() {
+    if (p) cudaFreeHost(p);
+  }
+  int alloc(size_t n) {
+    if (cudaMallocHost(&p, n) != cudaSuccess) {
+      p = nullptr;
+      (void)cudaGetLastError();
+      return fail(DD_ERR_OOM, "pinned host allocation failed");
+    }
+    return DD_OK;
+  }
+};
+
+struct Inner {
+  const dd_clover* op;
+  int pg, pv;
+  bool eo;
+  int N, m;
+  int64_t L;     // 16-byte groups per vector
+  size_t vbytes;
+  DevBuf basis, w, rvec, tmp, red, partials, coef;
+  Pinned hred, hcoef;
+  // counters
+  int applies = 0, steps = 0, cycles = 0;
+
+  int init(const dd_clover* op_, int pg_, int pv_, bool eo_, int N_, int m_) {
+    op = op_;
+    pg = pg_;
+    pv = pv_;
+    eo = eo_;
+    N = N_;
+    m = m_;
+    const dd_lattice* lat = op->lat;
+    vbytes = field_bytes(lat, pv, eo ? 1 : 0, N);
+    L = (int64_t)(vbytes / 16);
+    DD_TRY(basis.ensure(vbytes * (m + 1)));
+    DD_TRY(w.ensure(vbytes));
+    DD_TRY(rvec.ensure(vbytes));
+    if (eo) DD_TRY(tmp.ensure(field_bytes(lat, pv, 2, N)));
+    const size_t nred = (size_t)(2 * (m + 1) + 1) * N;
+    DD_TRY(red.ensure(nred * sizeof(double2)));
+    DD_TRY(partials.ensure((size_t)blas_partials_len(N) * sizeof(double2)));
+    DD_TRY(coef.ensure((size_t)(m + 1) * N * sizeof(double2)));
+    if (!hred.p) DD_TRY(hred.alloc(nred * sizeof(double2)));
+    if (!hcoef.p) DD_TRY(hcoef.alloc((size_t)(m + 1) * N * sizeof(double2)));
+    return DD_OK;
+  }
+
+  void* V(int j) { return reinterpret_cast<char*>(basis.ptr) + vbytes * j; }
+  Field fv(void* p) { return field_view(op->lat, pv, eo ? 1 : 0, p, N); }
+
+  int apply(void* in, void* out, cudaStream_t st) {
+    ++applies;
+    if (eo) return op_Dhat(op, pg, pv, false, fv(in), fv(out), field_view(op->lat, pv, 2, tmp.ptr, N), st);
+    return op_D(op, pg, pv, false, fv(in), fv(out), st);
+  }
+
+  int dots(const VecList& vs, int J, const void* x, double2* out, int add, cudaStream_t st) {
+    if (pv == P64) return blas_multidot<P64>(vs, J, x, L, N, out, add, (double2*)partials.ptr, st);
+    return blas_multidot<P32>(vs, J, x, L, N, out, add, (double2*)partials.ptr, st);
+  }
+  int axpys(const VecList& vs, int J, const double2* c, double sgn, void* x, cudaStream_t st) {
+    if (pv == P64) return blas_multiaxpy<P64>(vs, J, c, sgn, x, L, N, st);
+    return blas_multiaxpy<P32>(vs, J, c, sgn, x, L, N, st);
+  }
+  int scale(const double2* c, const void* in, void* out, cudaStream_t st) {
+    if (pv == P64) return blas_scale<P64>(c, in, out, L, N, st);
+    return blas_scale<P32>(c, in, out, L, N, st);
+  }
+  int norms(const void* x, std::vector<double>& out, cudaStream_t st) {
+    VecList vs;
+    vs.p[0] = x;
+    double2* d = reinterpret_cast<double2*>(red.ptr);
+    DD_TRY(dots(vs, 1, x, d, 0, st));
+    DD_CUDA(cudaMemcpyAsync(hred.p, d, N * sizeof(double2), cudaMemcpyDeviceToHost, st));
+    DD_CUDA(cudaStreamSynchronize(st));
+    const double2* h = reinterpret_cast<const double2*>(hred.p);
+    out.resize(N);
+    for (int r = 0; r < N; ++r) out[r] = std::sqrt(std::max(h[r].x, 0.0));
+    return DD_OK;
+  }
+
+  // Solve A e = f; e (a vector of this solver's shape) must be zero on entry.
+  // tol_rel[r]: requested reduction of ||f_r - A e_r|| / ||f_r||.
+  int solve(const void* f, void* e, const std::vector<double>& tol_rel, int max_restarts, cudaStream_t st,
+            std::vector<double>* est_out) {
+    std::vector<double> fnorm;
+    DD_TRY(norms(f, fnorm, st));
+    std::vector<cd> H((size_t)N * (m + 1) * m), g((size_t)N * (m + 1)), sn((size_t)N * m);
+    std::vector<double> cs((size_t)N * m), est(N), beta(N);
+    std::vector<int> k(N), live(N);
+    double2* dd = reinterpret_cast<double2*>(red.ptr);
+    double2* dots1 = dd;
+    double2* dots2 = dd + (size_t)(m + 1) * N;
+    double2* nrm = dd + (size_t)2 * (m + 1) * N;
+    const double2* h1 = reinterpret_cast<const double2*>(hred.p);
+    const double2* h2 = h1 + (size_t)(m + 1) * N;
+    const double2* hn = h1 + (size_t)2 * (m + 1) * N;
+    double2* hc = reinterpret_cast<double2*>(hcoef.p);
+    double2* dcoef = reinterpret_cast<double2*>(coef.ptr);
+    bool done = false;
+    for (int cyc = 0; cyc < max_restarts && !done; ++cyc) {
+      ++cycles;
+      // residual of this cycle (Algorithm 2, line 4); x0 = 0 on the first
+      if (cyc == 0) {
+        DD_CUDA(cudaMemcpyAsync(rvec.ptr, f, vbytes, cudaMemcpyDeviceToDevice, st));
+      } else {
+        DD_TRY(apply(e, w.ptr, st));
+        DD_CUDA(cudaMemcpyAsync(rvec.ptr, f, vbytes, cudaMemcpyDeviceToDevice, st));
+        VecList vw;
+        vw.p[0] = w.ptr;
+        for (int r = 0; r < N; ++r) hc[r] = make_double2(1.0, 0.0);
+        DD_CUDA(cudaMemcpyAsync(dcoef, hc, N * sizeof(double2), cudaMemcpyHostToDevice, st));
+        DD_TRY(axpys(vw, 1, dcoef, -1.0, rvec.ptr, st));
+      }
+      DD_TRY(norms(rvec.ptr, beta, st));  // line 5
+      int nlive = 0;
+      for (int r = 0; r < N; ++r) {
+        live[r] = beta[r] > tol_rel[r] * fnorm[r] && fnorm[r] > 0.0;
+        est[r] = fnorm[r] > 0.0 ? beta[r] / fnorm[r] : 0.0;
+        nlive += live[r];
+        k[r] = 0;
+        for (int i = 0; i <= m; ++i) g[(size_t)r * (m + 1) + i] = 0.0;
+        g[(size_t)r * (m + 1)] = beta[r];
+      }
+      if (!nlive) break;
+      for (int r = 0; r < N; ++r) hc[r] = make_double2(live[r] ? 1.0 / beta[r] : 0.0, 0.0);
+      DD_CUDA(cudaMemcpyAsync(dcoef, hc, N * sizeof(double2), cudaMemcpyHostToDevice, st));
+      DD_TRY(scale(dcoef, rvec.ptr, V(0), st));  // line 6
+      int jmax = 0;
+      for (int j = 0; j < m; ++j) {
+        ++steps;
+        DD_TRY(apply(V(j), w.ptr, st));  // line 9 (z_j = v_j)
+        VecList vs;
+        for (int i = 0; i <= j; ++i) vs.p[i] = V(i);
+        // lines 10-13: two passes of classical Gram-Schmidt
+        DD_TRY(dots(vs, j + 1, w.ptr, dots1, 0, st));
+        DD_TRY(axpys(vs, j + 1, dots1, -1.0, w.ptr, st));
+        DD_TRY(dots(vs, j + 1, w.ptr, dots2, 0, st));
+        DD_TRY(axpys(vs, j + 1, dots2, -1.0, w.ptr, st));
+        VecList vw;
+        vw.p[0] = w.ptr;
+        DD_TRY(dots(vw, 1, w.ptr, nrm, 0, st));  // line 14
+        DD_CUDA(cudaMemcpyAsync(hred.p, dd, (size_t)(2 * (m + 1) + 1) * N * sizeof(double2), cudaMemcpyDeviceToHost,
+                                st));
+        DD_CUDA(cudaStreamSynchronize(st));
+        int still = 0;
+        for (int r = 0; r < N; ++r) {
+          hc[r] = make_double2(0.0, 0.0);
+          if (!live[r]) continue;
+          cd* h = &H[((size_t)r * m + j) * (m + 1)];
+          for (int i = 0; i <= j; ++i) {
+            const double2 a = h1[(size_t)i * N + r], b = h2[(size_t)i * N + r];
+            h[i] = cd(a.x + b.x, a.y + b.y);
+          }
+          const double hn1 = std::sqrt(std::max(hn[r].x, 0.0));
+          h[j + 1] = hn1;
+          // apply the previous rotations to the new column
+          for (int i = 0; i < j; ++i) {
+            const double c = cs[(size_t)r * m + i];
+            const cd s = sn[(size_t)r * m + i];
+            const cd t = c * h[i] + s * h[i + 1];
+            h[i + 1] = -std::conj(s) * h[i] + c * h[i + 1];
+            h[i] = t;
+          }
+          // new rotation zeroing h[j+1]
+          const double aa = std::abs(h[j]), bb = std::abs(h[j + 1]);
+          const double rho = std::sqrt(aa * aa + bb * bb);
+          double c;
+          cd s;
+          if (aa == 0.0) {
+            c = 0.0;
+            s = 1.0;
+            h[j] = rho;
+          } else {
+            c = aa / rho;
+            s = (h[j] / aa) * std::conj(h[j + 1]) / rho;
+            h[j] = (h[j] / aa) * rho;
+          }
+          h[j + 1] = 0.0;
+          cs[(size_t)r * m + j] = c;
+          sn[(size_t)r * m + j] = s;
+          cd* gr = &g[(size_t)r * (m + 1)];
+          gr[j + 1] = -std::conj(s) * gr[j];
+          gr[j] = c * gr[j];
+          k[r] = j + 1;
+          est[r] = std::abs(gr[j + 1]) / fnorm[r];
+          const bool conv = std::abs(gr[j + 1]) < tol_rel[r] * fnorm[r];
+          const bool brk = hn1 < 0.1 * tol_rel[r] * fnorm[r];
+          if (conv || brk || rho == 0.0) {
+            live[r] = 0;
+          } else {
+            hc[r] = make_double2(1.0 / hn1, 0.0);
+            ++still;
+          }
+        }
+        jmax = j + 1;
+        if (!still) break;
+        DD_CUDA(cudaMemcpyAsync(dcoef, hc, N * sizeof(double2), cudaMemcpyHostToDevice, st));
+        DD_TRY(scale(dcoef, w.ptr, V(j + 1), st));  // line 15
+      }
+      DD_CUDA(cudaStreamSynchronize(st));  // the last coefficient upload has landed before hc is reused
+      // line 18: back substitution R y = g; line 19: e += V y
+      std::vector<cd> y((size_t)N * m);
+      for (int r = 0; r < N; ++r) {
+        for (int i = k[r] - 1; i >= 0; --i) {
+          cd acc = g[(size_t)r * (m + 1) + i];
+          for (int l = i + 1; l < k[r]; ++l) acc -= H[((size_t)r * m + l) * (m + 1) + i] * y[(size_t)r * m + l];
+          y[(size_t)r * m + i] = acc / H[((size_t)r * m + i) * (m + 1) + i];
+        }
+      }
+      for (int i = 0; i < jmax; ++i)
+        for (int r = 0; r < N; ++r) {
+          const cd v = i < k[r] ? y[(size_t)r * m + i] : cd(0.0);
+          hc[(size_t)i * N + r] = make_double2(v.real(), v.imag());
+        }
+      DD_CUDA(cudaMemcpyAsync(dcoef, hc, (size_t)jmax * N * sizeof(double2), cudaMemcpyHostToDevice, st));
+      VecList vs;
+      for (int i = 0; i < jmax; ++i) vs.p[i] = V(i);
+      DD_TRY(axpys(vs, jmax, dcoef, 1.0, e, st));
+      DD_CUDA(cudaStreamSynchronize(st));  // hc is reused by the next cycle
+      done = true;
+      for (int r = 0; r < N; ++r)
+        if (est[r] >= tol_rel[r] && fnorm[r] > 0.0) done = false;
+    }
+    if (est_out) *est_out = est;
+    return DD_OK;
+  }
+};
+
+int dot_norms64(const dd_lattice* lat, const void* x, int N, double2* scratch_red, double2* partials,
+                Pinned& hbuf, std::vector<double>& out, cudaStream_t st) {
+  VecList vs;
+  vs.p[0] = x;
+  const int64_t L = (int64_t)(field_bytes(lat, P64, 0, N) / 16);
+  DD_TRY(blas_multidot<P64>(vs, 1, x, L, N, scratch_red, 0, partials, st));
+  DD_CUDA(cudaMemcpyAsync(hbuf.p, scratch_red, N * sizeof(double2), cudaMemcpyDeviceToHost, st));
+  DD_CUDA(cudaStreamSynchronize(st));
+  out.resize(N);
+  const double2* h = reinterpret_cast<const double2*>(hbuf.p);
+  for (int r = 0; r < N; ++r) out[r] = std::sqrt(std::max(h[r].x, 0.0));
+  return DD_OK;
+}
+
+}  // namespace
+
+int solve(dd_clover* op, const dd_solve_params* prm, const double* b_canon, double* x_canon, int N, cudaStream_t st,
+          dd_stats* stats) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const dd_lattice* lat = op->lat;
+  const int pin = prm->inner_prec;
+  const int pv = pin == P64 ? P64 : P32;
+  const int pg = pin;
+  if (prec_index(pin) < 0) return fail(DD_ERR_ARG, "bad inner precision");
+  if (!op->clov[prec_index(pg)].ptr || !op->gauge->links[prec_index(pg)].ptr)
+    return fail(DD_ERR_UNSUPPORTED, "inner precision not created in the handles");
+  if (prm->restart < 1 || prm->restart > 32) return fail(DD_ERR_ARG, "restart must be in 1..32");
+  const bool eo = prm->even_odd != 0;
+  const size_t f64 = field_bytes(lat, P64, 0, N);
+  DevBuf b64, x64, r64, r32, fvec, evec, tmp, red, partials;
+  Pinned hbuf;
+  DD_TRY(hbuf.alloc((size_t)N * sizeof(double2)));
+  DD_TRY(b64.alloc(f64));
+  DD_TRY(x64.alloc(f64));
+  DD_TRY(r64.alloc(f64));
+  DD_TRY(red.alloc((size_t)N * sizeof(double2)));
+  DD_TRY(partials.alloc((size_t)blas_partials_len(N) * sizeof(double2)));
+  if (pv == P32) DD_TRY(r32.alloc(field_bytes(lat, P32, 0, N)));
+  DD_TRY(evec.alloc(field_bytes(lat, pv, 0, N)));
+  if (eo) {
+    DD_TRY(fvec.alloc(field_bytes(lat, pv, 1, N)));
+    DD_TRY(tmp.alloc(field_bytes(lat, pv, 2, N)));
+  }
+  Field B = field_view(lat, P64, 0, b64.ptr, N), X = field_view(lat, P64, 0, x64.ptr, N),
+        Rr = field_view(lat, P64, 0, r64.ptr, N);
+  DD_TRY(pack(lat, P64, 0, b_canon, B, st));
+  DD_TRY(pack(lat, P64, 0, x_canon, X, st));
+  std::vector<double> bnorm, rnorm;
+  DD_TRY(dot_norms64(lat, b64.ptr, N, (double2*)red.ptr, (double2*)partials.ptr, hbuf, bnorm, st));
+
+  for (int r = 0; r < N; ++r)
+    if (!std::isfinite(bnorm[r])) return fail(DD_ERR_ARG, "right-hand side contains NaN or Inf");
+  Inner inner;
+  DD_TRY(inner.init(op, pg, pv, eo, N, prm->restart));
+  dd_stats s{};
+  int status = DD_ERR_NOT_CONVERGED;
+  for (int outer = 0;; ++outer) {
+    DD_TRY(op_residual(op, P64, P64, B, X, Rr, st));  // r = b - D x in FP64
+    ++s.applies_fp64;
+    DD_TRY(dot_norms64(lat, r64.ptr, N, (double2*)red.ptr, (double2*)partials.ptr, hbuf, rnorm, st));
+    double worst = 0.0;
+    bool all = true;
+    for (int r = 0; r < N; ++r) {
+      const double rel = bnorm[r] > 0 ? rnorm[r] / bnorm[r] : 0.0;
+      worst = std::max(worst, rel);
+      if (!(rel < prm->tol) && bnorm[r] > 0) all = false;
+    }
+    s.true_residual = worst;
+    s.outer_iterations = outer;
+    if (prm->verbose)
+      fprintf(stderr, "[dd_solve] outer %d  max ||b-Dx||/||b|| = %.3e  inner steps so far %d\n", outer, worst,
+              inner.steps);
+    if (all) {
+      status = DD_OK;
+      break;
+    }
+    if (outer >= prm->max_outer) break;
+    // inner right-hand side in the inner precision
+    const void* rin = r64.ptr;
+    if (pv == P32) {
+      DD_TRY(blas_demote(r64.ptr, r32.ptr, 2, lat->Vh * N, st));
+      rin = r32.ptr;
+    }
+    Field Rin = field_view(lat, pv, 0, const_cast<void*>(rin), N);
+    Field E = field_view(lat, pv, 0, evec.ptr, N);
+    DD_CUDA(cudaMemsetAsync(evec.ptr, 0, field_bytes(lat, pv, 0, N), st));
+    const void* f = rin;
+    void* e = evec.ptr;
+    if (eo) {
+      DD_TRY(op_prepare(op, pg, pv, Rin, field_view(lat, pv, 1, fvec.ptr, N), field_view(lat, pv, 2, tmp.ptr, N),
+                        st));
+      f = fvec.ptr;
+      e = E.h[1].base;
+    }
+    std::vector<double> fn;
+    DD_TRY(inner.norms(f, fn, st));
+    std::vector<double> tol_rel(N);
+    for (int r = 0; r < N; ++r) {
+      const double need = fn[r] > 0 ? 0.3 * prm->tol * bnorm[r] / fn[r] : 1.0;
+      tol_rel[r] = std::max(prm->inner_tol, need);
+      if (pv == P64) tol_rel[r] = need;  // FP64 inner: one inner solve reaches the target
+    }
+    DD_TRY(inner.solve(f, e, tol_rel, prm->max_restarts, st, nullptr));
+    if (eo) DD_TRY(op_reconstruct(op, pg, pv, Rin, E, st));
+    if (pv == P32)
+      DD_TRY(blas_promote_add(evec.ptr, x64.ptr, 2, lat->Vh * N, st));
+    else
+      DD_TRY(blas_add64(evec.ptr, x64.ptr, (int64_t)(f64 / 16), st));
+  }
+  DD_TRY(unpack(lat, P64, 0, X, x_canon, st));
+  DD_CUDA(cudaStreamSynchronize(st));
+  s.converged = status == DD_OK;
+  s.inner_iterations = inner.steps;
+  s.restarts = inner.cycles;
+  s.applies_inner = inner.applies;
+  s.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (stats) *stats = s;
+  if (status != DD_OK) set_error("solver reached its iteration limits");
+  return status;
+}
+
+}  // namespace dd

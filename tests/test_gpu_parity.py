@@ -1,0 +1,160 @@
+"""GPU parity: the CUDA path against the CPU oracle, element by element.
+
+Tolerances (relative L2): FP64 1e-13, FP32 1e-6, FP16 storage 5e-3.
+Lattice shapes cover several 128-thread tiles with a ragged tail
+(e.g. 6x4x2x8: 192 sites per parity), non-cubic shapes and extent 2.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synthetic
+import paper_2407_00041_gb300 as dd
+from tests._gpu import CSW, M0, TOL, apply, make, rel
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(4, 4, 4, 4), (6, 4, 2, 8), (2, 2, 2, 2), (8, 6, 4, 2), (4, 8, 8, 8)]
+PRECS = [dd.DD_PREC_F64, dd.DD_PREC_F32, dd.DD_PREC_F16]
+
+
+def g5(psi):
+    p = psi.reshape(psi.shape[0], -1, 4, 3).copy()
+    p[:, :, 2:] *= -1
+    return p
+
+
+@pytest.fixture(scope="module", params=SHAPES, ids=lambda d: "x".join(map(str, d)))
+def system(request):
+    dims = request.param
+    U, lat, g, op = make(dims)
+    A = oracle.clover(U, dims, M0, CSW)
+    return dims, U, A, op, (lat, g)
+
+
+def test_clover_matches_oracle(system):
+    dims, U, A, op, _ = system
+    assert rel(op.clover_dense(), A) < 1e-13
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("nrhs", [1, 3])
+def test_D_and_DH(system, prec, nrhs):
+    dims, U, A, op, _ = system
+    psi = synthetic.spinor(dims, nrhs=nrhs)
+    got = apply(op, dd.DD_OP_D, prec, psi)
+    gotH = apply(op, dd.DD_OP_DH, prec, psi)
+    for r in range(nrhs):
+        ref = oracle.apply_D(U, A, psi[r].reshape(-1, 12), dims)
+        assert rel(got[r], ref) < TOL[prec]
+        refH = oracle.apply_DH(U, A, psi[r].reshape(-1, 12), dims)
+        assert rel(gotH[r], refH) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_self_coupling(system, prec):
+    dims, U, A, op, _ = system
+    psi = synthetic.spinor(dims, nrhs=2)
+    got = apply(op, dd.DD_OP_SC, prec, psi)
+    for r in range(2):
+        ref = np.einsum("xij,xj->xi", A, psi[r].reshape(-1, 12))
+        assert rel(got[r], ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_Dhat(system, prec):
+    dims, U, A, op, _ = system
+    eo = oracle.EvenOdd(U, A, dims)
+    nrhs = 2
+    full = synthetic.spinor(dims, nrhs=nrhs)
+    v = np.stack([full[r].reshape(-1, 12)[eo.odd] for r in range(nrhs)])
+    got = apply(op, dd.DD_OP_DHAT, prec, v)
+    gotH = apply(op, dd.DD_OP_DHAT_H, prec, v)
+    for r in range(nrhs):
+        assert rel(got[r], eo.Dhat(v[r])) < TOL[prec]
+        assert rel(gotH[r], eo.DhatH(v[r])) < TOL[prec]
+
+
+def test_host_layout_roundtrip(system):
+    dims, U, A, op, _ = system
+    psi = synthetic.spinor(dims, nrhs=2)
+    got = apply(op, dd.DD_OP_D, dd.DD_PREC_F64, psi, layout=dd.DD_LAYOUT_CANONICAL_HOST)
+    for r in range(2):
+        assert rel(got[r], oracle.apply_D(U, A, psi[r].reshape(-1, 12), dims)) < 1e-13
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_pack_unpack_roundtrip(system, prec):
+    dims, U, A, op, _ = system
+    nrhs = 3
+    psi = torch.from_numpy(synthetic.spinor(dims, nrhs=nrhs)).cuda()
+    for subset, nsites in ((0, psi.shape[1]), (1, psi.shape[1] // 2)):
+        x = psi[:, :nsites].contiguous()
+        nat = torch.empty(op.field_bytes(prec, subset, nrhs), dtype=torch.uint8, device="cuda")
+        back = torch.empty_like(x)
+        op.pack(prec, subset, x, nat, nrhs)
+        op.unpack(prec, subset, nat, back, nrhs)
+        torch.cuda.synchronize()
+        tol = {1: 0.0, 2: 1e-7, 4: 1e-3}[prec]
+        assert rel(back.cpu().numpy(), x.cpu().numpy()) <= tol
+
+
+def test_native_layout_matches_canonical(system):
+    """The native-layout entry point (what the bench times) gives the same result."""
+    dims, U, A, op, _ = system
+    nrhs = 2
+    psi = torch.from_numpy(synthetic.spinor(dims, nrhs=nrhs)).cuda()
+    for prec in PRECS:
+        nat_in = torch.empty(op.field_bytes(prec, 0, nrhs), dtype=torch.uint8, device="cuda")
+        nat_out = torch.empty_like(nat_in)
+        op.pack(prec, 0, psi, nat_in, nrhs)
+        op.apply(dd.DD_OP_D, prec, nat_in, nat_out, nrhs, dd.DD_LAYOUT_NATIVE)
+        out = torch.empty_like(psi)
+        op.unpack(prec, 0, nat_out, out, nrhs)
+        torch.cuda.synchronize()
+        ref = apply(op, dd.DD_OP_D, prec, psi.cpu().numpy())
+        assert rel(out.cpu().numpy(), ref) == 0.0
+
+
+def test_periodic_time_boundary():
+    dims = (4, 2, 4, 2)
+    U, lat, g, op = make(dims, t_bc=+1)
+    A = oracle.clover(U, dims, M0, CSW)
+    psi = synthetic.spinor(dims)
+    got = apply(op, dd.DD_OP_D, dd.DD_PREC_F64, psi)
+    assert rel(got[0], oracle.apply_D(U, A, psi[0].reshape(-1, 12), dims, t_bc=+1)) < 1e-13
+
+
+def test_gamma5_hermiticity_on_gpu(system):
+    dims, U, A, op, _ = system
+    psi = synthetic.spinor(dims, seed=31)
+    phi = synthetic.spinor(dims, seed=32)
+    Dpsi = apply(op, dd.DD_OP_D, dd.DD_PREC_F64, psi)
+    DHphi = apply(op, dd.DD_OP_DH, dd.DD_PREC_F64, phi)
+    lhs = np.vdot(phi, Dpsi)
+    assert abs(lhs - np.vdot(DHphi, psi)) / abs(lhs) < 1e-13
+    assert rel(DHphi, g5(apply(op, dd.DD_OP_D, dd.DD_PREC_F64, g5(phi)))) < 1e-13
+
+
+def test_free_field_plane_wave_on_gpu():
+    dims = (8, 4, 4, 4)
+    V = int(np.prod(dims))
+    U = np.broadcast_to(np.eye(3, dtype=np.complex128), (V, 4, 3, 3)).copy()
+    _, lat, g, op = make(dims, U=U)
+    coords = np.array(np.unravel_index(np.arange(V), dims)).T
+    p = np.array([np.pi * 3 / dims[0], 2 * np.pi / dims[1], 4 * np.pi / dims[2], 0.0])
+    u = synthetic.gaussian(12, seed=5)
+    phase = np.exp(1j * coords @ p)
+    psi = (phase[:, None] * u[None, :])[None]
+    gam = [oracle.gamma(mu) for mu in range(4)]
+    Dp = (M0 + np.sum(1 - np.cos(p))) * np.eye(4) + sum(1j * np.sin(p[m]) * gam[m] for m in range(4))
+    expect = phase[:, None] * (np.kron(Dp, np.eye(3)) @ u)[None, :]
+    assert rel(apply(op, dd.DD_OP_D, dd.DD_PREC_F64, psi)[0], expect) < 1e-13
+
+
+def test_zero_input_gives_zero_fp16():
+    dims = (4, 4, 2, 2)
+    U, lat, g, op = make(dims)
+    psi = np.zeros((1, int(np.prod(dims)), 4, 3), dtype=np.complex128)
+    assert np.all(apply(op, dd.DD_OP_D, dd.DD_PREC_F16, psi) == 0)

@@ -1,0 +1,94 @@
+"""GPU solver: FGMRES (Algorithm 2) inside FP64 iterative refinement.
+
+Parity for an iteration is on results: the FP64 true residual of the GPU
+solution, recomputed by the CPU oracle, must be below the tolerance, and the
+solution must match the oracle's own FGMRES solution.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synthetic
+import paper_2407_00041_gb300 as dd
+from tests._gpu import CSW, M0, make, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sys44():
+    dims = (4, 4, 4, 4)
+    U, lat, g, op = make(dims)
+    A = oracle.clover(U, dims, M0, CSW)
+    b = synthetic.spinor(dims, nrhs=3)
+    xs = []
+    for r in range(3):
+        x, st = oracle.fgmres(lambda v: oracle.apply_D(U, A, v.reshape(-1, 12), dims).reshape(-1),
+                              b[r].reshape(-1), m=30, tol=1e-12, max_restarts=400)
+        assert st.converged
+        xs.append(x.reshape(b[r].shape))
+    return dims, U, A, op, b, np.stack(xs), (lat, g)
+
+
+def oracle_residual(U, A, dims, b, x):
+    r = b.reshape(-1, 12) - oracle.apply_D(U, A, x.reshape(-1, 12), dims)
+    return np.linalg.norm(r) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("inner", [dd.DD_PREC_F64, dd.DD_PREC_F32, dd.DD_PREC_F16])
+@pytest.mark.parametrize("even_odd", [1, 0])
+def test_solve_to_1e10(sys44, inner, even_odd):
+    dims, U, A, op, b, xref, _ = sys44
+    bt = torch.from_numpy(b[:1]).cuda()
+    x = torch.zeros_like(bt)
+    status, st = op.solve(bt, x, 1, tol=1e-10, inner_prec=inner, even_odd=even_odd, restart=30)
+    assert status == 0, st
+    assert st["converged"] == 1 and st["true_residual"] < 1e-10
+    xn = x.cpu().numpy()[0]
+    assert oracle_residual(U, A, dims, b[0], xn) < 1e-10
+    assert rel(xn, xref[0]) < 1e-8
+    if inner != dd.DD_PREC_F64:
+        assert st["outer_iterations"] >= 2  # refinement did the last digits
+
+
+def test_multi_rhs_solve(sys44):
+    dims, U, A, op, b, xref, _ = sys44
+    bt = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bt)
+    status, st = op.solve(bt, x, 3, tol=1e-10, inner_prec=dd.DD_PREC_F32, restart=16)
+    assert status == 0, st
+    xn = x.cpu().numpy()
+    for r in range(3):
+        assert oracle_residual(U, A, dims, b[r], xn[r]) < 1e-10
+        assert rel(xn[r], xref[r]) < 1e-8
+
+
+def test_host_layout_and_initial_guess(sys44):
+    dims, U, A, op, b, xref, _ = sys44
+    b0 = np.ascontiguousarray(b[:1])
+    x = np.ascontiguousarray(xref[:1] * (1 + 1e-6))  # good initial guess
+    status, st = op.solve(b0, x, 1, layout=dd.DD_LAYOUT_CANONICAL_HOST, tol=1e-10)
+    assert status == 0 and oracle_residual(U, A, dims, b0[0], x[0]) < 1e-10
+    assert st["outer_iterations"] <= 2
+
+
+def test_not_converged_reports_best_iterate(sys44):
+    dims, U, A, op, b, xref, _ = sys44
+    bt = torch.from_numpy(b[:1]).cuda()
+    x = torch.zeros_like(bt)
+    status, st = op.solve(bt, x, 1, tol=1e-10, max_outer=1, inner_tol=1e-3, max_restarts=1, restart=4)
+    assert status == dd.DD_ERR_NOT_CONVERGED
+    assert st["converged"] == 0 and 1e-10 < st["true_residual"] < 1.0
+    assert oracle_residual(U, A, dims, b[0], x.cpu().numpy()[0]) == pytest.approx(st["true_residual"], rel=1e-6)
+
+
+def test_nan_rhs_is_rejected(sys44):
+    dims, U, A, op, b, xref, _ = sys44
+    bb = b[:1].copy()
+    bb[0, 3, 1, 2] = np.nan
+    bt = torch.from_numpy(bb).cuda()
+    x = torch.zeros_like(bt)
+    with pytest.raises(dd.DDError) as e:
+        op.solve(bt, x, 1)
+    assert e.value.status == dd.DD_ERR_ARG
