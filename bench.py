@@ -1,0 +1,498 @@
+"""Benchmark of the Wilson-clover hot path on GB300.
+
+Workload: the 48^3 x 96 lattice (nT = 96, nZ = nY = nX = 48; 10,616,832
+sites), synthetic SU(3) links exp(i 0.3 H), m0 = -0.4, c_sw = 1.0,
+antiperiodic time, one Gaussian right-hand side.
+
+Headline metric: algorithmic HBM GB/s of one D psi application (Eq. 1.13)
+in the chosen precision (default FP32), inputs resident in HBM, native
+layout.  One step = one full-lattice D psi.  The working set (links,
+self coupling, spinors: > 8 GB) is far larger than the 129 MB L2, so no
+flush is needed between steps.
+
+Algorithmic bytes per site for N right-hand sides (every link, clover
+block and spinor read once, the result written once):
+  FP64 1152 + 384 N,  FP32 576 + 192 N,  FP16 storage 288 + 104 N.
+
+The JSON line also carries:
+  variants    GB/s of the FP64, FP32 and FP16-storage applies, each with its
+              binding roof (FP64 is bound by the FP64 pipeline on this GPU);
+  e2e         the same apply through the C ABI on host buffers, copies
+              included;
+  solve       time to ||b - D x|| < 1e-10 ||b|| of the mixed-precision
+              even-odd FGMRES with FP64 refinement against the plain FP64 GPU
+              solve;
+  roofline    the headline kernel against the measured HBM copy bandwidth;
+  cpu_baseline the CPU oracle on a bounded sample of the same workload.
+
+--impl reference times the CPU oracle instead (each step: D psi on a
+bounded sample of sites of the same lattice).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DIMS = (96, 48, 48, 48)  # nT, nZ, nY, nX
+M0, CSW, EPS = -0.4, 1.0, 0.3
+WORKLOAD = "48^3x96 Wilson-clover D.psi, 1 RHS, eps=0.3 SU(3) links, m0=-0.4, c_sw=1.0, antiperiodic T"
+BYTES = {"f64": (1152, 384), "f32": (576, 192), "f16": (288, 104)}
+PREC = {"f64": 1, "f32": 2, "f16": 4}
+FLOPS_PER_SITE = 1848  # nominal: hopping 1320 + self coupling 504 + combine 24
+
+
+_T0 = time.time()
+
+
+def log(msg):
+    print(f"[bench {time.time() - _T0:7.1f}s] {msg}", file=sys.stderr, flush=True)
+
+
+def bytes_per_site(prec, nrhs=1):
+    a, b = BYTES[prec]
+    return a + b * nrhs
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    """nvidia-smi sampler running during the measurement."""
+
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id=None):
+        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50"]
+        if gpu_id:
+            cmd.insert(1, f"--id={gpu_id}")
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        self.windows = []
+
+    def window(self, t0, t1):
+        self.windows.append((t0, t1))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(5)
+            except Exception:
+                self.proc.kill()
+        self.tmp.flush()
+        self.tmp.seek(0)
+        rows = []
+        for line in self.tmp.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                ts += float("0." + parts[0].split(".")[1]) if "." in parts[0] else 0.0
+                rows.append((ts, float(parts[1]), float(parts[2]), parts[3], parts[4:]))
+            except Exception:
+                continue
+        os.unlink(self.tmp.name)
+        return rows
+
+    def summary(self, rows):
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        inwin = [r for r in rows if any(a - 0.05 <= r[0] <= b + 0.05 for a, b in self.windows)]
+        use = inwin if inwin else rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in use:
+            for n, v in zip(names, r[4][1:]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(r[1] for r in use), "sm_max_mhz": max(r[2] for r in use),
+                "reasons": sorted(reasons), "samples": len(use), "samples_in_timed_windows": len(inwin)}
+
+
+# ---------------------------------------------------------------- distributed
+def dist_env():
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    return rank, world, local
+
+
+def init_dist(world, local):
+    """One process per GPU (torchrun); NCCL on GPUs, gloo otherwise.  The
+    path shards as independent replicas, so the process group only carries
+    the barrier and the max-over-ranks reduction of the timings."""
+    import torch
+    if world <= 1:
+        return None
+    import torch.distributed as tdist
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    tdist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return tdist
+
+
+def _sync():
+    import torch
+    if torch.cuda.is_available():
+        torch.cuda.synchronize()
+
+
+def barrier(tdist):
+    if tdist is not None:
+        tdist.barrier()
+    _sync()
+
+
+def max_over_ranks(tdist, x):
+    import torch
+    if tdist is None:
+        return x
+    dev = "cuda" if (torch.cuda.is_available() and tdist.get_backend() == "nccl") else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_gbs(bytes_per_unit, units_per_rank, world, seconds_max):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return bytes_per_unit * units_per_rank * world / seconds_max / 1e9
+
+
+# ---------------------------------------------------------------- timing
+def time_steps(fn, steps, warmup, stream, tdist, clocks):
+    """W untimed steps, then exactly K timed steps bracketed by barrier + sync.
+    Returns (total seconds max over ranks, per-step seconds list)."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    barrier(tdist)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    w0 = time.time()
+    t_start.record(stream)
+    for i in range(steps):
+        ev[i][0].record(stream)
+        fn()
+        ev[i][1].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    w1 = time.time()
+    barrier(tdist)
+    if clocks is not None:
+        clocks.window(w0, w1)
+    total = t_start.elapsed_time(t_end) * 1e-3
+    per = [a.elapsed_time(b) * 1e-3 for a, b in ev]
+    return max_over_ranks(tdist, total), per
+
+
+# ---------------------------------------------------------------- profiles
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2407_00041_gb300", "csrc", "dd_hop*")) +
+                    [os.path.join(ROOT, "paper_2407_00041_gb300", "csrc", "dd_device.cuh"),
+                     os.path.join(ROOT, "paper_2407_00041_gb300", "csrc", "dd_ops.h")]):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic(prec):
+    """DRAM bytes per launch of the stencil from the committed ncu summary, if
+    it was taken with the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", f"dslash_{prec}_48x48x48x96.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    h = re.search(r"kernel_sources_sha256_16:\s*([0-9a-f]+)", txt)
+    if not m or not h or h.group(1) != kernel_source_hash():
+        return None
+    return float(m.group(1))
+
+
+# ---------------------------------------------------------------- CPU oracle
+def fill_sample(U, psi, dims, tslices):
+    """Fill links and spinor of the listed time slices (lazily mapped arrays)."""
+    import synthetic
+    nT, nZ, nY, nX = dims
+    per = nZ * nY * nX
+    for t in tslices:
+        sites = np.arange(t * per, (t + 1) * per, dtype=np.int64)
+        U[t * per:(t + 1) * per] = synthetic.gauge_sites(sites, eps=EPS)
+        psi[t * per:(t + 1) * per] = synthetic.spinor_sites(dims, sites)
+
+
+def oracle_sample_rate(U, psi, dims, slices, reps):
+    """Time the oracle's D psi on the sites of time slices [0, slices); the
+    self coupling of the sample is built first (setup, timed separately)."""
+    import oracle
+    per = dims[1] * dims[2] * dims[3]
+    sites = np.arange(slices * per, dtype=np.int64)
+    t0 = time.perf_counter()
+    A = oracle.clover_sites(U, dims, M0, CSW, sites)
+    t_setup = time.perf_counter() - t0
+    out = None
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        out = oracle.apply_D_sites(U, A, psi, dims, sites)
+    dt = (time.perf_counter() - t0) / reps
+    return sites, out, dt, t_setup
+
+
+def cpu_baseline(U, psi, dims, budget_s=20.0, reps=3):
+    """The oracle on a bounded sample: a number of whole time slices chosen
+    from a one-slice trial so that setup plus `reps` applies take about
+    `budget_s` seconds."""
+    import oracle
+    _, _, t1, s1 = oracle_sample_rate(U, psi, dims, 1, 1)
+    slices = int(max(1, min(dims[0] - 2, (budget_s - s1 - t1) / max(s1 + reps * t1, 1e-6))))
+    sites, out, dt, ts = oracle_sample_rate(U, psi, dims, slices, reps)
+    gbs = bytes_per_site("f64") * sites.size / dt / 1e9
+    return {"value": gbs, "unit": "GB/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"FP64 CPU oracle D psi (Eq. 1.13) on the {sites.size} sites of time slices 0..{slices - 1} "
+                      f"of the 48^3x96 lattice, {reps} repetitions, {dt:.3f} s per apply (self-coupling setup "
+                      f"{ts:.1f} s not timed); GB/s counts the FP64 algorithmic 1536 B/site"}, (sites, out)
+
+
+def run_reference(args):
+    """The CPU oracle as the reference arm: each step = D psi on a bounded
+    sample of sites of the same 48^3 x 96 workload."""
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    import synthetic
+    synthetic.build()
+    oracle.build()
+    dims = DIMS
+    V = int(np.prod(dims))
+    U = np.empty((V, 4, 3, 3), dtype=np.complex128)  # only the sample's slices are touched
+    psi = np.empty((V, 4, 3), dtype=np.complex128)
+    slices = 4
+    fill_sample(U, psi, dims, [dims[0] - 1] + list(range(slices + 1)))
+    per = dims[1] * dims[2] * dims[3]
+    sites = np.arange(slices * per, dtype=np.int64)
+    A = oracle.clover_sites(U, dims, M0, CSW, sites)
+    for _ in range(args.warmup):
+        oracle.apply_D_sites(U, A, psi, dims, sites)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.apply_D_sites(U, A, psi, dims, sites)
+    total = time.perf_counter() - t0
+    gbs = bytes_per_site("f64") * sites.size * args.steps / total / 1e9
+    sample = (f"each step: FP64 CPU oracle D psi on the {sites.size} sites of time slices 0..{slices - 1} of the "
+              f"48^3x96 lattice; GB/s counts the FP64 algorithmic 1536 B/site")
+    line = {"impl": "reference", "metric": "D.psi HBM GB/s at 48^3x96 (CPU oracle)", "value": gbs, "unit": "GB/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_sites": int(sites.size)},
+            "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": oracle.threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="f32", choices=["f64", "f32", "f16"], help="headline precision")
+    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--solve-inner", default="f32", choices=["f32", "f16"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import synthetic
+    import paper_2407_00041_gb300 as dd
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    tdist = init_dist(world, local)
+    stream = torch.cuda.current_stream()
+    peaks, peak_kind = measured_peaks()
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+        gpu_id = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        gpu_id = None
+    clocks = Clocks(gpu_id)
+
+    dims = DIMS
+    V = int(np.prod(dims))
+    log("generating links and spinor")
+    U = synthetic.gauge(dims, eps=EPS)
+    psi = synthetic.spinor(dims, nrhs=1)
+    log("building gauge and operator handles")
+    lat = dd.Lattice(dims, -1)
+    gauge = dd.Gauge(lat, U)
+    op = dd.Operator(gauge, M0, CSW)
+    log("handles ready")
+    psi_dev = torch.from_numpy(psi).to("cuda")
+
+    gpu_launches = 0
+    variants = {}
+    f64_peak = f32_peak = None
+    fl = np.zeros(1, dtype=np.float64)
+    dd.check(dd.lib.dd_probe_flops(dd.DD_PREC_F64, fl.ctypes.data, stream.cuda_stream), "probe")
+    f64_peak = float(fl[0])
+    dd.check(dd.lib.dd_probe_flops(dd.DD_PREC_F32, fl.ctypes.data, stream.cuda_stream), "probe")
+    f32_peak = float(fl[0])
+
+    order = ["f64", "f32", "f16"]
+    head = None
+    for prec in order:
+        p = PREC[prec]
+        nbytes = op.field_bytes(p, 0, 1)
+        xin = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        xout = torch.empty_like(xin)
+        op.pack(p, 0, psi_dev, xin, 1)
+
+        def step():
+            dd.check(dd.lib.dd_apply(op.h, dd.DD_OP_D, p, xin.data_ptr(), xout.data_ptr(), 1,
+                                     dd.DD_LAYOUT_NATIVE, stream.cuda_stream), "dd_apply")
+
+        log(f"timing D psi in {prec}")
+        steps = args.steps if prec == args.prec else max(10, min(args.steps, 50))
+        total, per = time_steps(step, steps, args.warmup, stream, tdist, clocks if prec == args.prec else None)
+        if prec == args.prec:
+            gpu_launches += steps
+        ms = total / steps * 1e3
+        gbs = aggregate_gbs(bytes_per_site(prec), V, world, total / steps)
+        kern = statistics.mean(per)
+        achieved = bytes_per_site(prec) * V / kern / 1e9
+        gflops = FLOPS_PER_SITE * V / kern / 1e9
+        bound = "hbm"
+        peak, unit, frac = peaks["hbm_gbs"], "GB/s", achieved / peaks["hbm_gbs"]
+        alu_peak = f64_peak if prec == "f64" else f32_peak
+        if gflops * 1e9 / alu_peak > frac:  # the arithmetic pipe is the closer roof
+            bound, peak, unit, frac = "alu", alu_peak / 1e12, "TFLOP/s", gflops * 1e9 / alu_peak
+            achieved = gflops / 1e3
+        variants[prec] = {"gbs": gbs, "ms_per_apply": ms, "hbm_frac": bytes_per_site(prec) * V / kern / 1e9 /
+                          peaks["hbm_gbs"], "gflops_nominal": gflops, "bound": bound,
+                          "roof_frac": frac, "bytes_per_site": bytes_per_site(prec)}
+        if prec == args.prec:
+            traffic = profile_traffic(prec)
+            head = {"value": gbs, "ms": ms, "kernel_s": kern,
+                    "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": frac,
+                                 "traffic": traffic,
+                                 "peak_source": f"{peak_kind} MEASURED_PEAKS.json hbm_gbs" if bound == "hbm"
+                                 else "FMA-chain probe dd_probe_flops on this GPU"}}
+            # parity of the timed launch configuration on a sample of sites
+            out_c = torch.empty_like(psi_dev)
+            op.unpack(p, 0, xout, out_c, 1)
+            head["_out"] = out_c
+        del xin, xout
+
+    # e2e through the C ABI on pinned host buffers
+    p = PREC[args.prec]
+    hin = torch.from_numpy(psi).pin_memory()
+    hout = torch.empty_like(hin).pin_memory()
+
+    def e2e_step():
+        dd.check(dd.lib.dd_apply(op.h, dd.DD_OP_D, p, hin.data_ptr(), hout.data_ptr(), 1,
+                                 dd.DD_LAYOUT_CANONICAL_HOST, stream.cuda_stream), "dd_apply host")
+
+    log("timing the host-buffer path")
+    e2e_steps = max(3, min(args.steps, 20))
+    e_total, _ = time_steps(e2e_step, e2e_steps, 1, stream, tdist, None)
+    e2e = {"value": bytes_per_site(args.prec) * V * world / (e_total / e2e_steps) / 1e9, "unit": "GB/s",
+           "h2d_bytes_per_step": V * 12 * 16, "d2h_bytes_per_step": V * 12 * 16,
+           "ms_per_step": e_total / e2e_steps * 1e3}
+
+    # solves: mixed-precision vs plain FP64, time to ||b - D x|| < 1e-10 ||b||
+    solve = None
+    if not args.no_solve:
+        solve = {}
+        b = psi_dev
+        sols = {}
+        for name, inner, restart in (("mixed", PREC[args.solve_inner], 30), ("fp64", PREC["f64"], 30)):
+            x = torch.zeros_like(b)
+            log(f"solve {name}")
+            barrier(tdist)
+            w0 = time.time()
+            status, st = op.solve(b, x, 1, tol=1e-10, inner_prec=inner, restart=restart, max_restarts=400,
+                                  max_outer=20)
+            w1 = time.time()
+            clocks.window(w0, w1)
+            sols[name] = x
+            log(f"solve {name}: {st}")
+            solve[name] = {"seconds": max_over_ranks(tdist, st["seconds"]), "status": status,
+                           "true_residual": st["true_residual"], "outer": st["outer_iterations"],
+                           "inner_steps": st["inner_iterations"], "applies_inner": st["applies_inner"],
+                           "applies_fp64": st["applies_fp64"],
+                           "inner_prec": {1: "f64", 2: "f32", 4: "f16"}[inner]}
+        d = (sols["mixed"] - sols["fp64"]).norm().item() / sols["fp64"].norm().item()
+        solve["mixed_vs_fp64_solution_rel_diff"] = d
+        solve["speedup_mixed_over_fp64"] = solve["fp64"]["seconds"] / solve["mixed"]["seconds"]
+
+    rows = clocks.stop()
+    clk = clocks.summary(rows)
+
+    cpu = None
+    parity = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        log("CPU oracle baseline")
+        cpu, (sites, ref) = cpu_baseline(U, psi[0], dims)
+        log("CPU oracle baseline done")
+        got = head["_out"][0].reshape(V, 12)[torch.from_numpy(sites).cuda()].cpu().numpy()
+        tol = {"f64": 1e-13, "f32": 1e-6, "f16": 5e-3}[args.prec]
+        err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        parity = {"sample_sites": int(sites.size), "rel_l2_vs_oracle": err, "tol": tol, "ok": err < tol}
+
+    head.pop("_out", None)
+    if tdist is not None:
+        tdist.destroy_process_group()
+    if rank != 0:
+        return 0
+    line = {
+        "metric": "D.psi HBM GB/s (algorithmic) at 48^3x96; mixed vs FP64 FGMRES time-to-1e-10",
+        "value": head["value"], "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"f64": "f64", "f32": "f32", "f16": "f32 (fp16 storage)"}[args.prec], "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": args.prec, "nrhs": 1, "sites": V,
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "inputs (>8 GB) larger than L2; no flush"},
+        "roofline": head["roofline"], "variants": variants, "e2e": e2e, "solve": solve,
+        "cpu_baseline": cpu, "parity_sample": parity, "gpu_launches": gpu_launches, "clocks": clk,
+        "probe_tflops": {"f64": f64_peak / 1e12, "f32": f32_peak / 1e12},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -179,8 +179,14 @@ typedef struct {
   int inner_prec;      /* DD_PREC_F64, DD_PREC_F32 or DD_PREC_F16 (FP16 links/clover, FP32 vectors) */
   double inner_tol;    /* relative residual reduction asked of each inner solve, e.g. 1e-6 */
   int even_odd;        /* 1: inner solves use Dhat on odd sites; 0: D on the full lattice */
-  int verbose;         /* 1: print one line per refinement step to stderr */
+  int verbose;         /* 1: print progress lines to stderr */
+  int precond;         /* right preconditioner M^{-1} of Algorithm 2: DD_PRECOND_NONE (M = I)
+                          or DD_PRECOND_NORMAL (M^{-1} = A^H, so A M^{-1} = A A^H is Hermitian
+                          positive definite and restarted FGMRES cannot stagnate) */
 } dd_solve_params;
+
+#define DD_PRECOND_NONE 0
+#define DD_PRECOND_NORMAL 1
 
 typedef struct {
   int converged;             /* 1 if every right-hand side met tol */
@@ -194,7 +200,7 @@ typedef struct {
 } dd_stats;
 
 /* Fill `p` with defaults: tol 1e-10, restart 30, max_restarts 100,
- * max_outer 30, inner_prec F32, inner_tol 1e-6, even_odd 1. */
+ * max_outer 30, inner_prec F32, inner_tol 1e-6, even_odd 1, precond NONE. */
 void dd_solve_params_default(dd_solve_params* p);
 
 /*
@@ -243,6 +249,14 @@ int dd_apply_batched_graph(dd_batch* b, const void* const* ins, void* const* out
  * dots[r] = <a_r, b_r> = sum a_r^H b_r over `nsites` sites, for r < nrhs;
  * written to host memory after synchronising the stream. */
 int dd_dot(const double* a, const double* b, int64_t nsites, int nrhs, double* dots_host /*[nrhs][2]*/, void* stream);
+
+/* ---- arithmetic peak probe ----
+ * The method of Section 3.1 / Table 3.1 of the thesis: many threads each run
+ * long register-only chains of floating-point operations (here eight
+ * independent fused multiply-add chains).  Writes the measured rate in FLOP/s
+ * (an FMA counts as 2) for DD_PREC_F64 or DD_PREC_F32 on the current device.
+ * Synchronises `stream`. */
+int dd_probe_flops(int prec, double* flops_per_second, void* stream);
 
 #ifdef __cplusplus
 }

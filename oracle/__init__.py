@@ -58,6 +58,8 @@ def _load():
             "oracle_Q": [P, P, L, I, I, P],
             "oracle_clover_site": [P, P, D, D, L, P],
             "oracle_clover_field": [P, P, D, D, P],
+            "oracle_clover_sites": [P, P, D, D, P, L, P],
+            "oracle_threads": [],
             "oracle_apply_D": [P, I, P, P, P, P],
             "oracle_apply_D_sites": [P, I, P, P, P, P, L, P],
             "oracle_apply_DH": [P, I, P, P, P, P],
@@ -70,6 +72,7 @@ def _load():
             f.argtypes = args
             f.restype = None
         lib.oracle_shift.restype = L
+        lib.oracle_threads.restype = I
         _lib = lib
     return _lib
 
@@ -117,13 +120,17 @@ def clover(U, dims, m0: float, csw: float) -> np.ndarray:
 
 
 def clover_sites(U, dims, m0: float, csw: float, sites) -> np.ndarray:
+    """A(x) of Eq. 2.5 for the listed sites only: [len(sites), 12, 12]."""
     U = _c(U)
-    out = np.empty((len(sites), 12, 12), dtype=np.complex128)
-    lib = _load()
-    d = _dims(dims)
-    for i, s in enumerate(sites):
-        lib.oracle_clover_site(d, U.ctypes.data, m0, csw, int(s), out[i].ctypes.data)
+    s = np.ascontiguousarray(sites, dtype=np.int64)
+    out = np.empty((s.size, 12, 12), dtype=np.complex128)
+    _load().oracle_clover_sites(_dims(dims), U.ctypes.data, m0, csw, s.ctypes.data, s.size, out.ctypes.data)
     return out
+
+
+def threads() -> int:
+    """OpenMP threads the oracle's site loops use."""
+    return int(_load().oracle_threads())
 
 
 def apply_D(U, A, psi, dims, t_bc: int = -1) -> np.ndarray:

@@ -32,6 +32,9 @@
  *   psi [V][12], U [V][4][3][3], A [V][12][12], G and F [V][4][3][3].
  */
 #include <complex.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdint.h>
 #include <string.h>
 
@@ -183,6 +186,22 @@ void oracle_clover_site(const int d[4], const cplx* U, double m0, double csw, in
             for (int b = 0; b < 3; ++b)
               A[(3 * s + a) * 12 + 3 * sp + b] -= (csw / 32.0) * GG[4 * s + sp] * F[3 * a + b];
     }
+}
+
+/* A(x) for a list of sites: A[i] = A(sites[i]). */
+void oracle_clover_sites(const int d[4], const cplx* U, double m0, double csw, const int64_t* sites, int64_t n,
+                         cplx* A) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) oracle_clover_site(d, U, m0, csw, sites[i], A + i * 144);
+}
+
+/* Threads an OpenMP loop of this library uses. */
+int oracle_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
 }
 
 void oracle_clover_field(const int d[4], const cplx* U, double m0, double csw, cplx* A) {

@@ -8,3 +8,4 @@ from .binding import *  # noqa: F401,F403
 from .binding import load, Lattice, Gauge, Operator, SolveParams, Stats, DDError  # noqa: F401
 
 lib = load()
+from .autograd import dirac, su3_force, DiracApply  # noqa: E402,F401

@@ -254,6 +254,7 @@ void dd_solve_params_default(dd_solve_params* p) {
   p->inner_tol = 1e-6;
   p->even_odd = 1;
   p->verbose = 0;
+  p->precond = DD_PRECOND_NONE;
 }
 
 int dd_solve(dd_clover* op, const dd_solve_params* params, const void* b, void* x, int nrhs, int layout,
@@ -261,6 +262,8 @@ int dd_solve(dd_clover* op, const dd_solve_params* params, const void* b, void* 
   if (!op || !params || !b || !x || nrhs < 1) return fail(DD_ERR_ARG, "null argument or nrhs < 1");
   if (layout != DD_LAYOUT_CANONICAL && layout != DD_LAYOUT_CANONICAL_HOST)
     return fail(DD_ERR_ARG, "dd_solve takes canonical fields");
+  if (params->precond != DD_PRECOND_NONE && params->precond != DD_PRECOND_NORMAL)
+    return fail(DD_ERR_ARG, "unknown preconditioner");
   if (!(params->tol > 0) || params->max_restarts < 1 || params->max_outer < 0)
     return fail(DD_ERR_ARG, "bad solver parameters");
   cudaStream_t st = as_stream(stream);

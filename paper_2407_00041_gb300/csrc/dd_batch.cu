@@ -1,18 +1,283 @@
-// Batched uneven-lattice apply (placeholder until the persistent kernel lands).
+// Batched apply of D over lattices of different sizes in one persistent launch.
+//
+// Work items are tiles of `tile` consecutive (site, right-hand side) output
+// slots of one lattice; with the RHS-innermost layout a tile covers
+// tile / N sites times all N right-hand sides (the RHS block), so the links
+// and self-coupling blocks of a site are fetched once for all its RHS.
+// A fixed grid of CTAs (a multiple of the SM count) pulls items from a
+// global counter with atomicAdd until the list is exhausted: there are no
+// waits, so a CTA can never block on another.  The launch shape (tile,
+// CTAs per SM) is chosen by timing candidates (dd_batch_tune), and the
+// counter reset plus the launch can be captured once in a CUDA graph and
+// replayed.
+#include <algorithm>
+#include <vector>
+
+#include "dd_hop.cuh"
 #include "dd_internal.h"
 
+struct dd_batch {
+  std::vector<dd_clover*> ops;
+  std::vector<int> nrhs;
+  int prec = 0;
+  int count = 0;
+  int tile = 128;
+  int ctas_per_sm = 4;
+  int sms = 0;
+  dd::DevBuf args, item_start, counter;
+  dd::HopArgs* h_args = nullptr;  // pinned staging
+  std::vector<const void*> last_in;
+  std::vector<void*> last_out;
+  int64_t total_items = 0;
+  int staged_tile = -1;
+  cudaGraphExec_t gexec = nullptr;
+  cudaGraph_t graph = nullptr;
+  std::vector<const void*> g_in;
+  std::vector<void*> g_out;
+  ~dd_batch() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    if (h_args) cudaFreeHost(h_args);
+  }
+};
+
+namespace dd {
+
+namespace {
+
+template <int PG, int PIN, int POUT>
+__global__ void __launch_bounds__(256) k_hop_batch(const HopArgs* __restrict__ args,
+                                                   const int64_t* __restrict__ item_start, int count,
+                                                   int64_t total_items, unsigned long long* counter) {
+  __shared__ int64_t s_item;
+  __shared__ int s_lat;
+  __shared__ HopArgs s_args;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int64_t item = (int64_t)atomicAdd(counter, 1ULL);
+      s_item = item;
+      int l = 0;
+      if (item < total_items)
+        while (l + 1 < count && item >= item_start[l + 1]) ++l;
+      s_lat = l;
+    }
+    __syncthreads();
+    const int64_t item = s_item;
+    if (item >= total_items) break;
+    if (threadIdx.x == 0) s_args = args[s_lat];
+    __syncthreads();
+    const int64_t tid = (item - item_start[s_lat]) * blockDim.x + threadIdx.x;
+    if (tid < (int64_t)s_args.g.Vh * s_args.nrhs * s_args.npar) hop_thread<PG, PIN, POUT, false, EPI_D>(s_args, tid);
+    __syncthreads();
+  }
+}
+
+int stage(dd_batch* b, const void* const* ins, void* const* outs, cudaStream_t st) {
+  bool same = b->staged_tile == b->tile && (int)b->last_in.size() == b->count;
+  for (int i = 0; same && i < b->count; ++i) same = b->last_in[i] == ins[i] && b->last_out[i] == outs[i];
+  if (same) return DD_OK;
+  DD_CUDA(cudaStreamSynchronize(st));  // the staging buffer may still be in flight
+  std::vector<int64_t> starts(b->count + 1, 0);
+  const int pi = prec_index(b->prec);
+  for (int i = 0; i < b->count; ++i) {
+    const dd_clover* op = b->ops[i];
+    const dd_lattice* lat = op->lat;
+    HopArgs& a = b->h_args[i];
+    a.g = lat->geom();
+    a.nrhs = b->nrhs[i];
+    a.p0 = 0;
+    a.npar = 2;
+    a.gstride = lat->Vh * b->nrhs[i];
+    Field fi = field_view(lat, b->prec, 0, const_cast<void*>(ins[i]), b->nrhs[i]);
+    Field fo = field_view(lat, b->prec, 0, outs[i], b->nrhs[i]);
+    for (int p = 0; p < 2; ++p) {
+      a.in[p] = fi.h[p];
+      a.y[p] = fi.h[p];
+      a.out[p] = fo.h[p];
+      a.z[p] = HalfField{nullptr, nullptr};
+      a.U[p] = op->gauge->U(pi, p);
+      a.M[p] = op->M(pi, p);
+    }
+    a.beta = -0.5;
+    const int64_t slots = 2 * lat->Vh * b->nrhs[i];
+    starts[i + 1] = starts[i] + (slots + b->tile - 1) / b->tile;
+  }
+  b->total_items = starts[b->count];
+  DD_CUDA(cudaMemcpyAsync(b->args.ptr, b->h_args, sizeof(HopArgs) * b->count, cudaMemcpyHostToDevice, st));
+  DD_CUDA(cudaMemcpyAsync(b->item_start.ptr, starts.data(), sizeof(int64_t) * (b->count + 1),
+                          cudaMemcpyHostToDevice, st));
+  DD_CUDA(cudaStreamSynchronize(st));
+  b->last_in.assign(ins, ins + b->count);
+  b->last_out.assign(outs, outs + b->count);
+  b->staged_tile = b->tile;
+  return DD_OK;
+}
+
+int launch(dd_batch* b, cudaStream_t st) {
+  DD_CUDA(cudaMemsetAsync(b->counter.ptr, 0, sizeof(unsigned long long), st));
+  const int grid = b->sms * b->ctas_per_sm;
+  const HopArgs* args = reinterpret_cast<const HopArgs*>(b->args.ptr);
+  const int64_t* starts = reinterpret_cast<const int64_t*>(b->item_start.ptr);
+  unsigned long long* ctr = reinterpret_cast<unsigned long long*>(b->counter.ptr);
+  if (b->prec == P32)
+    k_hop_batch<P32, P32, P32><<<grid, b->tile, 0, st>>>(args, starts, b->count, b->total_items, ctr);
+  else
+    k_hop_batch<P16, P16, P16><<<grid, b->tile, 0, st>>>(args, starts, b->count, b->total_items, ctr);
+  DD_CUDA(cudaGetLastError());
+  return DD_OK;
+}
+
+int max_ctas(int prec, int tile) {
+  int n = 0;
+  cudaError_t e = prec == P32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hop_batch<P32, P32, P32>, tile, 0)
+                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hop_batch<P16, P16, P16>, tile, 0);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 1;
+  }
+  return std::max(1, n);
+}
+
+void drop_graph(dd_batch* b) {
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->gexec = nullptr;
+  b->graph = nullptr;
+}
+
+}  // namespace
+
+}  // namespace dd
+
+using namespace dd;
+
 extern "C" {
-int dd_batch_create(dd_clover* const*, int, int, const int*, dd_batch**) {
-  return dd::fail(DD_ERR_UNSUPPORTED, "batched apply is not built yet");
+
+int dd_batch_create(dd_clover* const* ops, int count, int prec, const int* nrhs, dd_batch** out) {
+  if (!ops || !nrhs || !out || count < 1) return fail(DD_ERR_ARG, "null argument or empty batch");
+  if (prec != DD_PREC_F32 && prec != DD_PREC_F16) return fail(DD_ERR_ARG, "batched precision must be F32 or F16");
+  const int pi = prec_index(prec);
+  for (int i = 0; i < count; ++i) {
+    if (!ops[i] || nrhs[i] < 1) return fail(DD_ERR_ARG, "null operator or nrhs < 1");
+    if (!ops[i]->clov[pi].ptr || !ops[i]->gauge->links[pi].ptr)
+      return fail(DD_ERR_UNSUPPORTED, "precision not created in an operator of the batch");
+  }
+  dd_batch* b = new dd_batch;
+  b->ops.assign(ops, ops + count);
+  b->nrhs.assign(nrhs, nrhs + count);
+  b->prec = prec;
+  b->count = count;
+  int dev = 0;
+  int s = DD_OK;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev))
+    s = cuda_fail(cudaGetLastError(), "device query");
+  if (s == DD_OK) s = b->args.alloc(sizeof(HopArgs) * count);
+  if (s == DD_OK) s = b->item_start.alloc(sizeof(int64_t) * (count + 1));
+  if (s == DD_OK) s = b->counter.alloc(sizeof(unsigned long long));
+  if (s == DD_OK && cudaMallocHost((void**)&b->h_args, sizeof(HopArgs) * count) != cudaSuccess) {
+    b->h_args = nullptr;
+    s = fail(DD_ERR_OOM, "pinned host allocation failed");
+  }
+  if (s == DD_OK) b->ctas_per_sm = std::min(4, max_ctas(prec, b->tile));
+  if (s != DD_OK) {
+    delete b;
+    return s;
+  }
+  *out = b;
+  return DD_OK;
 }
-int dd_batch_destroy(dd_batch*) { return DD_OK; }
-int dd_apply_batched(dd_batch*, const void* const*, void* const*, void*) {
-  return dd::fail(DD_ERR_UNSUPPORTED, "batched apply is not built yet");
+
+int dd_batch_destroy(dd_batch* b) {
+  delete b;
+  return DD_OK;
 }
-int dd_batch_tune(dd_batch*, const void* const*, void* const*, void*, int*) {
-  return dd::fail(DD_ERR_UNSUPPORTED, "batched apply is not built yet");
+
+int dd_apply_batched(dd_batch* b, const void* const* ins, void* const* outs, void* stream) {
+  if (!b || !ins || !outs) return fail(DD_ERR_ARG, "null argument");
+  for (int i = 0; i < b->count; ++i)
+    if (!ins[i] || !outs[i]) return fail(DD_ERR_ARG, "null field pointer");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  DD_TRY(stage(b, ins, outs, st));
+  return launch(b, st);
 }
-int dd_apply_batched_graph(dd_batch*, const void* const*, void* const*, void*) {
-  return dd::fail(DD_ERR_UNSUPPORTED, "batched apply is not built yet");
+
+int dd_batch_tune(dd_batch* b, const void* const* ins, void* const* outs, void* stream, int* chosen3) {
+  if (!b || !ins || !outs) return fail(DD_ERR_ARG, "null argument");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  DD_CUDA(cudaEventCreate(&e0));
+  DD_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_tile = b->tile, best_ctas = b->ctas_per_sm;
+  const int tiles[3] = {64, 128, 256};
+  const int ctas[5] = {1, 2, 4, 8, 16};
+  for (int ti = 0; ti < 3; ++ti) {
+    const int cap = max_ctas(b->prec, tiles[ti]);
+    for (int ci = 0; ci < 5; ++ci) {
+      if (ctas[ci] > cap) continue;
+      b->tile = tiles[ti];
+      b->ctas_per_sm = ctas[ci];
+      DD_TRY(stage(b, ins, outs, st));
+      DD_TRY(launch(b, st));  // warm-up
+      DD_CUDA(cudaEventRecord(e0, st));
+      for (int r = 0; r < 3; ++r) DD_TRY(launch(b, st));
+      DD_CUDA(cudaEventRecord(e1, st));
+      DD_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      DD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) {
+        best = ms;
+        best_tile = tiles[ti];
+        best_ctas = ctas[ci];
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->tile = best_tile;
+  b->ctas_per_sm = best_ctas;
+  drop_graph(b);
+  DD_TRY(stage(b, ins, outs, st));
+  if (chosen3) {
+    chosen3[0] = b->tile;
+    chosen3[1] = b->tile;
+    chosen3[2] = b->ctas_per_sm;
+  }
+  return DD_OK;
 }
+
+int dd_apply_batched_graph(dd_batch* b, const void* const* ins, void* const* outs, void* stream) {
+  if (!b || !ins || !outs) return fail(DD_ERR_ARG, "null argument");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (b->gexec) {
+    bool same = (int)b->g_in.size() == b->count;
+    for (int i = 0; same && i < b->count; ++i) same = b->g_in[i] == ins[i] && b->g_out[i] == outs[i];
+    if (!same) return fail(DD_ERR_ARG, "graph was captured with other field pointers");
+    DD_CUDA(cudaGraphLaunch(b->gexec, st));
+    return DD_OK;
+  }
+  DD_TRY(stage(b, ins, outs, st));
+  cudaStream_t cap;
+  DD_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  int s = DD_OK;
+  if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    s = cuda_fail(cudaGetLastError(), "cudaStreamBeginCapture");
+  if (s == DD_OK) s = launch(b, cap);
+  cudaGraph_t g = nullptr;
+  if (cudaStreamEndCapture(cap, &g) != cudaSuccess && s == DD_OK) s = cuda_fail(cudaGetLastError(), "capture");
+  if (s == DD_OK && cudaGraphInstantiate(&b->gexec, g, 0) != cudaSuccess)
+    s = cuda_fail(cudaGetLastError(), "cudaGraphInstantiate");
+  cudaStreamDestroy(cap);
+  if (s != DD_OK) {
+    if (g) cudaGraphDestroy(g);
+    b->gexec = nullptr;
+    return s;
+  }
+  b->graph = g;
+  b->g_in.assign(ins, ins + b->count);
+  b->g_out.assign(outs, outs + b->count);
+  DD_CUDA(cudaGraphLaunch(b->gexec, st));
+  return DD_OK;
 }
+
+}  // extern "C"

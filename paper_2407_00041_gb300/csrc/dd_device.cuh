@@ -277,6 +277,18 @@ __device__ __forceinline__ SiteCoord site_coords(const Geom& g, int s, int p) {
   return sc;
 }
 
+__device__ __forceinline__ SiteCoord lex_coords(const Geom& g, int lex) {
+  SiteCoord sc;
+  sc.lex = lex;
+  const int r1 = lex / g.n[3];
+  sc.c[3] = lex - r1 * g.n[3];
+  const int r2 = r1 / g.n[2];
+  sc.c[2] = r1 - r2 * g.n[2];
+  sc.c[0] = r2 / g.n[1];
+  sc.c[1] = r2 - sc.c[0] * g.n[1];
+  return sc;
+}
+
 // lexicographic index of the neighbour x + mu (fwd) or x - mu (bwd)
 __device__ __forceinline__ int nb_fwd(const Geom& g, const SiteCoord& sc, int mu) {
   return sc.c[mu] == g.n[mu] - 1 ? sc.lex - (g.n[mu] - 1) * g.stride[mu] : sc.lex + g.stride[mu];

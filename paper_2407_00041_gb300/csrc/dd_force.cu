@@ -1,8 +1,349 @@
-// Link derivative of L = Re <phi, D psi> (placeholder until the kernel lands).
+// Link derivative of L = Re <phi, D psi> = Re sum_x phi(x)^H (D psi)(x).
+//
+// G_mu(x) = dL/dRe U_mu(x) + i dL/dIm U_mu(x); F = P(G U^H) with
+// P(M) = (M - M^H)/2 - tr(M - M^H)/6 I (the su(3) component).
+//
+// Hopping terms (Eq. 1.13).  The link U = U_mu(x) enters the forward hop at
+// x and the backward hop at y = x + mu.  Because (I -+ gamma_mu) / 2 are
+// Hermitian projectors of rank two, each spin sum reduces to the two
+// independent components of the projected spinors (the same half-spinors
+// h = u -+ B_mu l that the stencil forms; nothing is stored, they are
+// recomputed here):
+//   G[a][b] = -1/2 s sum_{k=0,1} ( h-(phi(x))_{k,a} conj(h-(psi(y))_{k,b})
+//                                 + h+(psi(x))_{k,a} conj(h+(phi(y))_{k,b}) )
+// with s the time-boundary sign of the hop, summed over right-hand sides.
+//
+// Self coupling (Eq. 1.11, 1.12).  Since Q_numu = Q_munu^H,
+//   L_sc = const + Re sum_x sum_{mu<nu} tr(Q_munu(x) T'_munu(x)),
+//   T'_munu = 2 (T_munu - T_munu^H),
+//   T_munu[b][a] = -(c_sw/32) sum_{s,s'} (gamma_mu gamma_nu)[s][s'] psi(x)[s'][b] conj(phi(x)[s][a]).
+// For a leaf F1 F2 F3 F4 of Q_munu(x), tr(F1..F4 T') = tr(F_k R_k) with
+// R_k = F_{k+1}..F4 T' F1..F_{k-1}; the link of factor k receives R_k^H if
+// F_k = U and R_k if F_k = U^H (accumulated with atomic adds).
 #include "dd_internal.h"
 
 namespace dd {
-int force(dd_clover*, int, const double*, const double*, int, int, double*, double*, cudaStream_t) {
-  return fail(DD_ERR_UNSUPPORTED, "dd_force is not built yet");
+
+namespace {
+
+struct FGeom {
+  int n[4];
+  int stride[4];
+  int64_t V, Vh;
+  double t_bc;
+};
+
+FGeom fgeom(const dd_lattice* lat) {
+  FGeom g;
+  for (int i = 0; i < 4; ++i) g.n[i] = lat->dims[i];
+  g.stride[3] = 1;
+  g.stride[2] = g.n[3];
+  g.stride[1] = g.n[3] * g.n[2];
+  g.stride[0] = g.n[3] * g.n[2] * g.n[1];
+  g.V = lat->V;
+  g.Vh = lat->Vh;
+  g.t_bc = lat->t_bc;
+  return g;
 }
+
+__device__ __forceinline__ void coords_of(const FGeom& g, int lex, int c[4]) {
+  c[3] = lex % g.n[3];
+  int r = lex / g.n[3];
+  c[2] = r % g.n[2];
+  r /= g.n[2];
+  c[1] = r % g.n[1];
+  c[0] = r / g.n[1];
+}
+
+template <typename R>
+struct M3 {
+  cx<R> m[9];
+};
+
+template <typename R>
+__device__ __forceinline__ M3<R> load_link(const FGeom& g, const double2* U64, const int c[4], int mu) {
+  const int lex = ((c[0] * g.n[1] + c[1]) * g.n[2] + c[2]) * g.n[3] + c[3];
+  const int p = (c[0] + c[1] + c[2] + c[3]) & 1;
+  const double2* b = U64 + (int64_t)p * 36 * g.Vh + (int64_t)mu * 9 * g.Vh + (lex >> 1);
+  M3<R> r;
+#pragma unroll
+  for (int e = 0; e < 9; ++e) {
+    double2 v = b[e * g.Vh];
+    r.m[e] = mk<R>((R)v.x, (R)v.y);
+  }
+  return r;
+}
+
+template <typename R>
+__device__ __forceinline__ M3<R> mmul(const M3<R>& a, const M3<R>& b) {
+  M3<R> r;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      cx<R> acc = zero<R>();
+#pragma unroll
+      for (int k = 0; k < 3; ++k) acc = cfma(a.m[3 * i + k], b.m[3 * k + j], acc);
+      r.m[3 * i + j] = acc;
+    }
+  return r;
+}
+
+template <typename R>
+__device__ __forceinline__ M3<R> mdag(const M3<R>& a) {
+  M3<R> r;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) r.m[3 * i + j] = mk(a.m[3 * j + i].re, -a.m[3 * j + i].im);
+  return r;
+}
+
+// h = u + t B_mu l for a spinor given as 12 complex (3 spin + colour)
+template <typename R>
+__device__ __forceinline__ void half_spinor(int mu, int t, const cx<R> v[12], cx<R> h[2][3]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const cx<R> l0 = v[6 + c], l1 = v[9 + c];
+    cx<R> b0, b1;
+    switch (mu) {
+      case 0: b0 = l0; b1 = l1; break;
+      case 1: b0 = mul_mi(l0); b1 = mul_i(l1); break;
+      case 2: b0 = neg(l1); b1 = l0; break;
+      default: b0 = mul_mi(l1); b1 = mul_mi(l0); break;
+    }
+    h[0][c] = t > 0 ? v[c] + b0 : v[c] - b0;
+    h[1][c] = t > 0 ? v[3 + c] + b1 : v[3 + c] - b1;
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void load_canon(const double2* f, int64_t site, cx<R> v[12]) {
+#pragma unroll
+  for (int c = 0; c < 12; ++c) {
+    double2 d = f[site * 12 + c];
+    v[c] = mk<R>((R)d.x, (R)d.y);
+  }
+}
+
+// One thread per link (x, mu): hopping contribution, written (not added).
+template <typename R>
+__global__ void k_force_hop(FGeom g, const double2* __restrict__ phi, const double2* __restrict__ psi, int nrhs,
+                            double2* G) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= g.V * 4) return;
+  const int x = (int)(t >> 2), mu = (int)(t & 3);
+  int c[4];
+  coords_of(g, x, c);
+  R s = 1;
+  int y;
+  if (c[mu] == g.n[mu] - 1) {
+    y = x - (g.n[mu] - 1) * g.stride[mu];
+    if (mu == 0) s = (R)g.t_bc;
+  } else {
+    y = x + g.stride[mu];
+  }
+  cx<R> acc[9];
+#pragma unroll
+  for (int e = 0; e < 9; ++e) acc[e] = zero<R>();
+  for (int r = 0; r < nrhs; ++r) {
+    const double2* ph = phi + (int64_t)r * g.V * 12;
+    const double2* ps = psi + (int64_t)r * g.V * 12;
+    cx<R> v[12], hA[2][3], hB[2][3];
+    // h-(phi(x)) (x) conj(h-(psi(y)))
+    load_canon<R>(ph, x, v);
+    half_spinor<R>(mu, -1, v, hA);
+    load_canon<R>(ps, y, v);
+    half_spinor<R>(mu, -1, v, hB);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int k = 0; k < 2; ++k) acc[3 * a + b] = cfmac(hB[k][b], hA[k][a], acc[3 * a + b]);
+    // h+(psi(x)) (x) conj(h+(phi(y)))
+    load_canon<R>(ps, x, v);
+    half_spinor<R>(mu, +1, v, hA);
+    load_canon<R>(ph, y, v);
+    half_spinor<R>(mu, +1, v, hB);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int k = 0; k < 2; ++k) acc[3 * a + b] = cfmac(hB[k][b], hA[k][a], acc[3 * a + b]);
+  }
+  const R f = (R)(-0.5) * s;
+#pragma unroll
+  for (int e = 0; e < 9; ++e) G[t * 9 + e] = make_double2((double)(f * acc[e].re), (double)(f * acc[e].im));
+}
+
+__device__ __forceinline__ cx<double> Bm(int mu, int i, int j) {
+  if (mu == 0) return mk(i == j ? 1.0 : 0.0, 0.0);
+  if (mu == 1) return i != j ? mk(0.0, 0.0) : mk(0.0, i == 0 ? -1.0 : 1.0);
+  if (mu == 2) return i == j ? mk(0.0, 0.0) : mk(i == 0 ? -1.0 : 1.0, 0.0);
+  return i == j ? mk(0.0, 0.0) : mk(0.0, -1.0);
+}
+
+// (gamma_mu gamma_nu)[s][s'] in the chiral basis: block diagonal,
+// upper B_mu B_nu^H, lower B_mu^H B_nu.
+__device__ __forceinline__ cx<double> gg(int mu, int nu, int s, int sp) {
+  if ((s < 2) != (sp < 2)) return mk(0.0, 0.0);
+  const int i = s & 1, j = sp & 1;
+  cx<double> acc = zero<double>();
+  for (int k = 0; k < 2; ++k) {
+    if (s < 2) {
+      cx<double> b = Bm(nu, j, k);
+      acc = cfma(Bm(mu, i, k), mk(b.re, -b.im), acc);
+    } else {
+      cx<double> a = Bm(mu, k, i);
+      acc = cfma(mk(a.re, -a.im), Bm(nu, k, j), acc);
+    }
+  }
+  return acc;
+}
+
+template <typename R>
+__device__ __forceinline__ void atomic_add_m3(double2* G, const M3<R>& m, bool dagger) {
+  double* g = reinterpret_cast<double*>(G);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const cx<R> v = dagger ? mk(m.m[3 * j + i].re, -m.m[3 * j + i].im) : m.m[3 * i + j];
+      atomicAdd(g + 2 * (3 * i + j), (double)v.re);
+      atomicAdd(g + 2 * (3 * i + j) + 1, (double)v.im);
+    }
+}
+
+// One thread per site: self-coupling contribution, accumulated atomically.
+template <typename R>
+__global__ void k_force_clover(FGeom g, const double2* __restrict__ U64, const double2* __restrict__ phi,
+                               const double2* __restrict__ psi, int nrhs, double csw, double2* G) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= g.V) return;
+  int c[4];
+  coords_of(g, x, c);
+  cx<R> ph[12], ps[12];
+  for (int mu = 0; mu < 4; ++mu)
+    for (int nu = mu + 1; nu < 4; ++nu) {
+      // T[b][a] = -(c_sw/32) sum_{s,s'} gg[s][s'] psi[s'][b] conj(phi[s][a]), summed over RHS
+      M3<R> T;
+      for (int e = 0; e < 9; ++e) T.m[e] = zero<R>();
+      for (int r = 0; r < nrhs; ++r) {
+        load_canon<R>(phi + (int64_t)r * g.V * 12, x, ph);
+        load_canon<R>(psi + (int64_t)r * g.V * 12, x, ps);
+        for (int s = 0; s < 4; ++s)
+          for (int sp = 0; sp < 4; ++sp) {
+            const cx<double> w = gg(mu, nu, s, sp);
+            if (w.re == 0.0 && w.im == 0.0) continue;
+            const cx<R> wr = mk<R>((R)w.re, (R)w.im);
+            for (int b = 0; b < 3; ++b)
+              for (int a = 0; a < 3; ++a)
+                T.m[3 * b + a] = cfmac(ph[3 * s + a], cmul(wr, ps[3 * sp + b]), T.m[3 * b + a]);
+          }
+      }
+      // T' = 2 (T - T^H) scaled by -(c_sw / 32)
+      M3<R> Tp;
+      const R f = (R)(-2.0 * csw / 32.0);
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+          Tp.m[3 * i + j] = f * mk(T.m[3 * i + j].re - T.m[3 * j + i].re, T.m[3 * i + j].im + T.m[3 * j + i].im);
+      // the four leaves of Q_munu(x), Eq. 1.12: factor sites, directions, daggers
+      int xpm[4], xpn[4], xmm[4], xmn[4], xmm_pn[4], xmm_mn[4], xmn_pm[4];
+      auto sh = [&](const int* a, int d, int st, int* o) {
+        for (int i = 0; i < 4; ++i) o[i] = a[i];
+        o[d] = (a[d] + st + g.n[d]) % g.n[d];
+      };
+      sh(c, mu, +1, xpm);
+      sh(c, nu, +1, xpn);
+      sh(c, mu, -1, xmm);
+      sh(c, nu, -1, xmn);
+      sh(xmm, nu, +1, xmm_pn);
+      sh(xmm, nu, -1, xmm_mn);
+      sh(xmn, mu, +1, xmn_pm);
+      const int* site[4][4] = {{c, xpm, xpn, c}, {c, xmm_pn, xmm, xmm}, {xmm, xmm_mn, xmm_mn, xmn}, {xmn, xmn, xmn_pm, c}};
+      const int dir[4][4] = {{mu, nu, mu, nu}, {nu, mu, nu, mu}, {mu, nu, mu, nu}, {nu, mu, nu, mu}};
+      const int dag[4][4] = {{0, 0, 1, 1}, {0, 1, 1, 0}, {1, 1, 0, 0}, {1, 0, 0, 1}};
+      for (int l = 0; l < 4; ++l) {
+        M3<R> F[4];
+        for (int k = 0; k < 4; ++k) {
+          M3<R> u = load_link<R>(g, U64, site[l][k], dir[l][k]);
+          F[k] = dag[l][k] ? mdag(u) : u;
+        }
+        for (int k = 0; k < 4; ++k) {
+          M3<R> Rk;
+          bool first = true;
+          for (int j = k + 1; j < 4; ++j) {
+            Rk = first ? F[j] : mmul(Rk, F[j]);
+            first = false;
+          }
+          Rk = first ? Tp : mmul(Rk, Tp);
+          for (int j = 0; j < k; ++j) Rk = mmul(Rk, F[j]);
+          const int* sc = site[l][k];
+          const int lex = ((sc[0] * g.n[1] + sc[1]) * g.n[2] + sc[2]) * g.n[3] + sc[3];
+          atomic_add_m3<R>(G + ((int64_t)lex * 4 + dir[l][k]) * 9, Rk, dag[l][k] == 0);
+        }
+      }
+    }
+}
+
+// F = P(G U^H)
+__global__ void k_force_project(FGeom g, const double2* __restrict__ U64, const double2* __restrict__ G,
+                                double2* F) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= g.V * 4) return;
+  const int x = (int)(t >> 2), mu = (int)(t & 3);
+  int c[4];
+  coords_of(g, x, c);
+  M3<double> u = load_link<double>(g, U64, c, mu), gm;
+  for (int e = 0; e < 9; ++e) gm.m[e] = mk(G[t * 9 + e].x, G[t * 9 + e].y);
+  M3<double> M = mmul(gm, mdag(u));
+  cx<double> f[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      f[3 * i + j] = mk(0.5 * (M.m[3 * i + j].re - M.m[3 * j + i].re), 0.5 * (M.m[3 * i + j].im + M.m[3 * j + i].im));
+  const cx<double> tr = mk((f[0].re + f[4].re + f[8].re) / 3.0, (f[0].im + f[4].im + f[8].im) / 3.0);
+  for (int i = 0; i < 3; ++i) f[4 * i] = f[4 * i] - tr;
+  for (int e = 0; e < 9; ++e) F[t * 9 + e] = make_double2(f[e].re, f[e].im);
+}
+
+}  // namespace
+
+int force(dd_clover* op, int prec, const double* phi, const double* psi, int nrhs, int with_clover, double* G,
+          double* F, cudaStream_t st) {
+  const dd_lattice* lat = op->lat;
+  const FGeom g = fgeom(lat);
+  DevBuf gtmp;
+  double2* Gd = reinterpret_cast<double2*>(G);
+  if (!Gd) {
+    DD_TRY(gtmp.alloc((size_t)lat->V * 4 * 9 * sizeof(double2)));
+    Gd = reinterpret_cast<double2*>(gtmp.ptr);
+  }
+  const double2* ph = reinterpret_cast<const double2*>(phi);
+  const double2* ps = reinterpret_cast<const double2*>(psi);
+  const double2* U64 = reinterpret_cast<const double2*>(op->gauge->links[0].ptr);
+  const int64_t nl = lat->V * 4;
+  const unsigned bl = (unsigned)((nl + 127) / 128);
+  if (prec == P64)
+    k_force_hop<double><<<bl, 128, 0, st>>>(g, ph, ps, nrhs, Gd);
+  else
+    k_force_hop<float><<<bl, 128, 0, st>>>(g, ph, ps, nrhs, Gd);
+  DD_CUDA(cudaGetLastError());
+  if (with_clover && op->csw != 0.0) {
+    const unsigned bs = (unsigned)((lat->V + 63) / 64);
+    if (prec == P64)
+      k_force_clover<double><<<bs, 64, 0, st>>>(g, U64, ph, ps, nrhs, op->csw, Gd);
+    else
+      k_force_clover<float><<<bs, 64, 0, st>>>(g, U64, ph, ps, nrhs, op->csw, Gd);
+    DD_CUDA(cudaGetLastError());
+  }
+  if (F) {
+    k_force_project<<<bl, 128, 0, st>>>(g, U64, Gd, reinterpret_cast<double2*>(F));
+    DD_CUDA(cudaGetLastError());
+  }
+  if (!G) DD_CUDA(cudaStreamSynchronize(st));  // the temporary G is released on return
+  return DD_OK;
+}
+
 }  // namespace dd

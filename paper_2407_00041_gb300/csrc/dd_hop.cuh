@@ -141,23 +141,30 @@ __device__ __forceinline__ void block_apply(const typename Store<PG>::elem* M, i
   }
 }
 
+// The work of one thread: output slot `tid` in [0, npar * Vh * nrhs).
 template <int PG, int PIN, int POUT, bool DAG, int EPI>
-__global__ void __launch_bounds__(128) k_hop(const HopArgs a) {
+__device__ __forceinline__ void hop_thread(const HopArgs& a, int64_t tid) {
   using R = typename Store<PG>::real;
   using E = typename Store<PG>::elem;
-  const int64_t nper = (int64_t)a.g.Vh * a.nrhs;
-  int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= nper * a.npar) return;
-  int p = a.p0;
-  if (tid >= nper) {
-    tid -= nper;
-    p ^= 1;
+  int p, s, r;
+  SiteCoord sc;
+  if (a.npar == 2) {
+    // both parities: threads follow the lexicographic site order, so the two
+    // uses of every link (forward hop at x, backward hop at x + mu) and the
+    // reads of a neighbour spinor fall within about one time slice of traffic
+    const int lex = (int)(tid / a.nrhs);
+    r = (int)(tid - (int64_t)lex * a.nrhs);
+    sc = lex_coords(a.g, lex);
+    p = (sc.c[0] + sc.c[1] + sc.c[2] + sc.c[3]) & 1;
+    s = lex >> 1;
+  } else {
+    p = a.p0;
+    s = (int)(tid / a.nrhs);
+    r = (int)(tid - (int64_t)s * a.nrhs);
+    sc = site_coords(a.g, s, p);
   }
-  const int s = (int)(tid / a.nrhs);
-  const int r = (int)(tid - (int64_t)s * a.nrhs);
   const int q = p ^ 1;
   const int64_t Vh = a.g.Vh;
-  const SiteCoord sc = site_coords(a.g, s, p);
   // forward hop: (I - gamma) for D, (I + gamma) for D^H; backward the opposite
   constexpr int TF = DAG ? +1 : -1;
   constexpr int TB = -TF;
@@ -188,7 +195,7 @@ __global__ void __launch_bounds__(128) k_hop(const HopArgs a) {
 #undef DD_HOP_DIR
 
   const R beta = (R)a.beta;
-  const int64_t i = tid;  // == s * nrhs + r
+  const int64_t i = (int64_t)s * a.nrhs + r;
   const E* M = reinterpret_cast<const E*>(a.M[p]);
   cx<R> res[12];
   if constexpr (EPI == EPI_D || EPI == EPI_RESID) {
@@ -231,6 +238,13 @@ __global__ void __launch_bounds__(128) k_hop(const HopArgs a) {
     block_apply<PG, R>(M + s, Vh, y, res);
   }
   store_spinor<POUT, R>(a.out[p], a.gstride, i, res);
+}
+
+template <int PG, int PIN, int POUT, bool DAG, int EPI>
+__global__ void __launch_bounds__(128) k_hop(const HopArgs a) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= (int64_t)a.g.Vh * a.nrhs * a.npar) return;
+  hop_thread<PG, PIN, POUT, DAG, EPI>(a, tid);
 }
 
 template <int PG, int PIN, int POUT>

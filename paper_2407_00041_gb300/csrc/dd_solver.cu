@@ -54,12 +54,15 @@ struct Inner {
   int N, m;
   int64_t L;     // 16-byte groups per vector
   size_t vbytes;
-  DevBuf basis, w, rvec, tmp, red, partials, coef;
+  bool normal = false;  // right preconditioner M^{-1} = D^H (Dhat^H)
+  int verbose = 0;
+  DevBuf basis, w, rvec, tmp, red, partials, coef, zt, ut;
   Pinned hred, hcoef;
   // counters
   int applies = 0, steps = 0, cycles = 0;
 
-  int init(const dd_clover* op_, int pg_, int pv_, bool eo_, int N_, int m_) {
+  int init(const dd_clover* op_, int pg_, int pv_, bool eo_, int N_, int m_, bool normal_) {
+    normal = normal_;
     op = op_;
     pg = pg_;
     pv = pv_;
@@ -72,6 +75,10 @@ struct Inner {
     DD_TRY(basis.ensure(vbytes * (m + 1)));
     DD_TRY(w.ensure(vbytes));
     DD_TRY(rvec.ensure(vbytes));
+    if (normal) {
+      DD_TRY(zt.ensure(vbytes));
+      DD_TRY(ut.ensure(vbytes));
+    }
     if (eo) DD_TRY(tmp.ensure(field_bytes(lat, pv, 2, N)));
     const size_t nred = (size_t)(2 * (m + 1) + 1) * N;
     DD_TRY(red.ensure(nred * sizeof(double2)));
@@ -85,10 +92,18 @@ struct Inner {
   void* V(int j) { return reinterpret_cast<char*>(basis.ptr) + vbytes * j; }
   Field fv(void* p) { return field_view(op->lat, pv, eo ? 1 : 0, p, N); }
 
-  int apply(void* in, void* out, cudaStream_t st) {
+  // the operator A of the inner system (Dhat or D)
+  int apply_op(const void* in, void* out, bool dagger, cudaStream_t st) {
     ++applies;
-    if (eo) return op_Dhat(op, pg, pv, false, fv(in), fv(out), field_view(op->lat, pv, 2, tmp.ptr, N), st);
-    return op_D(op, pg, pv, false, fv(in), fv(out), st);
+    void* i = const_cast<void*>(in);
+    if (eo) return op_Dhat(op, pg, pv, dagger, fv(i), fv(out), field_view(op->lat, pv, 2, tmp.ptr, N), st);
+    return op_D(op, pg, pv, dagger, fv(i), fv(out), st);
+  }
+  // w = A M^{-1} v (Algorithm 2, lines 8-9)
+  int apply(const void* v, void* out, cudaStream_t st) {
+    if (!normal) return apply_op(v, out, false, st);
+    DD_TRY(apply_op(v, zt.ptr, true, st));
+    return apply_op(zt.ptr, out, false, st);
   }
 
   int dots(const VecList& vs, int J, const void* x, double2* out, int add, cudaStream_t st) {
@@ -141,7 +156,7 @@ struct Inner {
       if (cyc == 0) {
         DD_CUDA(cudaMemcpyAsync(rvec.ptr, f, vbytes, cudaMemcpyDeviceToDevice, st));
       } else {
-        DD_TRY(apply(e, w.ptr, st));
+        DD_TRY(apply_op(e, w.ptr, false, st));
         DD_CUDA(cudaMemcpyAsync(rvec.ptr, f, vbytes, cudaMemcpyDeviceToDevice, st));
         VecList vw;
         vw.p[0] = w.ptr;
@@ -253,8 +268,26 @@ struct Inner {
       DD_CUDA(cudaMemcpyAsync(dcoef, hc, (size_t)jmax * N * sizeof(double2), cudaMemcpyHostToDevice, st));
       VecList vs;
       for (int i = 0; i < jmax; ++i) vs.p[i] = V(i);
-      DD_TRY(axpys(vs, jmax, dcoef, 1.0, e, st));
+      if (!normal) {
+        DD_TRY(axpys(vs, jmax, dcoef, 1.0, e, st));  // line 19 with z_j = v_j
+      } else {
+        // fixed preconditioner: e += M^{-1} (V y) (line 19 of Algorithm 1)
+        DD_CUDA(cudaMemsetAsync(ut.ptr, 0, vbytes, st));
+        DD_TRY(axpys(vs, jmax, dcoef, 1.0, ut.ptr, st));
+        DD_TRY(apply_op(ut.ptr, zt.ptr, true, st));
+        VecList vz;
+        vz.p[0] = zt.ptr;
+        DD_CUDA(cudaStreamSynchronize(st));
+        for (int r = 0; r < N; ++r) hc[r] = make_double2(1.0, 0.0);
+        DD_CUDA(cudaMemcpyAsync(dcoef, hc, N * sizeof(double2), cudaMemcpyHostToDevice, st));
+        DD_TRY(axpys(vz, 1, dcoef, 1.0, e, st));
+      }
       DD_CUDA(cudaStreamSynchronize(st));  // hc is reused by the next cycle
+      if (verbose) {
+        double worst = 0.0;
+        for (int r = 0; r < N; ++r) worst = std::max(worst, est[r]);
+        fprintf(stderr, "[dd_solve]   cycle %d: %d steps, max residual estimate %.3e\n", cycles, jmax, worst);
+      }
       done = true;
       for (int r = 0; r < N; ++r)
         if (est[r] >= tol_rel[r] && fnorm[r] > 0.0) done = false;
@@ -317,7 +350,8 @@ int solve(dd_clover* op, const dd_solve_params* prm, const double* b_canon, doub
   for (int r = 0; r < N; ++r)
     if (!std::isfinite(bnorm[r])) return fail(DD_ERR_ARG, "right-hand side contains NaN or Inf");
   Inner inner;
-  DD_TRY(inner.init(op, pg, pv, eo, N, prm->restart));
+  DD_TRY(inner.init(op, pg, pv, eo, N, prm->restart, prm->precond == DD_PRECOND_NORMAL));
+  inner.verbose = prm->verbose;
   dd_stats s{};
   int status = DD_ERR_NOT_CONVERGED;
   for (int outer = 0;; ++outer) {

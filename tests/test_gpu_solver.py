@@ -38,11 +38,12 @@ def oracle_residual(U, A, dims, b, x):
 
 @pytest.mark.parametrize("inner", [dd.DD_PREC_F64, dd.DD_PREC_F32, dd.DD_PREC_F16])
 @pytest.mark.parametrize("even_odd", [1, 0])
-def test_solve_to_1e10(sys44, inner, even_odd):
+@pytest.mark.parametrize("precond", [dd.DD_PRECOND_NONE, dd.DD_PRECOND_NORMAL])
+def test_solve_to_1e10(sys44, inner, even_odd, precond):
     dims, U, A, op, b, xref, _ = sys44
     bt = torch.from_numpy(b[:1]).cuda()
     x = torch.zeros_like(bt)
-    status, st = op.solve(bt, x, 1, tol=1e-10, inner_prec=inner, even_odd=even_odd, restart=30)
+    status, st = op.solve(bt, x, 1, tol=1e-10, inner_prec=inner, even_odd=even_odd, restart=30, precond=precond)
     assert status == 0, st
     assert st["converged"] == 1 and st["true_residual"] < 1e-10
     xn = x.cpu().numpy()[0]
