@@ -250,6 +250,22 @@ int dd_apply_batched_graph(dd_batch* b, const void* const* ins, void* const* out
  * written to host memory after synchronising the stream. */
 int dd_dot(const double* a, const double* b, int64_t nsites, int nrhs, double* dots_host /*[nrhs][2]*/, void* stream);
 
+/* Allocation-free variant of dd_dot.  The thesis has no counterpart; it is
+ * for callers that cannot allocate device memory when they need the inner
+ * products: code whose memory pool already owns the free device memory,
+ * callers under a hard allocation cap, and phases where cudaMalloc or cudaFree
+ * would synchronise the device.  Same arguments and result as dd_dot; no
+ * cudaMalloc, cudaFree or allocating library routine is called.
+ * Scratch: a fixed device array of about 20 KB inside the library, held on
+ * every GPU that loads the library until the process exits.  Its device
+ * address is looked up on the first call made on each device, so make that
+ * first call before any stream capture.  All calls share the array and it
+ * keeps the last call's contents (nothing in it has to start at zero), so
+ * calls that overlap on the GPU (other streams or threads) race.
+ * Limit: nrhs <= 64, else DD_ERR_ARG.  Synchronises `stream`. */
+int dd_dot_noalloc(const double* a, const double* b, int64_t nsites, int nrhs, double* dots_host /*[nrhs][2]*/,
+                   void* stream);
+
 /* ---- arithmetic peak probe ----
  * The method of Section 3.1 / Table 3.1 of the thesis: many threads each run
  * long register-only chains of floating-point operations (here eight
