@@ -320,6 +320,113 @@ def run_reference(args):
     return 0
 
 
+# ---------------------------------------------------------------- other rows of the hot path
+def _time_fn(fn, reps, warmup=3):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps * 1e-3
+
+
+def extra_measurements(dd, torch, stream, op48, psi48, V48, tdist, clocks):
+    """Multi-RHS D psi at 32^4 x 12 RHS, the batched uneven-lattice launch
+    (8^4 x 1, 16^4 x 5, 24^4 x 17, 32^4 x 32 RHS) against one launch per
+    lattice, Dhat at 48^3 x 96, and the autograd adjoint at 24^4."""
+    import ctypes
+    import synthetic
+    out = {}
+    st = stream.cuda_stream
+    # Dhat on the odd sites of the 48^3 x 96 lattice
+    for name, p in (("f32", 2), ("f16", 4)):
+        hb = op48.field_bytes(p, 1, 1)
+        hi = torch.empty(hb, dtype=torch.uint8, device="cuda")
+        ho = torch.empty_like(hi)
+        op48.pack(p, 1, psi48[:, : V48 // 2].contiguous(), hi, 1)
+        t = _time_fn(lambda: dd.check(dd.lib.dd_apply(op48.h, dd.DD_OP_DHAT, p, hi.data_ptr(), ho.data_ptr(), 1,
+                                                      dd.DD_LAYOUT_NATIVE, st), "Dhat"), 20)
+        # two half-lattice hops read every link twice; A_oo and A_ee^-1 once;
+        # five half-field spinor passes (psi_o twice, t_e written and read, out_o)
+        link, clov, spin = {"f32": (288, 288, 96), "f16": (144, 144, 52)}[name]
+        bytes_ = 2 * link * V48 + clov * V48 + 5 * spin * (V48 // 2)
+        out[f"dhat_{name}"] = {"ms": t * 1e3, "gbs_formula": bytes_ / t / 1e9}
+    # lattices of config 3
+    shapes = [(8, 8, 8, 8), (16, 16, 16, 16), (24, 24, 24, 24), (32, 32, 32, 32)]
+    nrhs = [1, 5, 17, 32]
+    keep, ops, ins, outs = [], [], [], []
+    for dims, n in zip(shapes, nrhs):
+        lat = dd.Lattice(dims, -1)
+        g = dd.Gauge(lat, synthetic.gauge(dims, eps=EPS), precisions=dd.DD_PREC_F64 | dd.DD_PREC_F32 | dd.DD_PREC_F16)
+        o = dd.Operator(g, M0, CSW)
+        keep.append((lat, g, o))
+        ops.append(o)
+        x = torch.from_numpy(synthetic.spinor(dims, nrhs=n)).cuda()
+        nb = o.field_bytes(2, 0, n)
+        xi = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        o.pack(2, 0, x, xi, n)
+        ins.append(xi)
+        outs.append(torch.empty_like(xi))
+        del x
+    # multi-RHS at 32^4 x 12 (the first 12 of the 32 RHS) in FP32 and FP16
+    lat32, g32, o32 = keep[3]
+    V32 = lat32.V
+    x12 = torch.from_numpy(synthetic.spinor(shapes[3], nrhs=12)).cuda()
+    for name, p in (("f32", 2), ("f16", 4)):
+        nb = o32.field_bytes(p, 0, 12)
+        xi = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        xo = torch.empty_like(xi)
+        o32.pack(p, 0, x12, xi, 12)
+        t = _time_fn(lambda: dd.check(dd.lib.dd_apply(o32.h, dd.DD_OP_D, p, xi.data_ptr(), xo.data_ptr(), 12,
+                                                      dd.DD_LAYOUT_NATIVE, st), "D 12 RHS"), 20)
+        out[f"mrhs_32x4_12rhs_{name}"] = {"ms": t * 1e3, "gbs": bytes_per_site(name, 12) * V32 / t / 1e9,
+                                          "site_rhs_per_s": V32 * 12 / t,
+                                          "hbm_frac": bytes_per_site(name, 12) * V32 / t / 1e9 / 6791.0}
+    del x12
+    # batched uneven lattices, FP32
+    arr = lambda v, t=ctypes.c_void_p: (t * len(v))(*v)
+    b = ctypes.c_void_p()
+    dd.check(dd.lib.dd_batch_create(arr([o.h.value for o in ops]), len(ops), 2, arr(nrhs, ctypes.c_int),
+                                    ctypes.byref(b)), "dd_batch_create")
+    pin = arr([x.data_ptr() for x in ins])
+    pout = arr([x.data_ptr() for x in outs])
+    chosen = (ctypes.c_int * 3)()
+    dd.check(dd.lib.dd_batch_tune(b, pin, pout, st, chosen), "dd_batch_tune")
+    t_batch = _time_fn(lambda: dd.check(dd.lib.dd_apply_batched_graph(b, pin, pout, st), "graph"), 20)
+
+    def separate():
+        for o, n, xi, xo in zip(ops, nrhs, ins, outs):
+            dd.check(dd.lib.dd_apply(o.h, dd.DD_OP_D, 2, xi.data_ptr(), xo.data_ptr(), n, dd.DD_LAYOUT_NATIVE, st),
+                     "D")
+
+    t_sep = _time_fn(separate, 20)
+    units = sum(int(np.prod(d)) * n for d, n in zip(shapes, nrhs))
+    bytes_ = sum(int(np.prod(d)) * bytes_per_site("f32", n) for d, n in zip(shapes, nrhs))
+    out["batch_config3_f32"] = {"ms_one_graph_launch": t_batch * 1e3, "ms_four_launches": t_sep * 1e3,
+                                "gbs": bytes_ / t_batch / 1e9, "site_rhs": units,
+                                "tuned_tile_threads": chosen[0], "tuned_ctas_per_sm": chosen[2]}
+    dd.lib.dd_batch_destroy(b)
+    # autograd adjoint at 24^4 (FP64 and FP32): D^H and the link force with the clover term
+    lat24, g24, o24 = keep[2]
+    V24 = lat24.V
+    phi = torch.from_numpy(synthetic.spinor(shapes[2], seed=synthetic.SEED_PHI)).cuda()
+    ps = torch.from_numpy(synthetic.spinor(shapes[2], seed=synthetic.SEED_RHS)).cuda()
+    G = torch.empty((V24, 4, 3, 3), dtype=torch.complex128, device="cuda")
+    F = torch.empty_like(G)
+    for name, p in (("f64", 1), ("f32", 2)):
+        t_f = _time_fn(lambda: o24.force(p, phi, ps, 1, True, G=G, F=F), 5, warmup=1)
+        tmp = torch.empty_like(phi)
+        t_dh = _time_fn(lambda: o24.apply(dd.DD_OP_DH, p, phi, tmp, 1), 10)
+        out[f"adjoint_24x4_{name}"] = {"ms_link_force_with_clover": t_f * 1e3, "ms_DH_canonical": t_dh * 1e3}
+    return out
+
+
 # ---------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -330,7 +437,9 @@ def main():
     ap.add_argument("--prec", default="f32", choices=["f64", "f32", "f16"], help="headline precision")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the multi-RHS, batch, Dhat and adjoint lines")
     ap.add_argument("--solve-inner", default="f32", choices=["f32", "f16"])
+    ap.add_argument("--dims", default="96x48x48x48", help="nT x nZ x nY x nX (a smaller lattice for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -351,7 +460,7 @@ def main():
         gpu_id = None
     clocks = Clocks(gpu_id)
 
-    dims = DIMS
+    dims = tuple(int(v) for v in args.dims.split("x"))
     V = int(np.prod(dims))
     log("generating links and spinor")
     U = synthetic.gauge(dims, eps=EPS)
@@ -439,13 +548,15 @@ def main():
         solve = {}
         b = psi_dev
         sols = {}
-        for name, inner, restart in (("mixed", PREC[args.solve_inner], 30), ("fp64", PREC["f64"], 30)):
+        # FGMRES(24) with the right preconditioner M^{-1} = Dhat^H: plain
+        # restarted FGMRES stalls near 2.5e-3 on this lattice at m0 = -0.4
+        for name, inner, restart in (("mixed", PREC[args.solve_inner], 24), ("fp64", PREC["f64"], 24)):
             x = torch.zeros_like(b)
             log(f"solve {name}")
             barrier(tdist)
             w0 = time.time()
-            status, st = op.solve(b, x, 1, tol=1e-10, inner_prec=inner, restart=restart, max_restarts=400,
-                                  max_outer=20)
+            status, st = op.solve(b, x, 1, tol=1e-10, inner_prec=inner, restart=restart, max_restarts=100,
+                                  max_outer=10, precond=dd.DD_PRECOND_NORMAL)
             w1 = time.time()
             clocks.window(w0, w1)
             sols[name] = x
@@ -454,10 +565,16 @@ def main():
                            "true_residual": st["true_residual"], "outer": st["outer_iterations"],
                            "inner_steps": st["inner_iterations"], "applies_inner": st["applies_inner"],
                            "applies_fp64": st["applies_fp64"],
-                           "inner_prec": {1: "f64", 2: "f32", 4: "f16"}[inner]}
+                           "inner_prec": {1: "f64", 2: "f32", 4: "f16"}[inner],
+                           "method": "even-odd FGMRES(24), M^-1 = Dhat^H, one classical Gram-Schmidt pass, FP64 refinement"}
         d = (sols["mixed"] - sols["fp64"]).norm().item() / sols["fp64"].norm().item()
         solve["mixed_vs_fp64_solution_rel_diff"] = d
         solve["speedup_mixed_over_fp64"] = solve["fp64"]["seconds"] / solve["mixed"]["seconds"]
+
+    extra = None
+    if not args.no_extra:
+        log("extra measurements (multi-RHS, batch, Dhat, adjoint)")
+        extra = extra_measurements(dd, torch, stream, op, psi_dev, V, tdist, clocks)
 
     rows = clocks.stop()
     clk = clocks.summary(rows)
@@ -483,11 +600,12 @@ def main():
         "value": head["value"], "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"f64": "f64", "f32": "f32", "f16": "f32 (fp16 storage)"}[args.prec], "data": "synthetic",
-        "config": {"workload": WORKLOAD, "precision": args.prec, "nrhs": 1, "sites": V,
+        "config": {"workload": WORKLOAD if dims == DIMS else WORKLOAD.replace("48^3x96", args.dims),
+                   "precision": args.prec, "nrhs": 1, "sites": V,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "inputs (>8 GB) larger than L2; no flush"},
         "roofline": head["roofline"], "variants": variants, "e2e": e2e, "solve": solve,
-        "cpu_baseline": cpu, "parity_sample": parity, "gpu_launches": gpu_launches, "clocks": clk,
+        "cpu_baseline": cpu, "parity_sample": parity, "extra": extra, "gpu_launches": gpu_launches, "clocks": clk,
         "probe_tflops": {"f64": f64_peak / 1e12, "f32": f32_peak / 1e12},
     }
     print(json.dumps(line), flush=True)

@@ -183,6 +183,7 @@ typedef struct {
   int precond;         /* right preconditioner M^{-1} of Algorithm 2: DD_PRECOND_NONE (M = I)
                           or DD_PRECOND_NORMAL (M^{-1} = A^H, so A M^{-1} = A A^H is Hermitian
                           positive definite and restarted FGMRES cannot stagnate) */
+  int gs_passes;       /* classical Gram-Schmidt passes per Arnoldi step: 1, or 2 (re-orthogonalised) */
 } dd_solve_params;
 
 #define DD_PRECOND_NONE 0
@@ -200,7 +201,7 @@ typedef struct {
 } dd_stats;
 
 /* Fill `p` with defaults: tol 1e-10, restart 30, max_restarts 100,
- * max_outer 30, inner_prec F32, inner_tol 1e-6, even_odd 1, precond NONE. */
+ * max_outer 30, inner_prec F32, inner_tol 1e-6, even_odd 1, precond NONE, gs_passes 1. */
 void dd_solve_params_default(dd_solve_params* p);
 
 /*
@@ -239,7 +240,8 @@ int dd_batch_destroy(dd_batch* b);
 /* ins[i], outs[i]: native device fields of operator i (full lattice, nrhs[i] RHS). */
 int dd_apply_batched(dd_batch* b, const void* const* ins, void* const* outs, void* stream);
 /* Time candidate launch shapes on `stream` and keep the fastest; optional
- * report of the chosen shape (tile sites, threads per block, CTAs per SM). */
+ * report of the chosen shape (slots per tile, threads per block, CTAs per SM,
+ * where 0 CTAs per SM means one CTA per work item instead of a persistent grid). */
 int dd_batch_tune(dd_batch* b, const void* const* ins, void* const* outs, void* stream, int* chosen3);
 /* Capture the batched launch in a CUDA graph on first call and replay it
  * afterwards (same pointers required; DD_ERR_ARG otherwise). */

@@ -255,6 +255,7 @@ void dd_solve_params_default(dd_solve_params* p) {
   p->even_odd = 1;
   p->verbose = 0;
   p->precond = DD_PRECOND_NONE;
+  p->gs_passes = 1;
 }
 
 int dd_solve(dd_clover* op, const dd_solve_params* params, const void* b, void* x, int nrhs, int layout,

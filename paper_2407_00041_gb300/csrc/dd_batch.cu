@@ -1,15 +1,16 @@
-// Batched apply of D over lattices of different sizes in one persistent launch.
+// Batched apply of D over lattices of different sizes in one launch.
 //
 // Work items are tiles of `tile` consecutive (site, right-hand side) output
 // slots of one lattice; with the RHS-innermost layout a tile covers
 // tile / N sites times all N right-hand sides (the RHS block), so the links
-// and self-coupling blocks of a site are fetched once for all its RHS.
-// A fixed grid of CTAs (a multiple of the SM count) pulls items from a
-// global counter with atomicAdd until the list is exhausted: there are no
-// waits, so a CTA can never block on another.  The launch shape (tile,
-// CTAs per SM) is chosen by timing candidates (dd_batch_tune), and the
-// counter reset plus the launch can be captured once in a CUDA graph and
-// replayed.
+// and self-coupling blocks of a site are fetched once for all its RHS from
+// L1/L2.  The kernel walks the item list with a static stride of gridDim:
+// in the persistent shape the grid is the resident CTA count (a multiple of
+// the SM count) and every CTA loops over many items; in the flat shape the
+// grid has one CTA per item.  There are no atomics, barriers or waits; each
+// thread finds its lattice in the item prefix table.  The autotuner
+// (dd_batch_tune) times tile sizes and both shapes, and the chosen launch
+// can be captured once in a CUDA graph and replayed.
 #include <algorithm>
 #include <vector>
 
@@ -24,7 +25,7 @@ struct dd_batch {
   int tile = 128;
   int ctas_per_sm = 4;
   int sms = 0;
-  dd::DevBuf args, item_start, counter;
+  dd::DevBuf args, item_start;
   dd::HopArgs* h_args = nullptr;  // pinned staging
   std::vector<const void*> last_in;
   std::vector<void*> last_out;
@@ -45,30 +46,21 @@ namespace dd {
 
 namespace {
 
-template <int PG, int PIN, int POUT>
-__global__ void __launch_bounds__(256) k_hop_batch(const HopArgs* __restrict__ args,
-                                                   const int64_t* __restrict__ item_start, int count,
-                                                   int64_t total_items, unsigned long long* counter) {
-  __shared__ int64_t s_item;
-  __shared__ int s_lat;
-  __shared__ HopArgs s_args;
-  for (;;) {
-    if (threadIdx.x == 0) {
-      const int64_t item = (int64_t)atomicAdd(counter, 1ULL);
-      s_item = item;
-      int l = 0;
-      if (item < total_items)
-        while (l + 1 < count && item >= item_start[l + 1]) ++l;
-      s_lat = l;
-    }
-    __syncthreads();
-    const int64_t item = s_item;
-    if (item >= total_items) break;
-    if (threadIdx.x == 0) s_args = args[s_lat];
-    __syncthreads();
-    const int64_t tid = (item - item_start[s_lat]) * blockDim.x + threadIdx.x;
-    if (tid < (int64_t)s_args.g.Vh * s_args.nrhs * s_args.npar) hop_thread<PG, PIN, POUT, false, EPI_D>(s_args, tid);
-    __syncthreads();
+template <int THREADS>
+struct BatchMinBlocks {
+  static constexpr int value = THREADS >= 256 ? 2 : 640 / THREADS;
+};
+
+template <int P, int THREADS>
+__global__ void __launch_bounds__(THREADS, BatchMinBlocks<THREADS>::value)
+    k_hop_batch(const HopArgs* __restrict__ args, const int64_t* __restrict__ item_start, int count,
+                int64_t total_items) {
+  int l = 0;
+  for (int64_t item = blockIdx.x; item < total_items; item += gridDim.x) {
+    while (l + 1 < count && item >= item_start[l + 1]) ++l;  // items only grow within a CTA
+    const HopArgs& a = args[l];
+    const int64_t tid = (item - item_start[l]) * THREADS + threadIdx.x;
+    if (tid < (int64_t)a.g.Vh * a.nrhs * a.npar) hop_thread<P, P, P, false, EPI_D>(a, tid);
   }
 }
 
@@ -113,29 +105,43 @@ int stage(dd_batch* b, const void* const* ins, void* const* outs, cudaStream_t s
   return DD_OK;
 }
 
+template <int P, int T>
+void launch_t(dd_batch* b, unsigned grid, cudaStream_t st) {
+  k_hop_batch<P, T><<<grid, T, 0, st>>>(reinterpret_cast<const HopArgs*>(b->args.ptr),
+                                        reinterpret_cast<const int64_t*>(b->item_start.ptr), b->count,
+                                        b->total_items);
+}
+
+// ctas_per_sm == 0 selects the flat shape (one CTA per item).
 int launch(dd_batch* b, cudaStream_t st) {
-  DD_CUDA(cudaMemsetAsync(b->counter.ptr, 0, sizeof(unsigned long long), st));
-  const int grid = b->sms * b->ctas_per_sm;
-  const HopArgs* args = reinterpret_cast<const HopArgs*>(b->args.ptr);
-  const int64_t* starts = reinterpret_cast<const int64_t*>(b->item_start.ptr);
-  unsigned long long* ctr = reinterpret_cast<unsigned long long*>(b->counter.ptr);
-  if (b->prec == P32)
-    k_hop_batch<P32, P32, P32><<<grid, b->tile, 0, st>>>(args, starts, b->count, b->total_items, ctr);
-  else
-    k_hop_batch<P16, P16, P16><<<grid, b->tile, 0, st>>>(args, starts, b->count, b->total_items, ctr);
+  const int64_t g = b->ctas_per_sm > 0 ? (int64_t)b->sms * b->ctas_per_sm : b->total_items;
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, b->total_items));
+  if (b->prec == P32) {
+    if (b->tile == 64) launch_t<P32, 64>(b, grid, st);
+    else if (b->tile == 256) launch_t<P32, 256>(b, grid, st);
+    else launch_t<P32, 128>(b, grid, st);
+  } else {
+    if (b->tile == 64) launch_t<P16, 64>(b, grid, st);
+    else if (b->tile == 256) launch_t<P16, 256>(b, grid, st);
+    else launch_t<P16, 128>(b, grid, st);
+  }
   DD_CUDA(cudaGetLastError());
   return DD_OK;
 }
 
-int max_ctas(int prec, int tile) {
+template <int P, int T>
+int occupancy_t() {
   int n = 0;
-  cudaError_t e = prec == P32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hop_batch<P32, P32, P32>, tile, 0)
-                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hop_batch<P16, P16, P16>, tile, 0);
-  if (e != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hop_batch<P, T>, T, 0) != cudaSuccess) {
     (void)cudaGetLastError();
     return 1;
   }
   return std::max(1, n);
+}
+
+int max_ctas(int prec, int tile) {
+  if (prec == P32) return tile == 64 ? occupancy_t<P32, 64>() : tile == 256 ? occupancy_t<P32, 256>() : occupancy_t<P32, 128>();
+  return tile == 64 ? occupancy_t<P16, 64>() : tile == 256 ? occupancy_t<P16, 256>() : occupancy_t<P16, 128>();
 }
 
 void drop_graph(dd_batch* b) {
@@ -173,12 +179,11 @@ int dd_batch_create(dd_clover* const* ops, int count, int prec, const int* nrhs,
     s = cuda_fail(cudaGetLastError(), "device query");
   if (s == DD_OK) s = b->args.alloc(sizeof(HopArgs) * count);
   if (s == DD_OK) s = b->item_start.alloc(sizeof(int64_t) * (count + 1));
-  if (s == DD_OK) s = b->counter.alloc(sizeof(unsigned long long));
   if (s == DD_OK && cudaMallocHost((void**)&b->h_args, sizeof(HopArgs) * count) != cudaSuccess) {
     b->h_args = nullptr;
     s = fail(DD_ERR_OOM, "pinned host allocation failed");
   }
-  if (s == DD_OK) b->ctas_per_sm = std::min(4, max_ctas(prec, b->tile));
+  if (s == DD_OK) b->ctas_per_sm = max_ctas(prec, b->tile);
   if (s != DD_OK) {
     delete b;
     return s;
@@ -210,13 +215,13 @@ int dd_batch_tune(dd_batch* b, const void* const* ins, void* const* outs, void* 
   float best = 1e30f;
   int best_tile = b->tile, best_ctas = b->ctas_per_sm;
   const int tiles[3] = {64, 128, 256};
-  const int ctas[5] = {1, 2, 4, 8, 16};
   for (int ti = 0; ti < 3; ++ti) {
     const int cap = max_ctas(b->prec, tiles[ti]);
-    for (int ci = 0; ci < 5; ++ci) {
-      if (ctas[ci] > cap) continue;
+    // persistent shapes at full and reduced residency, then the flat shape
+    const int shapes[4] = {cap, std::max(1, cap - 1), std::max(1, cap / 2), 0};
+    for (int ci = 0; ci < 4; ++ci) {
       b->tile = tiles[ti];
-      b->ctas_per_sm = ctas[ci];
+      b->ctas_per_sm = shapes[ci];
       DD_TRY(stage(b, ins, outs, st));
       DD_TRY(launch(b, st));  // warm-up
       DD_CUDA(cudaEventRecord(e0, st));
@@ -227,8 +232,8 @@ int dd_batch_tune(dd_batch* b, const void* const* ins, void* const* outs, void* 
       DD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
       if (ms < best) {
         best = ms;
-        best_tile = tiles[ti];
-        best_ctas = ctas[ci];
+        best_tile = b->tile;
+        best_ctas = b->ctas_per_sm;
       }
     }
   }

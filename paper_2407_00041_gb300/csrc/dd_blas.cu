@@ -10,6 +10,8 @@
 // fixed-order pass over per-block partials, so results are reproducible).
 // FP32 data is summed in FP32 over short runs of 16 groups per thread
 // before entering the FP64 accumulator.
+#include <algorithm>
+
 #include "dd_blas.h"
 #include "dd_internal.h"
 
@@ -60,6 +62,7 @@ __device__ __forceinline__ void caxpy(float cr, float ci, float4 v, float4& w) {
 }
 
 constexpr int MAXJ = 8;
+constexpr int kMaxCoef = 1024;
 
 // partials[block][j][r] = sum over this block's groups of <V_j, w> for RHS r.
 template <int PV>
@@ -103,42 +106,84 @@ __global__ void __launch_bounds__(256) k_multidot(VecList vs, int J, const void*
   }
 }
 
-// out[j][r] (+)= sum over blocks of partials[block][j][r], fixed order.
-__global__ void k_reduce_partials(const double2* __restrict__ partials, int nblocks, int JN, double2* out, int add) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= JN) return;
+// out[j][r] (+)= sum over blocks of partials[block][j][r]: one CTA per
+// output, a strided pass over the blocks and a fixed-shape tree, so the
+// result does not depend on scheduling.
+__global__ void __launch_bounds__(256) k_reduce_partials(const double2* __restrict__ partials, int nblocks, int JN,
+                                                         double2* out, int add) {
+  __shared__ double sre[256], sim[256];
+  const int i = blockIdx.x;
   double re = 0.0, im = 0.0;
-  for (int b = 0; b < nblocks; ++b) {
-    double2 v = partials[(int64_t)b * JN + i];
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+    const double2 v = partials[(int64_t)b * JN + i];
     re += v.x;
     im += v.y;
   }
-  if (add) {
-    re += out[i].x;
-    im += out[i].y;
+  sre[threadIdx.x] = re;
+  sim[threadIdx.x] = im;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+      sre[threadIdx.x] += sre[threadIdx.x + h];
+      sim[threadIdx.x] += sim[threadIdx.x + h];
+    }
+    __syncthreads();
   }
-  out[i] = make_double2(re, im);
+  if (threadIdx.x == 0) {
+    if (add) {
+      sre[0] += out[i].x;
+      sim[0] += out[i].y;
+    }
+    out[i] = make_double2(sre[0], sim[0]);
+  }
 }
 
-// w = alpha_r * w + sum_j c[j][r] * V_j   (c, alpha complex double [.][N])
+// w += csign * sum_j c[j][r] * V_j; with `partials` set, also the per-RHS
+// |w|^2 of the result (per-block partials, as k_multidot writes them).
 template <int PV>
 __global__ void __launch_bounds__(256) k_multiaxpy(VecList vs, int J, const double2* __restrict__ c, double csign,
-                                                   void* wp, int64_t L, int N) {
+                                                   void* wp, int64_t L, int N, double2* partials) {
   using T = typename G<PV>::group;
   using R = typename G<PV>::real;
+  __shared__ R scr[kMaxCoef], sci[kMaxCoef];  // [J][N] coefficients, J * N <= kMaxCoef
+  __shared__ double sn[256];
   T* w = reinterpret_cast<T*>(wp);
-  const int r = threadIdx.x % N;
-  R cr[32], ci[32];
-  for (int j = 0; j < J; ++j) {
-    double2 cc = c[(int64_t)j * N + r];
-    cr[j] = (R)(csign * cc.x);
-    ci[j] = (R)(csign * cc.y);
+  for (int k = threadIdx.x; k < J * N; k += blockDim.x) {
+    const double2 cc = c[k];
+    scr[k] = (R)(csign * cc.x);
+    sci[k] = (R)(csign * cc.y);
   }
+  __syncthreads();
+  const int r = threadIdx.x % N;
+  double nrm = 0.0;
+  R fn = R(0);
+  int run = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < L; e += stride) {
     T we = w[e];
-    for (int j = 0; j < J; ++j) caxpy(cr[j], ci[j], reinterpret_cast<const T*>(vs.p[j])[e], we);
+    for (int j = 0; j < J; ++j) caxpy(scr[j * N + r], sci[j * N + r], reinterpret_cast<const T*>(vs.p[j])[e], we);
     w[e] = we;
+    if (partials) {
+      if constexpr (PV == P64) {
+        nrm += we.x * we.x + we.y * we.y;
+      } else {
+        fn += we.x * we.x + we.y * we.y + we.z * we.z + we.w * we.w;
+        if (++run == 16) {
+          run = 0;
+          nrm += (double)fn;
+          fn = R(0);
+        }
+      }
+    }
+  }
+  if (!partials) return;
+  nrm += (double)fn;
+  sn[threadIdx.x] = nrm;
+  __syncthreads();
+  if (threadIdx.x < N) {
+    double acc = 0.0;
+    for (int k = 0; k < (int)blockDim.x / N; ++k) acc += sn[threadIdx.x + k * N];
+    partials[(int64_t)blockIdx.x * N + threadIdx.x] = make_double2(acc, 0.0);
   }
 }
 
@@ -231,7 +276,7 @@ int blas_multidot(const VecList& vs, int J, const void* w, int64_t L, int N, dou
     for (int j = 0; j < Jc; ++j) sub.p[j] = vs.p[j0 + j];
     k_multidot<PV><<<grid, block, 0, st>>>(sub, Jc, w, L, N, partials);
     const int JN = Jc * N;
-    k_reduce_partials<<<(JN + 127) / 128, 128, 0, st>>>(partials, grid, JN, dots_dev + (int64_t)j0 * N, add);
+    k_reduce_partials<<<JN, 256, 0, st>>>(partials, grid, JN, dots_dev + (int64_t)j0 * N, add);
   }
   DD_CUDA(cudaGetLastError());
   return DD_OK;
@@ -239,16 +284,21 @@ int blas_multidot(const VecList& vs, int J, const void* w, int64_t L, int N, dou
 
 template <int PV>
 int blas_multiaxpy(const VecList& vs, int J, const double2* c_dev, double csign, void* w, int64_t L, int N,
-                   cudaStream_t st) {
+                   cudaStream_t st, double2* norm_out, double2* partials) {
   const int block = block_for(N);
   if (block <= 0) return fail(DD_ERR_ARG, "too many right-hand sides for the vector kernels");
   const int grid = blas_grid(L, block);
-  for (int j0 = 0; j0 < J; j0 += 32) {
-    const int Jc = J - j0 < 32 ? J - j0 : 32;
+  const int jc = std::max(1, std::min(32, kMaxCoef / N));
+  for (int j0 = 0; j0 < J || (J == 0 && j0 == 0); j0 += jc) {
+    const int Jc = std::min(jc, J - j0);
+    const bool last = j0 + jc >= J;
     VecList sub;
     for (int j = 0; j < Jc; ++j) sub.p[j] = vs.p[j0 + j];
-    k_multiaxpy<PV><<<grid, block, 0, st>>>(sub, Jc, c_dev + (int64_t)j0 * N, csign, w, L, N);
+    k_multiaxpy<PV><<<grid, block, 0, st>>>(sub, Jc, c_dev + (int64_t)j0 * N, csign, w, L, N,
+                                            last && norm_out ? partials : nullptr);
+    if (J == 0) break;
   }
+  if (norm_out) k_reduce_partials<<<N, 256, 0, st>>>(partials, grid, N, norm_out, 0);
   DD_CUDA(cudaGetLastError());
   return DD_OK;
 }
@@ -287,8 +337,10 @@ int blas_add64(const void* in, void* out, int64_t n, cudaStream_t st) {
 
 template int blas_multidot<P64>(const VecList&, int, const void*, int64_t, int, double2*, int, double2*, cudaStream_t);
 template int blas_multidot<P32>(const VecList&, int, const void*, int64_t, int, double2*, int, double2*, cudaStream_t);
-template int blas_multiaxpy<P64>(const VecList&, int, const double2*, double, void*, int64_t, int, cudaStream_t);
-template int blas_multiaxpy<P32>(const VecList&, int, const double2*, double, void*, int64_t, int, cudaStream_t);
+template int blas_multiaxpy<P64>(const VecList&, int, const double2*, double, void*, int64_t, int, cudaStream_t,
+                                 double2*, double2*);
+template int blas_multiaxpy<P32>(const VecList&, int, const double2*, double, void*, int64_t, int, cudaStream_t,
+                                 double2*, double2*);
 template int blas_scale<P64>(const double2*, const void*, void*, int64_t, int, cudaStream_t);
 template int blas_scale<P32>(const double2*, const void*, void*, int64_t, int, cudaStream_t);
 

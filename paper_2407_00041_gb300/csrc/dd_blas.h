@@ -16,10 +16,11 @@ int blas_grid(int64_t L, int block);
 template <int PV>
 int blas_multidot(const VecList& vs, int J, const void* w, int64_t L, int N, double2* dots_dev, int add,
                   double2* partials, cudaStream_t st);
-// w += csign * sum_j c[j][r] V_j
+// w += csign * sum_j c[j][r] V_j (J <= 32); with norm_out, also
+// norm_out[r].x = |w_r|^2 of the result (partials: scratch as for multidot)
 template <int PV>
 int blas_multiaxpy(const VecList& vs, int J, const double2* c_dev, double csign, void* w, int64_t L, int N,
-                   cudaStream_t st);
+                   cudaStream_t st, double2* norm_out = nullptr, double2* partials = nullptr);
 // out = c[r] * in
 template <int PV>
 int blas_scale(const double2* c_dev, const void* in, void* out, int64_t L, int N, cudaStream_t st);

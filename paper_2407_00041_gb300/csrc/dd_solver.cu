@@ -56,6 +56,7 @@ struct Inner {
   size_t vbytes;
   bool normal = false;  // right preconditioner M^{-1} = D^H (Dhat^H)
   int verbose = 0;
+  int gs_passes = 1;    // classical Gram-Schmidt passes per Arnoldi step
   DevBuf basis, w, rvec, tmp, red, partials, coef, zt, ut;
   Pinned hred, hcoef;
   // counters
@@ -110,9 +111,11 @@ struct Inner {
     if (pv == P64) return blas_multidot<P64>(vs, J, x, L, N, out, add, (double2*)partials.ptr, st);
     return blas_multidot<P32>(vs, J, x, L, N, out, add, (double2*)partials.ptr, st);
   }
-  int axpys(const VecList& vs, int J, const double2* c, double sgn, void* x, cudaStream_t st) {
-    if (pv == P64) return blas_multiaxpy<P64>(vs, J, c, sgn, x, L, N, st);
-    return blas_multiaxpy<P32>(vs, J, c, sgn, x, L, N, st);
+  int axpys(const VecList& vs, int J, const double2* c, double sgn, void* x, cudaStream_t st,
+            double2* norm_out = nullptr) {
+    double2* pp = (double2*)partials.ptr;
+    if (pv == P64) return blas_multiaxpy<P64>(vs, J, c, sgn, x, L, N, st, norm_out, pp);
+    return blas_multiaxpy<P32>(vs, J, c, sgn, x, L, N, st, norm_out, pp);
   }
   int scale(const double2* c, const void* in, void* out, cudaStream_t st) {
     if (pv == P64) return blas_scale<P64>(c, in, out, L, N, st);
@@ -184,14 +187,17 @@ struct Inner {
         DD_TRY(apply(V(j), w.ptr, st));  // line 9 (z_j = v_j)
         VecList vs;
         for (int i = 0; i <= j; ++i) vs.p[i] = V(i);
-        // lines 10-13: two passes of classical Gram-Schmidt
+        // lines 10-13: classical Gram-Schmidt (one pass, or two when
+        // gs_passes = 2); the norm of line 14 is fused into the last update
         DD_TRY(dots(vs, j + 1, w.ptr, dots1, 0, st));
-        DD_TRY(axpys(vs, j + 1, dots1, -1.0, w.ptr, st));
-        DD_TRY(dots(vs, j + 1, w.ptr, dots2, 0, st));
-        DD_TRY(axpys(vs, j + 1, dots2, -1.0, w.ptr, st));
-        VecList vw;
-        vw.p[0] = w.ptr;
-        DD_TRY(dots(vw, 1, w.ptr, nrm, 0, st));  // line 14
+        if (gs_passes > 1) {
+          DD_TRY(axpys(vs, j + 1, dots1, -1.0, w.ptr, st));
+          DD_TRY(dots(vs, j + 1, w.ptr, dots2, 0, st));
+          DD_TRY(axpys(vs, j + 1, dots2, -1.0, w.ptr, st, nrm));
+        } else {
+          DD_CUDA(cudaMemsetAsync(dots2, 0, (size_t)(j + 1) * N * sizeof(double2), st));
+          DD_TRY(axpys(vs, j + 1, dots1, -1.0, w.ptr, st, nrm));
+        }
         DD_CUDA(cudaMemcpyAsync(hred.p, dd, (size_t)(2 * (m + 1) + 1) * N * sizeof(double2), cudaMemcpyDeviceToHost,
                                 st));
         DD_CUDA(cudaStreamSynchronize(st));
@@ -324,6 +330,7 @@ int solve(dd_clover* op, const dd_solve_params* prm, const double* b_canon, doub
   if (!op->clov[prec_index(pg)].ptr || !op->gauge->links[prec_index(pg)].ptr)
     return fail(DD_ERR_UNSUPPORTED, "inner precision not created in the handles");
   if (prm->restart < 1 || prm->restart > 32) return fail(DD_ERR_ARG, "restart must be in 1..32");
+  if (prm->gs_passes < 1 || prm->gs_passes > 2) return fail(DD_ERR_ARG, "gs_passes must be 1 or 2");
   const bool eo = prm->even_odd != 0;
   const size_t f64 = field_bytes(lat, P64, 0, N);
   DevBuf b64, x64, r64, r32, fvec, evec, tmp, red, partials;
@@ -352,6 +359,7 @@ int solve(dd_clover* op, const dd_solve_params* prm, const double* b_canon, doub
   Inner inner;
   DD_TRY(inner.init(op, pg, pv, eo, N, prm->restart, prm->precond == DD_PRECOND_NORMAL));
   inner.verbose = prm->verbose;
+  inner.gs_passes = prm->gs_passes;
   dd_stats s{};
   int status = DD_ERR_NOT_CONVERGED;
   for (int outer = 0;; ++outer) {

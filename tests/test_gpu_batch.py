@@ -51,7 +51,7 @@ def test_batched_matches_single_and_oracle(prec):
             assert torch.equal(o, r)  # same kernel body, same arithmetic: bit-identical
         chosen = (ctypes.c_int * 3)()
         dd.check(dd.lib.dd_batch_tune(b, pin, pout, st, chosen), "dd_batch_tune")
-        assert chosen[0] in (64, 128, 256) and chosen[2] >= 1
+        assert chosen[0] in (64, 128, 256) and chosen[2] >= 0  # 0: one CTA per work item
         for o in outs:
             o.zero_()
         dd.check(dd.lib.dd_apply_batched_graph(b, pin, pout, st), "graph capture")

@@ -57,7 +57,7 @@ def test_multi_rhs_solve(sys44):
     dims, U, A, op, b, xref, _ = sys44
     bt = torch.from_numpy(b).cuda()
     x = torch.zeros_like(bt)
-    status, st = op.solve(bt, x, 3, tol=1e-10, inner_prec=dd.DD_PREC_F32, restart=16)
+    status, st = op.solve(bt, x, 3, tol=1e-10, inner_prec=dd.DD_PREC_F32, restart=16, gs_passes=2)
     assert status == 0, st
     xn = x.cpu().numpy()
     for r in range(3):
