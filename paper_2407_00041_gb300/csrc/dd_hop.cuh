@@ -17,6 +17,8 @@
 //   (I + t gamma_mu) psi = (h, t B_mu^H h),  h = u + t B_mu l,  t = +-1.
 #pragma once
 
+#include <cstdlib>
+
 #include "dd_ops.h"
 
 namespace dd {
@@ -247,6 +249,131 @@ __device__ __forceinline__ void hop_thread(const HopArgs& a, int64_t tid) {
   store_spinor<POUT, R>(a.out[p], a.gstride, i, res);
 }
 
+// RHS-blocked variant for several right-hand sides: one thread handles NB
+// right-hand sides r = rb + k * (N / NB), k < NB, of one site, so each link
+// element is loaded once per NB spinors (link reuse across RHS in
+// registers).  The strided RHS choice keeps every load instruction of a warp
+// on consecutive addresses.  EPI_D builds A(x) psi(x) first and folds beta
+// into the hops; EPI_AINV applies the block to beta * acc at the end.  The
+// self-coupling elements are re-read from L1 for each of the NB spinors.
+template <int PG, int R_, int NB>
+__device__ __forceinline__ void block_apply_add(const typename Store<PG>::elem* M, int64_t Vh,
+                                                const cx<typename Store<PG>::real> x[12],
+                                                cx<typename Store<PG>::real> out[12]) {
+  using R = typename Store<PG>::real;
+#pragma unroll
+  for (int b = 0; b < 2; ++b) {
+    const typename Store<PG>::elem* m = M + (int64_t)18 * b * Vh;
+#pragma unroll
+    for (int w = 0; w < 3; ++w) {
+      const cx<R> d = ld_elem<PG>(m + w * Vh);
+      out[6 * b + 2 * w] = out[6 * b + 2 * w] + d.re * x[6 * b + 2 * w];
+      out[6 * b + 2 * w + 1] = out[6 * b + 2 * w + 1] + d.im * x[6 * b + 2 * w + 1];
+    }
+    int e = 3;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = i + 1; j < 6; ++j) {
+        const cx<R> mm = ld_elem<PG>(m + e * Vh);
+        ++e;
+        out[6 * b + i] = cfma(mm, x[6 * b + j], out[6 * b + i]);
+        out[6 * b + j] = cfmac(mm, x[6 * b + i], out[6 * b + j]);
+      }
+  }
+}
+
+template <int PG, int PIN, int POUT, bool DAG, int EPI, int NB>
+__device__ __forceinline__ void hop_thread_rb(const HopArgs& a, int64_t tid) {
+  using R = typename Store<PG>::real;
+  using E = typename Store<PG>::elem;
+  const int nrb = a.nrhs / NB;
+  int p, s, rb;
+  SiteCoord sc;
+  if (a.npar == 2) {
+    const int lex = (int)(tid / nrb);
+    rb = (int)(tid - (int64_t)lex * nrb);
+    sc = lex_coords(a.g, lex);
+    p = (sc.c[0] + sc.c[1] + sc.c[2] + sc.c[3]) & 1;
+    s = lex >> 1;
+  } else {
+    p = a.p0;
+    s = (int)(tid / nrb);
+    rb = (int)(tid - (int64_t)s * nrb);
+    sc = site_coords(a.g, s, p);
+  }
+  const int q = p ^ 1;
+  const int64_t Vh = a.g.Vh;
+  constexpr int TF = DAG ? +1 : -1;
+  constexpr int TB = -TF;
+  const R beta = (R)a.beta;
+  const E* Up = reinterpret_cast<const E*>(a.U[p]);
+  const E* Uq = reinterpret_cast<const E*>(a.U[q]);
+  const E* M = reinterpret_cast<const E*>(a.M[p]) + s;
+  const int64_t ibase = (int64_t)s * a.nrhs + rb;
+
+  cx<R> res[NB][12];
+#pragma unroll
+  for (int k = 0; k < NB; ++k) {
+#pragma unroll
+    for (int c = 0; c < 12; ++c) res[k][c] = zero<R>();
+    if constexpr (EPI == EPI_D) {
+      cx<R> y[12];
+      load_spinor<PIN, R>(a.y[p], a.gstride, ibase + k * nrb, y);
+      block_apply_add<PG, 0, NB>(M, Vh, y, res[k]);
+    }
+  }
+  const R hop_scale = EPI == EPI_D ? beta : (R)1;
+
+#define DD_RB_HOP(MU, FWD)                                                                          \
+  {                                                                                                 \
+    const int nl = FWD ? nb_fwd(a.g, sc, MU) : nb_bwd(a.g, sc, MU);                                 \
+    R sg = hop_scale;                                                                               \
+    if (MU == 0 && sc.c[0] == (FWD ? a.g.n[0] - 1 : 0)) sg = sg * (R)a.g.t_bc;                      \
+    const E* U = FWD ? Up + (int64_t)(MU * 9) * Vh + s : Uq + (int64_t)(MU * 9) * Vh + (nl >> 1);   \
+    cx<R> u[9];                                                                                     \
+    _Pragma("unroll") for (int e = 0; e < 9; ++e) u[e] = ld_elem<PG>(U + e * Vh);                   \
+    const int64_t ib = (int64_t)(nl >> 1) * a.nrhs + rb;                                            \
+    _Pragma("unroll") for (int k = 0; k < NB; ++k) {                                                \
+      cx<R> psi[12];                                                                                \
+      load_spinor<PIN, R>(a.in[q], a.gstride, ib + k * nrb, psi);                                   \
+      hop_regs<MU, FWD ? TF : TB, !FWD, R>(res[k], psi, u, sg);                                     \
+    }                                                                                               \
+  }
+  DD_RB_HOP(0, true)
+  DD_RB_HOP(0, false)
+  DD_RB_HOP(1, true)
+  DD_RB_HOP(1, false)
+  DD_RB_HOP(2, true)
+  DD_RB_HOP(2, false)
+  DD_RB_HOP(3, true)
+  DD_RB_HOP(3, false)
+#undef DD_RB_HOP
+
+#pragma unroll
+  for (int k = 0; k < NB; ++k) {
+    if constexpr (EPI == EPI_AINV) {
+      // out_k = M (beta acc_k)
+#pragma unroll
+      for (int c = 0; c < 12; ++c) res[k][c] = beta * res[k][c];
+      cx<R> out[12];
+#pragma unroll
+      for (int c = 0; c < 12; ++c) out[c] = zero<R>();
+      block_apply_add<PG, 0, NB>(M, Vh, res[k], out);
+      store_spinor<POUT, R>(a.out[p], a.gstride, ibase + k * nrb, out);
+    } else {
+      store_spinor<POUT, R>(a.out[p], a.gstride, ibase + k * nrb, res[k]);
+    }
+  }
+}
+
+template <int PG, int PIN, int POUT, bool DAG, int EPI, int NB>
+__global__ void __launch_bounds__(128, NB >= 4 ? 2 : 3) k_hop_rb(const HopArgs a) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= (int64_t)a.g.Vh * (a.nrhs / NB) * a.npar) return;
+  hop_thread_rb<PG, PIN, POUT, DAG, EPI, NB>(a, tid);
+}
+
 // Memory-bound FP32 / FP16 variants ask for at least 5 resident CTAs of 128
 // threads (at most 102 registers): measured on the 48^3 x 96 lattice this
 // beats the unconstrained 108-register build by about 5%.  FP64 is bound by
@@ -282,6 +409,18 @@ __global__ void __launch_bounds__(128) k_block(const BlockArgs a) {
   store_spinor<POUT, R>(a.out[p], a.gstride, tid, res);
 }
 
+// Largest RHS block of the RHS-blocked stencil (DD_RHS_BLOCK overrides: 1
+// disables it).
+inline int rhs_block_limit() {
+  static int v = 0;
+  if (v == 0) {
+    const char* e = getenv("DD_RHS_BLOCK");
+    v = e ? atoi(e) : 4;
+    if (v < 1) v = 1;
+  }
+  return v;
+}
+
 // Host launchers; the instantiation units explicitly instantiate one
 // precision triple each, other units only see the declarations in dd_ops.h.
 template <int PG, int PIN, int POUT>
@@ -290,6 +429,27 @@ cudaError_t launch_hop(const HopArgs& a, bool dagger, int epi, cudaStream_t st) 
   if (n == 0) return cudaSuccess;
   const int threads = 128;
   const unsigned blocks = (unsigned)((n + threads - 1) / threads);
+  // several right-hand sides: RHS-blocked variant (not for FP64, which is
+  // bound by the FP64 pipe, nor for the residual / add epilogues)
+  const int rbmax = rhs_block_limit();
+  if (PG != P64 && rbmax >= 2 && (epi == EPI_D || epi == EPI_AINV) && a.nrhs >= 2 && a.nrhs % 2 == 0) {
+    // measured on 32^4: blocks of 4 win from 16 RHS up, blocks of 2 below
+    const int NBsel = (a.nrhs % 4 == 0 && a.nrhs >= 16 && rbmax >= 4) ? 4 : 2;
+    const int64_t nt = (int64_t)a.g.Vh * (a.nrhs / NBsel) * a.npar;
+    const unsigned bl = (unsigned)((nt + threads - 1) / threads);
+    const int key = (epi == EPI_D ? 0 : 4) + (dagger ? 2 : 0) + (NBsel == 4 ? 1 : 0);
+    switch (key) {
+      case 0: k_hop_rb<PG, PIN, POUT, false, EPI_D, 2><<<bl, threads, 0, st>>>(a); break;
+      case 1: k_hop_rb<PG, PIN, POUT, false, EPI_D, 4><<<bl, threads, 0, st>>>(a); break;
+      case 2: k_hop_rb<PG, PIN, POUT, true, EPI_D, 2><<<bl, threads, 0, st>>>(a); break;
+      case 3: k_hop_rb<PG, PIN, POUT, true, EPI_D, 4><<<bl, threads, 0, st>>>(a); break;
+      case 4: k_hop_rb<PG, PIN, POUT, false, EPI_AINV, 2><<<bl, threads, 0, st>>>(a); break;
+      case 5: k_hop_rb<PG, PIN, POUT, false, EPI_AINV, 4><<<bl, threads, 0, st>>>(a); break;
+      case 6: k_hop_rb<PG, PIN, POUT, true, EPI_AINV, 2><<<bl, threads, 0, st>>>(a); break;
+      default: k_hop_rb<PG, PIN, POUT, true, EPI_AINV, 4><<<bl, threads, 0, st>>>(a); break;
+    }
+    return cudaGetLastError();
+  }
   switch (epi * 2 + (dagger ? 1 : 0)) {
     case EPI_D * 2:
       k_hop<PG, PIN, POUT, false, EPI_D><<<blocks, threads, 0, st>>>(a);

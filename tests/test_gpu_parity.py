@@ -39,7 +39,7 @@ def test_clover_matches_oracle(system):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("nrhs", [1, 3])
+@pytest.mark.parametrize("nrhs", [1, 3, 4, 6])
 def test_D_and_DH(system, prec, nrhs):
     dims, U, A, op, _ = system
     psi = synthetic.spinor(dims, nrhs=nrhs)
@@ -63,10 +63,10 @@ def test_self_coupling(system, prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_Dhat(system, prec):
+@pytest.mark.parametrize("nrhs", [1, 2, 4])
+def test_Dhat(system, prec, nrhs):
     dims, U, A, op, _ = system
     eo = oracle.EvenOdd(U, A, dims)
-    nrhs = 2
     full = synthetic.spinor(dims, nrhs=nrhs)
     v = np.stack([full[r].reshape(-1, 12)[eo.odd] for r in range(nrhs)])
     got = apply(op, dd.DD_OP_DHAT, prec, v)
