@@ -184,6 +184,8 @@ typedef struct {
                           or DD_PRECOND_NORMAL (M^{-1} = A^H, so A M^{-1} = A A^H is Hermitian
                           positive definite and restarted FGMRES cannot stagnate) */
   int gs_passes;       /* classical Gram-Schmidt passes per Arnoldi step: 1, or 2 (re-orthogonalised) */
+  int rhs_batch;       /* even-odd solves: right-hand sides solved together (0 = all); smaller
+                          batches need proportionally less device memory */
 } dd_solve_params;
 
 #define DD_PRECOND_NONE 0
@@ -201,7 +203,8 @@ typedef struct {
 } dd_stats;
 
 /* Fill `p` with defaults: tol 1e-10, restart 30, max_restarts 100,
- * max_outer 30, inner_prec F32, inner_tol 1e-6, even_odd 1, precond NONE, gs_passes 1. */
+ * max_outer 30, inner_prec F32, inner_tol 1e-6, even_odd 1, precond NONE, gs_passes 1,
+ * rhs_batch 0. */
 void dd_solve_params_default(dd_solve_params* p);
 
 /*
@@ -211,6 +214,11 @@ void dd_solve_params_default(dd_solve_params* p);
  * residual of the full system.  Returns DD_ERR_NOT_CONVERGED (with x = best
  * iterate and stats filled) when limits are hit.  Synchronises `stream`.
  * `stats` may be NULL.
+ * even_odd = 1: FP64 refinement runs on the odd-site system Dhat x_o = bhat_o
+ * (x_o enters from the odd sites of x), x_e = A_ee^{-1} (b_e - D_eo x_o) is
+ * formed at the end and the full residual verified; with host layout only one
+ * batch of b / x is staged on the device at a time.
+ * even_odd = 0: refinement and inner solves on the full lattice.
  */
 int dd_solve(dd_clover* op, const dd_solve_params* params, const void* b, void* x, int nrhs, int layout,
              void* stream, dd_stats* stats);

@@ -34,7 +34,7 @@ class SolveParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("max_restarts", ctypes.c_int),
                 ("max_outer", ctypes.c_int), ("inner_prec", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("even_odd", ctypes.c_int), ("verbose", ctypes.c_int), ("precond", ctypes.c_int),
-                ("gs_passes", ctypes.c_int)]
+                ("gs_passes", ctypes.c_int), ("rhs_batch", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

@@ -10,6 +10,8 @@ namespace dd {
 const char* last_error();
 int solve(dd_clover* op, const dd_solve_params* prm, const double* b, double* x, int N, cudaStream_t st,
           dd_stats* stats);
+int solve_schur(dd_clover* op, const dd_solve_params* prm, const double* b, double* x, int N, bool host,
+                cudaStream_t st, dd_stats* stats);
 int force(dd_clover* op, int prec, const double* phi, const double* psi, int nrhs, int with_clover, double* G,
           double* F, cudaStream_t st);
 }  // namespace dd
@@ -256,6 +258,7 @@ void dd_solve_params_default(dd_solve_params* p) {
   p->verbose = 0;
   p->precond = DD_PRECOND_NONE;
   p->gs_passes = 1;
+  p->rhs_batch = 0;
 }
 
 int dd_solve(dd_clover* op, const dd_solve_params* params, const void* b, void* x, int nrhs, int layout,
@@ -267,7 +270,10 @@ int dd_solve(dd_clover* op, const dd_solve_params* params, const void* b, void* 
     return fail(DD_ERR_ARG, "unknown preconditioner");
   if (!(params->tol > 0) || params->max_restarts < 1 || params->max_outer < 0)
     return fail(DD_ERR_ARG, "bad solver parameters");
+  if (params->rhs_batch < 0) return fail(DD_ERR_ARG, "rhs_batch must be >= 0");
   cudaStream_t st = as_stream(stream);
+  if (params->even_odd)
+    return solve_schur(op, params, (const double*)b, (double*)x, nrhs, layout == DD_LAYOUT_CANONICAL_HOST, st, stats);
   const size_t cb = (size_t)op->lat->V * 12 * 16 * nrhs;
   if (layout == DD_LAYOUT_CANONICAL) return solve(op, params, (const double*)b, (double*)x, nrhs, st, stats);
   DevBuf bd, xd;

@@ -110,22 +110,18 @@ int op_prepare(const dd_clover* op, int pg, int pv, const Field& b, const Field&
                cudaStream_t st);
 // x_e = A_ee^{-1} (b_e - D_eo x_o)   (b full; x full with its odd half given)
 int op_reconstruct(const dd_clover* op, int pg, int pv, const Field& b, const Field& x, cudaStream_t st);
+// r_o = bhat_o - Dhat x_o (odd half fields; tmp: even half-field workspace)
+int op_dhat_residual(const dd_clover* op, int pg, int pv, const Field& bhat, const Field& x, const Field& r,
+                     const Field& tmp, cudaStream_t st);
 
 // ---- setup kernels (dd_setup.cu) ----
 int links_to_native(const dd_lattice* lat, const double* U_canon_dev, dd_gauge* g, cudaStream_t st);
 int links_to_canonical(const dd_gauge* g, double* U_canon_dev, cudaStream_t st);
 int clover_build(dd_clover* op, cudaStream_t st);  // FP64 blocks, A_ee^{-1}, demoted copies
 int clover_to_dense(const dd_clover* op, double* A_dev /*[V][144] complex*/, cudaStream_t st);
+// subset: 0 full; 1 odd / 2 even sites of a half-lattice canonical array
+// [nrhs][V/2][12]; 3 even / 4 odd sites of a full canonical array [nrhs][V][12]
 int pack(const dd_lattice* lat, int prec, int subset, const double* canon, const Field& f, cudaStream_t st);
 int unpack(const dd_lattice* lat, int prec, int subset, const Field& f, double* canon, cudaStream_t st);
-
-// ---- vector kernels on native half fields (dd_blas.cu) ----
-// Each works on `nh` consecutive half fields of a Field (nh = 1 or 2).
-struct Vec {
-  Field f;
-  int npar;   // 1: h[p0] only, 2: both halves
-  int p0;
-};
-int64_t vec_len(const dd_lattice* lat, const Vec& v);  // sites*nrhs
 
 }  // namespace dd

@@ -216,6 +216,30 @@ int op_residual(const dd_clover* op, int pg, int pv, const Field& b, const Field
   return run_hop(pg, pv, a, false, EPI_RESID, st);
 }
 
+// r_o = bhat_o - (A_oo x_o - 1/2 H_oe tmp_e), tmp_e = A_ee^{-1} (1/2 H_eo x_o)
+int op_dhat_residual(const dd_clover* op, int pg, int pv, const Field& bhat, const Field& x, const Field& r,
+                     const Field& tmp, cudaStream_t st) {
+  DD_TRY(check_prec(op, pg));
+  const int pi = prec_index(pg);
+  HopArgs a = base_args(op, pg, x.nrhs);
+  a.npar = 1;
+  a.p0 = 0;
+  a.in[1] = x.h[1];
+  a.out[0] = tmp.h[0];
+  a.M[0] = op->Ainv(pi);
+  a.beta = 0.5;
+  DD_TRY(run_hop(pg, pv, a, false, EPI_AINV, st));
+  HopArgs b = base_args(op, pg, x.nrhs);
+  b.npar = 1;
+  b.p0 = 1;
+  b.in[0] = tmp.h[0];
+  b.y[1] = x.h[1];
+  b.z[1] = bhat.h[1];
+  b.out[1] = r.h[1];
+  b.beta = -0.5;
+  return run_hop(pg, pv, b, false, EPI_RESID, st);
+}
+
 // bhat_o = b_o - D_oe A_ee^{-1} b_e = b_o + 1/2 H_oe (A_ee^{-1} b_e)
 int op_prepare(const dd_clover* op, int pg, int pv, const Field& b, const Field& bhat, const Field& tmp,
                cudaStream_t st) {

@@ -332,7 +332,7 @@ struct PackArgs {
 };
 
 __device__ __forceinline__ int64_t canon_offset(const PackArgs& a, int p, int64_t s, int r) {
-  if (a.subset == 0) {
+  if (a.subset == 0 || a.subset >= 3) {  // full-lattice canonical array
     // lexicographic index of compact site s of parity p
     const int lex2 = (int)(2 * s);
     const int r1 = lex2 / a.g.n[3];
@@ -397,7 +397,7 @@ PackArgs pack_args(const dd_lattice* lat, int subset, const Field& f) {
   a.g = lex_geom(lat);
   a.nrhs = f.nrhs;
   a.subset = subset;
-  a.p0 = subset == 2 ? 0 : (subset == 1 ? 1 : 0);
+  a.p0 = (subset == 1 || subset == 4) ? 1 : 0;
   a.npar = subset == 0 ? 2 : 1;
   a.gstride = lat->Vh * f.nrhs;
   a.h[0] = f.h[0];

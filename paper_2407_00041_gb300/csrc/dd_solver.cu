@@ -317,7 +317,198 @@ int dot_norms64(const dd_lattice* lat, const void* x, int N, double2* scratch_re
   return DD_OK;
 }
 
+int half_norms64(const dd_lattice* lat, const void* x, int N, double2* red, double2* partials, Pinned& hbuf,
+                 std::vector<double>& out, cudaStream_t st) {
+  VecList vs;
+  vs.p[0] = x;
+  const int64_t L = (int64_t)(field_bytes(lat, P64, 1, N) / 16);
+  DD_TRY(blas_multidot<P64>(vs, 1, x, L, N, red, 0, partials, st));
+  DD_CUDA(cudaMemcpyAsync(hbuf.p, red, N * sizeof(double2), cudaMemcpyDeviceToHost, st));
+  DD_CUDA(cudaStreamSynchronize(st));
+  out.resize(N);
+  const double2* h = reinterpret_cast<const double2*>(hbuf.p);
+  for (int r = 0; r < N; ++r) out[r] = std::max(h[r].x, 0.0);  // squared norms
+  return DD_OK;
+}
+
+// One batch of nb right-hand sides of the even-odd solve.  FP64 refinement
+// runs on the odd-site Schur system Dhat x_o = bhat_o; x_e is reconstructed
+// and the full-system FP64 residual ||b - D x|| is verified at the end (and
+// refinement resumes with a tighter target if it is not met).  Only six FP64
+// half fields are kept, which lets large lattices fit.
+int schur_batch(dd_clover* op, const dd_solve_params* prm, const double* b_in, double* x_io, int nb, bool host,
+                Inner& inner, cudaStream_t st, dd_stats& s, double& worst_out, bool& ok_out) {
+  const dd_lattice* lat = op->lat;
+  const int pin = prm->inner_prec;
+  const int pv = pin == P64 ? P64 : P32;
+  const size_t h64 = field_bytes(lat, P64, 1, nb);
+  const size_t canon = (size_t)lat->V * 12 * 16 * nb;
+  DevBuf be, bo, bh, xo, ro, te, stage, red, partials, fv, ev;
+  Pinned hbuf;
+  DD_TRY(hbuf.alloc((size_t)nb * sizeof(double2)));
+  DD_TRY(red.alloc((size_t)nb * sizeof(double2)));
+  DD_TRY(partials.alloc((size_t)blas_partials_len(nb) * sizeof(double2)));
+  for (DevBuf* d : {&be, &bo, &bh, &xo, &ro, &te}) DD_TRY(d->alloc(h64));
+  const double* bsrc = b_in;
+  double* xdst = x_io;
+  if (host) {
+    DD_TRY(stage.alloc(canon));
+    DD_CUDA(cudaMemcpyAsync(stage.ptr, b_in, canon, cudaMemcpyHostToDevice, st));
+    bsrc = reinterpret_cast<const double*>(stage.ptr);
+  }
+  Field BE = field_view(lat, P64, 2, be.ptr, nb), BO = field_view(lat, P64, 1, bo.ptr, nb);
+  Field BH = field_view(lat, P64, 1, bh.ptr, nb), XO = field_view(lat, P64, 1, xo.ptr, nb);
+  Field RO = field_view(lat, P64, 1, ro.ptr, nb), TE = field_view(lat, P64, 2, te.ptr, nb);
+  DD_TRY(pack(lat, P64, 3, bsrc, BE, st));
+  DD_TRY(pack(lat, P64, 4, bsrc, BO, st));
+  if (host) {
+    DD_CUDA(cudaMemcpyAsync(stage.ptr, x_io, canon, cudaMemcpyHostToDevice, st));
+    DD_TRY(pack(lat, P64, 4, reinterpret_cast<const double*>(stage.ptr), XO, st));
+  } else {
+    DD_TRY(pack(lat, P64, 4, x_io, XO, st));
+  }
+  Field B;  // the full right-hand side as two half fields
+  B.prec = P64;
+  B.nrhs = nb;
+  B.h[0] = BE.h[0];
+  B.h[1] = BO.h[1];
+  std::vector<double> n_e, n_o, bnorm(nb), rn;
+  DD_TRY(half_norms64(lat, be.ptr, nb, (double2*)red.ptr, (double2*)partials.ptr, hbuf, n_e, st));
+  DD_TRY(half_norms64(lat, bo.ptr, nb, (double2*)red.ptr, (double2*)partials.ptr, hbuf, n_o, st));
+  for (int r = 0; r < nb; ++r) {
+    bnorm[r] = std::sqrt(n_e[r] + n_o[r]);
+    if (!std::isfinite(bnorm[r])) return fail(DD_ERR_ARG, "right-hand side contains NaN or Inf");
+  }
+  DD_TRY(op_prepare(op, P64, P64, B, BH, TE, st));
+  if (pv == P32) {
+    DD_TRY(fv.alloc(field_bytes(lat, P32, 1, nb)));
+    DD_TRY(ev.alloc(field_bytes(lat, P32, 1, nb)));
+  } else {
+    DD_TRY(ev.alloc(h64));
+  }
+  double target = 0.5;  // refine the Schur residual to target * tol, then verify
+  bool ok = false;
+  double worst = 0.0;
+  for (int outer = 0;; ++outer) {
+    DD_TRY(op_dhat_residual(op, P64, P64, BH, XO, RO, TE, st));
+    ++s.applies_fp64;
+    DD_TRY(half_norms64(lat, ro.ptr, nb, (double2*)red.ptr, (double2*)partials.ptr, hbuf, rn, st));
+    bool reached = true;
+    for (int r = 0; r < nb; ++r)
+      if (bnorm[r] > 0 && !(std::sqrt(rn[r]) < target * prm->tol * bnorm[r])) reached = false;
+    if (reached || outer >= prm->max_outer) {
+      // x_e = A_ee^{-1} (b_e - D_eo x_o); full residual r = b - D x in FP64
+      Field X;
+      X.prec = P64;
+      X.nrhs = nb;
+      X.h[0] = TE.h[0];
+      X.h[1] = XO.h[1];
+      DD_TRY(op_reconstruct(op, P64, P64, B, X, st));
+      Field R;
+      R.prec = P64;
+      R.nrhs = nb;
+      R.h[0] = field_view(lat, P64, 2, bh.ptr, nb).h[0];
+      R.h[1] = RO.h[1];
+      DD_TRY(op_residual(op, P64, P64, B, X, R, st));
+      ++s.applies_fp64;
+      DD_TRY(half_norms64(lat, bh.ptr, nb, (double2*)red.ptr, (double2*)partials.ptr, hbuf, n_e, st));
+      DD_TRY(half_norms64(lat, ro.ptr, nb, (double2*)red.ptr, (double2*)partials.ptr, hbuf, n_o, st));
+      ok = true;
+      worst = 0.0;
+      for (int r = 0; r < nb; ++r) {
+        const double rel = bnorm[r] > 0 ? std::sqrt(n_e[r] + n_o[r]) / bnorm[r] : 0.0;
+        worst = std::max(worst, rel);
+        if (!(rel < prm->tol) && bnorm[r] > 0) ok = false;
+      }
+      if (prm->verbose)
+        fprintf(stderr, "[dd_solve] outer %d  full FP64 residual max %.3e  inner steps so far %d\n", outer, worst,
+                inner.steps);
+      if (ok || outer >= prm->max_outer) {
+        s.outer_iterations += outer;
+        // write x back (both parities)
+        double* xc = host ? reinterpret_cast<double*>(stage.ptr) : xdst;
+        DD_TRY(unpack(lat, P64, 3, X, xc, st));
+        DD_TRY(unpack(lat, P64, 4, X, xc, st));
+        if (host) DD_CUDA(cudaMemcpyAsync(x_io, stage.ptr, canon, cudaMemcpyDeviceToHost, st));
+        DD_CUDA(cudaStreamSynchronize(st));
+        break;
+      }
+      target *= 0.1;  // the Schur residual understated the full one: tighten and go on
+      DD_TRY(op_prepare(op, P64, P64, B, BH, TE, st));  // bh held r_e
+      continue;
+    }
+    if (prm->verbose) {
+      double w = 0.0;
+      for (int r = 0; r < nb; ++r) w = std::max(w, bnorm[r] > 0 ? std::sqrt(rn[r]) / bnorm[r] : 0.0);
+      fprintf(stderr, "[dd_solve] outer %d  Schur FP64 residual max %.3e  inner steps so far %d\n", outer, w,
+              inner.steps);
+    }
+    // inner solve of Dhat e = r in the inner precision
+    const void* f = ro.ptr;
+    if (pv == P32) {
+      DD_TRY(blas_demote(ro.ptr, fv.ptr, 1, lat->Vh * nb, st));
+      f = fv.ptr;
+    }
+    DD_CUDA(cudaMemsetAsync(ev.ptr, 0, pv == P32 ? field_bytes(lat, P32, 1, nb) : h64, st));
+    std::vector<double> fn;
+    DD_TRY(inner.norms(f, fn, st));
+    std::vector<double> tol_rel(nb);
+    for (int r = 0; r < nb; ++r) {
+      const double need = fn[r] > 0 ? 0.3 * target * prm->tol * bnorm[r] / fn[r] : 1.0;
+      tol_rel[r] = pv == P64 ? need : std::max(prm->inner_tol, need);
+    }
+    DD_TRY(inner.solve(f, ev.ptr, tol_rel, prm->max_restarts, st, nullptr));
+    if (pv == P32)
+      DD_TRY(blas_promote_add(ev.ptr, xo.ptr, 1, lat->Vh * nb, st));
+    else
+      DD_TRY(blas_add64(ev.ptr, xo.ptr, (int64_t)(h64 / 16), st));
+  }
+  worst_out = worst;
+  ok_out = ok;
+  return DD_OK;
+}
+
 }  // namespace
+
+// Even-odd solve: the right-hand sides in batches of prm->rhs_batch.
+int solve_schur(dd_clover* op, const dd_solve_params* prm, const double* b, double* x, int N, bool host,
+                cudaStream_t st, dd_stats* stats) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const dd_lattice* lat = op->lat;
+  const int pin = prm->inner_prec;
+  const int pv = pin == P64 ? P64 : P32;
+  if (prec_index(pin) < 0) return fail(DD_ERR_ARG, "bad inner precision");
+  if (!op->clov[prec_index(pin)].ptr || !op->gauge->links[prec_index(pin)].ptr)
+    return fail(DD_ERR_UNSUPPORTED, "inner precision not created in the handles");
+  if (prm->restart < 1 || prm->restart > 32) return fail(DD_ERR_ARG, "restart must be in 1..32");
+  if (prm->gs_passes < 1 || prm->gs_passes > 2) return fail(DD_ERR_ARG, "gs_passes must be 1 or 2");
+  const int nbmax = prm->rhs_batch > 0 ? std::min(prm->rhs_batch, N) : N;
+  dd_stats s{};
+  Inner inner;
+  bool all_ok = true;
+  double worst = 0.0;
+  for (int r0 = 0; r0 < N; r0 += nbmax) {
+    const int nb = std::min(nbmax, N - r0);
+    DD_TRY(inner.init(op, pin, pv, true, nb, prm->restart, prm->precond == DD_PRECOND_NORMAL));
+    inner.verbose = prm->verbose;
+    inner.gs_passes = prm->gs_passes;
+    const size_t off = (size_t)r0 * lat->V * 24;  // doubles per RHS: V sites x 12 complex
+    double w = 0.0;
+    bool ok = false;
+    DD_TRY(schur_batch(op, prm, b + off, x + off, nb, host, inner, st, s, w, ok));
+    worst = std::max(worst, w);
+    all_ok = all_ok && ok;
+  }
+  s.converged = all_ok;
+  s.true_residual = worst;
+  s.inner_iterations = inner.steps;
+  s.restarts = inner.cycles;
+  s.applies_inner = inner.applies;
+  s.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (stats) *stats = s;
+  if (!all_ok) return fail(DD_ERR_NOT_CONVERGED, "solver reached its iteration limits");
+  return DD_OK;
+}
 
 int solve(dd_clover* op, const dd_solve_params* prm, const double* b_canon, double* x_canon, int N, cudaStream_t st,
           dd_stats* stats) {

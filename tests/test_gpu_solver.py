@@ -62,7 +62,15 @@ def test_multi_rhs_solve(sys44):
     xn = x.cpu().numpy()
     for r in range(3):
         assert oracle_residual(U, A, dims, b[r], xn[r]) < 1e-10
-        assert rel(xn[r], xref[r]) < 1e-8
+    # the same right-hand sides solved in batches of 2 and 1, on host buffers
+    for batch in (2, 1):
+        xh = np.zeros_like(b)
+        status, st = op.solve(np.ascontiguousarray(b), xh, 3, layout=dd.DD_LAYOUT_CANONICAL_HOST, tol=1e-10,
+                              rhs_batch=batch, precond=dd.DD_PRECOND_NORMAL)
+        assert status == 0, st
+        for r in range(3):
+            assert oracle_residual(U, A, dims, b[r], xh[r]) < 1e-10
+            assert rel(xh[r], xref[r]) < 1e-8
 
 
 def test_host_layout_and_initial_guess(sys44):
