@@ -75,7 +75,7 @@ int stage(dd_batch* b, const void* const* ins, void* const* outs, cudaStream_t s
     const dd_clover* op = b->ops[i];
     const dd_lattice* lat = op->lat;
     HopArgs& a = b->h_args[i];
-    a.g = lat->geom();
+    a.g = lat->geom();  // lexicographic traversal: the batch mixes lattices of all sizes
     a.nrhs = b->nrhs[i];
     a.p0 = 0;
     a.npar = 2;

@@ -256,6 +256,7 @@ struct Geom {
   int stride[4];  // lexicographic strides of T, Z, Y, X
   int Vh;         // sites per parity
   float t_bc;     // sign of hops across the time boundary
+  int zblock;     // traversal of full-lattice launches: Z-slabs of this depth (divides nZ)
 };
 
 struct SiteCoord {
@@ -286,6 +287,28 @@ __device__ __forceinline__ SiteCoord lex_coords(const Geom& g, int lex) {
   sc.c[2] = r1 - r2 * g.n[2];
   sc.c[0] = r2 / g.n[1];
   sc.c[1] = r2 - sc.c[0] * g.n[1];
+  return sc;
+}
+
+// Traversal order of full-lattice launches: slab b of `zblock` Z-planes is
+// walked time slice by time slice, X fastest:
+//   k = (((b * nT + t) * zblock + zz) * nY + y) * nX + x,  z = b * zblock + zz.
+// Consecutive threads still cover consecutive sites of an X-row, while the
+// hops to t +- 1 find their data after one slab-slice of traffic
+// (zblock * nY * nX sites) instead of a whole time slice, which keeps that
+// reuse inside L2 on large lattices.
+__device__ __forceinline__ SiteCoord traversal_coords(const Geom& g, int k) {
+  SiteCoord sc;
+  int r = k / g.n[3];
+  sc.c[3] = k - r * g.n[3];
+  int r2 = r / g.n[2];
+  sc.c[2] = r - r2 * g.n[2];
+  r = r2 / g.zblock;
+  const int zz = r2 - r * g.zblock;
+  r2 = r / g.n[0];
+  sc.c[0] = r - r2 * g.n[0];
+  sc.c[1] = r2 * g.zblock + zz;
+  sc.lex = ((sc.c[0] * g.n[1] + sc.c[1]) * g.n[2] + sc.c[2]) * g.n[3] + sc.c[3];
   return sc;
 }
 

@@ -163,9 +163,9 @@ __device__ __forceinline__ void hop_thread(const HopArgs& a, int64_t tid) {
     // reads of a neighbour spinor fall within about one time slice of traffic
     const int lex = (int)(tid / a.nrhs);
     r = (int)(tid - (int64_t)lex * a.nrhs);
-    sc = lex_coords(a.g, lex);
+    sc = traversal_coords(a.g, lex);
     p = (sc.c[0] + sc.c[1] + sc.c[2] + sc.c[3]) & 1;
-    s = lex >> 1;
+    s = sc.lex >> 1;
   } else {
     p = a.p0;
     s = (int)(tid / a.nrhs);
@@ -293,9 +293,9 @@ __device__ __forceinline__ void hop_thread_rb(const HopArgs& a, int64_t tid) {
   if (a.npar == 2) {
     const int lex = (int)(tid / nrb);
     rb = (int)(tid - (int64_t)lex * nrb);
-    sc = lex_coords(a.g, lex);
+    sc = traversal_coords(a.g, lex);
     p = (sc.c[0] + sc.c[1] + sc.c[2] + sc.c[3]) & 1;
-    s = lex >> 1;
+    s = sc.lex >> 1;
   } else {
     p = a.p0;
     s = (int)(tid / nrb);
