@@ -89,6 +89,29 @@ Field field_view(const dd_lattice* lat, int prec, int subset, void* base, int nr
 // ---------------------------------------------------------------- dispatch
 namespace {
 
+// Depth of the Z-slabs of the full-lattice traversal: the largest divisor of
+// nZ whose slab-slice (depth * nY * nX sites) moves at most ~30 MB through the
+// stencil (bytes_per_site per site), well inside L2; DD_ZBLOCK overrides
+// (0 = no slabs).  Measured at 48^3 x 96: 16 for FP32 with one RHS (+4%);
+// at 32^4 with 12 RHS: 8 (+13%).
+int zblock_for(const int dims[4], int64_t bytes_per_site) {
+  static int forced = -2;
+  if (forced == -2) {
+    const char* e = getenv("DD_ZBLOCK");
+    forced = e ? atoi(e) : -1;
+  }
+  const int nZ = dims[1];
+  const int64_t plane = (int64_t)dims[2] * dims[3];
+  if (forced == 0) return nZ;
+  if (forced > 0 && nZ % forced == 0) return forced;
+  const int64_t budget = 30000000;
+  int best = 1;
+  for (int b = 1; b <= nZ; ++b)
+    if (nZ % b == 0 && b * plane * bytes_per_site <= budget) best = b;
+  return best;
+}
+
+
 int run_hop(int pg, int pv, const HopArgs& a, bool dag, int epi, cudaStream_t st) {
   cudaError_t e;
   if (pg == P64 && pv == P64)
@@ -290,28 +313,6 @@ int op_reconstruct(const dd_clover* op, int pg, int pv, const Field& b, const Fi
 }  // namespace dd
 
 // ---------------------------------------------------------------- handles
-// Depth of the Z-slabs of the full-lattice traversal: the largest divisor of
-// nZ whose slab-slice (depth * nY * nX sites) moves at most ~30 MB through the
-// stencil (bytes_per_site per site), well inside L2; DD_ZBLOCK overrides
-// (0 = no slabs).  Measured at 48^3 x 96: 16 for FP32 with one RHS (+4%);
-// at 32^4 with 12 RHS: 8 (+13%).
-static int zblock_for(const int dims[4], int64_t bytes_per_site) {
-  static int forced = -2;
-  if (forced == -2) {
-    const char* e = getenv("DD_ZBLOCK");
-    forced = e ? atoi(e) : -1;
-  }
-  const int nZ = dims[1];
-  const int64_t plane = (int64_t)dims[2] * dims[3];
-  if (forced == 0) return nZ;
-  if (forced > 0 && nZ % forced == 0) return forced;
-  const int64_t budget = 30000000;
-  int best = 1;
-  for (int b = 1; b <= nZ; ++b)
-    if (nZ % b == 0 && b * plane * bytes_per_site <= budget) best = b;
-  return best;
-}
-
 dd::Geom dd_lattice::geom() const {
   dd::Geom g;
   g.zblock = dims[1];
