@@ -180,16 +180,19 @@ typedef struct {
   double inner_tol;    /* relative residual reduction asked of each inner solve, e.g. 1e-6 */
   int even_odd;        /* 1: inner solves use Dhat on odd sites; 0: D on the full lattice */
   int verbose;         /* 1: print progress lines to stderr */
-  int precond;         /* right preconditioner M^{-1} of Algorithm 2: DD_PRECOND_NONE (M = I)
-                          or DD_PRECOND_NORMAL (M^{-1} = A^H, so A M^{-1} = A A^H is Hermitian
-                          positive definite and restarted FGMRES cannot stagnate) */
+  int precond;         /* preconditioner M_j of Algorithm 2: DD_PRECOND_NONE (M = I),
+                          DD_PRECOND_NORMAL (M^{-1} = A^H, so A M^{-1} = A A^H is Hermitian
+                          positive definite and restarted FGMRES cannot stagnate) or
+                          DD_PRECOND_CGNR (flexible: CG steps on the normal equations) */
   int gs_passes;       /* classical Gram-Schmidt passes per Arnoldi step: 1, or 2 (re-orthogonalised) */
   int rhs_batch;       /* even-odd solves: right-hand sides solved together (0 = all); smaller
                           batches need proportionally less device memory */
+  int precond_iters;   /* DD_PRECOND_CGNR: conjugate-gradient steps per preconditioner application */
 } dd_solve_params;
 
 #define DD_PRECOND_NONE 0
 #define DD_PRECOND_NORMAL 1
+#define DD_PRECOND_CGNR 2  /* flexible M_j: precond_iters CG steps on A^H A z = A^H v_j */
 
 typedef struct {
   int converged;             /* 1 if every right-hand side met tol */
@@ -204,7 +207,7 @@ typedef struct {
 
 /* Fill `p` with defaults: tol 1e-10, restart 30, max_restarts 100,
  * max_outer 30, inner_prec F32, inner_tol 1e-6, even_odd 1, precond NONE, gs_passes 1,
- * rhs_batch 0. */
+ * rhs_batch 0, precond_iters 32. */
 void dd_solve_params_default(dd_solve_params* p);
 
 /*

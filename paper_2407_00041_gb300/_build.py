@@ -67,7 +67,7 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
         objs = list(ex.map(compile_one, sources()))
     fd, tmp = tempfile.mkstemp(suffix=".so", dir=HERE)
     os.close(fd)
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"]
+    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static", "-Xlinker", "--no-undefined"]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         os.unlink(tmp)

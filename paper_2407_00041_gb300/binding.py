@@ -18,7 +18,7 @@ DD_PREC_F64, DD_PREC_F32, DD_PREC_F16 = 1, 2, 4
 DD_OP_D, DD_OP_DH, DD_OP_DHAT, DD_OP_DHAT_H, DD_OP_SC = 0, 1, 2, 3, 4
 DD_LAYOUT_CANONICAL, DD_LAYOUT_CANONICAL_HOST, DD_LAYOUT_NATIVE = 0, 1, 2
 
-DD_PRECOND_NONE, DD_PRECOND_NORMAL = 0, 1
+DD_PRECOND_NONE, DD_PRECOND_NORMAL, DD_PRECOND_CGNR = 0, 1, 2
 PREC = {"f64": DD_PREC_F64, "f32": DD_PREC_F32, "f16": DD_PREC_F16}
 OPS = {"D": DD_OP_D, "DH": DD_OP_DH, "DHAT": DD_OP_DHAT, "DHAT_H": DD_OP_DHAT_H, "SC": DD_OP_SC}
 
@@ -34,7 +34,7 @@ class SolveParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("max_restarts", ctypes.c_int),
                 ("max_outer", ctypes.c_int), ("inner_prec", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("even_odd", ctypes.c_int), ("verbose", ctypes.c_int), ("precond", ctypes.c_int),
-                ("gs_passes", ctypes.c_int), ("rhs_batch", ctypes.c_int)]
+                ("gs_passes", ctypes.c_int), ("rhs_batch", ctypes.c_int), ("precond_iters", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

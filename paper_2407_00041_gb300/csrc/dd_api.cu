@@ -259,6 +259,7 @@ void dd_solve_params_default(dd_solve_params* p) {
   p->precond = DD_PRECOND_NONE;
   p->gs_passes = 1;
   p->rhs_batch = 0;
+  p->precond_iters = 32;
 }
 
 int dd_solve(dd_clover* op, const dd_solve_params* params, const void* b, void* x, int nrhs, int layout,
@@ -266,8 +267,10 @@ int dd_solve(dd_clover* op, const dd_solve_params* params, const void* b, void* 
   if (!op || !params || !b || !x || nrhs < 1) return fail(DD_ERR_ARG, "null argument or nrhs < 1");
   if (layout != DD_LAYOUT_CANONICAL && layout != DD_LAYOUT_CANONICAL_HOST)
     return fail(DD_ERR_ARG, "dd_solve takes canonical fields");
-  if (params->precond != DD_PRECOND_NONE && params->precond != DD_PRECOND_NORMAL)
+  if (params->precond < DD_PRECOND_NONE || params->precond > DD_PRECOND_CGNR)
     return fail(DD_ERR_ARG, "unknown preconditioner");
+  if (params->precond == DD_PRECOND_CGNR && params->precond_iters < 1)
+    return fail(DD_ERR_ARG, "precond_iters must be >= 1");
   if (!(params->tol > 0) || params->max_restarts < 1 || params->max_outer < 0)
     return fail(DD_ERR_ARG, "bad solver parameters");
   if (params->rhs_batch < 0) return fail(DD_ERR_ARG, "rhs_batch must be >= 0");

@@ -60,7 +60,12 @@ __global__ void __launch_bounds__(THREADS, BatchMinBlocks<THREADS>::value)
     while (l + 1 < count && item >= item_start[l + 1]) ++l;  // items only grow within a CTA
     const HopArgs& a = args[l];
     const int64_t tid = (item - item_start[l]) * THREADS + threadIdx.x;
-    if (tid < (int64_t)a.g.Vh * a.nrhs * a.npar) hop_thread<P, P, P, false, EPI_D>(a, tid);
+    if (tid < (int64_t)a.g.Vh * (a.nrhs / a.rhs_block) * a.npar) {
+      if (a.rhs_block == 2)
+        hop_thread_rb<P, P, P, false, EPI_D, 2>(a, tid);
+      else
+        hop_thread<P, P, P, false, EPI_D>(a, tid);
+    }
   }
 }
 
@@ -75,7 +80,9 @@ int stage(dd_batch* b, const void* const* ins, void* const* outs, cudaStream_t s
     const dd_clover* op = b->ops[i];
     const dd_lattice* lat = op->lat;
     HopArgs& a = b->h_args[i];
-    a.g = lat->geom();  // lexicographic traversal: the batch mixes lattices of all sizes
+    a.g = lat->geom();
+    a.g.zblock = zblock_for(lat->dims, stencil_bytes_per_site(b->prec, b->nrhs[i]));
+    a.rhs_block = b->nrhs[i] % 2 == 0 ? 2 : 1;
     a.nrhs = b->nrhs[i];
     a.p0 = 0;
     a.npar = 2;
@@ -91,7 +98,7 @@ int stage(dd_batch* b, const void* const* ins, void* const* outs, cudaStream_t s
       a.M[p] = op->M(pi, p);
     }
     a.beta = -0.5;
-    const int64_t slots = 2 * lat->Vh * b->nrhs[i];
+    const int64_t slots = 2 * lat->Vh * (b->nrhs[i] / a.rhs_block);
     starts[i + 1] = starts[i] + (slots + b->tile - 1) / b->tile;
   }
   b->total_items = starts[b->count];

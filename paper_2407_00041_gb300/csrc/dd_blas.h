@@ -24,6 +24,13 @@ int blas_multiaxpy(const VecList& vs, int J, const double2* c_dev, double csign,
 // out = c[r] * in
 template <int PV>
 int blas_scale(const double2* c_dev, const void* in, void* out, int64_t L, int N, cudaStream_t st);
+// CG updates with step sizes from device scalars (squared norms in .x):
+// x += (g/n) p, r -= (g/n) w;   p = z + (gn/go) p
+template <int PV>
+int blas_cg_xr(void* x, void* r, const void* p, const void* w, const double2* g, const double2* n, int64_t L, int N,
+               cudaStream_t st);
+template <int PV>
+int blas_cg_p(void* p, const void* z, const double2* gn, const double2* go, int64_t L, int N, cudaStream_t st);
 // FP64 native field -> FP32 native field (nhalf half fields, VN = Vh * N)
 int blas_demote(const void* in64, void* out32, int64_t nhalf, int64_t VN, cudaStream_t st);
 // FP64 native field += FP32 native field

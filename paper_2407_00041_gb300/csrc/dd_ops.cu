@@ -86,8 +86,9 @@ Field field_view(const dd_lattice* lat, int prec, int subset, void* base, int nr
   return f;
 }
 
-// ---------------------------------------------------------------- dispatch
-namespace {
+int64_t stencil_bytes_per_site(int pg, int nrhs) {
+  return pg == P64 ? 1152 + 384 * nrhs : pg == P32 ? 576 + 192 * nrhs : 288 + 104 * nrhs;
+}
 
 // Depth of the Z-slabs of the full-lattice traversal: the largest divisor of
 // nZ whose slab-slice (depth * nY * nX sites) moves at most ~30 MB through the
@@ -110,6 +111,10 @@ int zblock_for(const int dims[4], int64_t bytes_per_site) {
     if (nZ % b == 0 && b * plane * bytes_per_site <= budget) best = b;
   return best;
 }
+
+// ---------------------------------------------------------------- dispatch
+namespace {
+
 
 
 int run_hop(int pg, int pv, const HopArgs& a, bool dag, int epi, cudaStream_t st) {
@@ -136,10 +141,6 @@ int check_prec(const dd_clover* op, int pg) {
   return DD_OK;
 }
 
-int64_t stencil_bytes_per_site(int pg, int nrhs) {
-  return pg == P64 ? 1152 + 384 * nrhs : pg == P32 ? 576 + 192 * nrhs : 288 + 104 * nrhs;
-}
-
 HopArgs base_args(const dd_clover* op, int pg, int nrhs) {
   HopArgs a;
   a.g = op->lat->geom();
@@ -157,6 +158,7 @@ HopArgs base_args(const dd_clover* op, int pg, int nrhs) {
     a.in[p] = a.out[p] = a.y[p] = a.z[p] = HalfField{nullptr, nullptr};
   }
   a.beta = -0.5;
+  a.rhs_block = 1;
   return a;
 }
 

@@ -28,6 +28,7 @@ struct HopArgs {
   const void* U[2];  // links by parity of their site: [mu][9][Vh] complex elements
   const void* M[2];  // 6x6 Hermitian blocks by output parity: [36][Vh] elements
   double beta;
+  int rhs_block;  // batched launch: right-hand sides per thread (1 or 2)
 };
 
 // Self-coupling apply without hopping: out = M y on npar parities.
@@ -42,6 +43,9 @@ struct BlockArgs {
 
 template <int PG, int PIN, int POUT>
 cudaError_t launch_hop(const HopArgs& a, bool dagger, int epi, cudaStream_t st);
+// traversal slab depth for a lattice and the bytes per site of the stencil (dd_ops.cu)
+int zblock_for(const int dims[4], int64_t bytes_per_site);
+int64_t stencil_bytes_per_site(int pg, int nrhs);
 template <int PG, int PIN, int POUT>
 cudaError_t launch_block(const BlockArgs& a, cudaStream_t st);
 

@@ -16,6 +16,15 @@
 // |h_{j+1,j}| falls below tol / 10 of ||f|| (the breakdown rule after
 // Algorithm 1).  Right-hand sides that have converged are masked out (their
 // new basis vectors are scaled by zero).
+//
+// Preconditioners M_j (Algorithm 2, line 8):
+//   none    z_j = v_j
+//   normal  the fixed right preconditioner M^{-1} = A^H: A M^{-1} = A A^H is
+//           Hermitian positive definite, so restarted FGMRES cannot stagnate
+//   cgnr    the flexible preconditioner z_j = k steps of the conjugate-gradient
+//           method on the normal equations A^H A z = A^H v_j (from z = 0), run
+//           on the device with step sizes kept in device memory; Z_m is stored
+//           and x += Z_m y (line 19).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -54,16 +63,19 @@ struct Inner {
   int N, m;
   int64_t L;     // 16-byte groups per vector
   size_t vbytes;
-  bool normal = false;  // right preconditioner M^{-1} = D^H (Dhat^H)
+  int mode = 0;         // DD_PRECOND_NONE / _NORMAL / _CGNR
+  int cg_iters = 32;    // CG steps per application of the cgnr preconditioner
+  bool normal = false;  // mode == DD_PRECOND_NORMAL
   int verbose = 0;
   int gs_passes = 1;    // classical Gram-Schmidt passes per Arnoldi step
-  DevBuf basis, w, rvec, tmp, red, partials, coef, zt, ut;
+  DevBuf basis, w, rvec, tmp, red, partials, coef, zt, ut, zbasis, cr, cz, cp, cgs;
   Pinned hred, hcoef;
   // counters
   int applies = 0, steps = 0, cycles = 0;
 
-  int init(const dd_clover* op_, int pg_, int pv_, bool eo_, int N_, int m_, bool normal_) {
-    normal = normal_;
+  int init(const dd_clover* op_, int pg_, int pv_, bool eo_, int N_, int m_, int mode_) {
+    mode = mode_;
+    normal = mode == DD_PRECOND_NORMAL;
     op = op_;
     pg = pg_;
     pv = pv_;
@@ -80,6 +92,13 @@ struct Inner {
       DD_TRY(zt.ensure(vbytes));
       DD_TRY(ut.ensure(vbytes));
     }
+    if (mode == DD_PRECOND_CGNR) {
+      DD_TRY(zbasis.ensure(vbytes * m));
+      DD_TRY(cr.ensure(vbytes));
+      DD_TRY(cz.ensure(vbytes));
+      DD_TRY(cp.ensure(vbytes));
+      DD_TRY(cgs.ensure((size_t)3 * N * sizeof(double2)));
+    }
     if (eo) DD_TRY(tmp.ensure(field_bytes(lat, pv, 2, N)));
     const size_t nred = (size_t)(2 * (m + 1) + 1) * N;
     DD_TRY(red.ensure(nred * sizeof(double2)));
@@ -91,6 +110,7 @@ struct Inner {
   }
 
   void* V(int j) { return reinterpret_cast<char*>(basis.ptr) + vbytes * j; }
+  void* Zb(int j) { return reinterpret_cast<char*>(zbasis.ptr) + vbytes * j; }
   Field fv(void* p) { return field_view(op->lat, pv, eo ? 1 : 0, p, N); }
 
   // the operator A of the inner system (Dhat or D)
@@ -105,6 +125,39 @@ struct Inner {
     if (!normal) return apply_op(v, out, false, st);
     DD_TRY(apply_op(v, zt.ptr, true, st));
     return apply_op(zt.ptr, out, false, st);
+  }
+
+  // z = k steps of CG on A^H A z = A^H v from z = 0 (the cgnr preconditioner)
+  int cgnr(const void* v, void* z, cudaStream_t st) {
+    double2* g0 = reinterpret_cast<double2*>(cgs.ptr);
+    double2* g1 = g0 + N;
+    double2* nw = g0 + 2 * N;
+    double2* g[2] = {g0, g1};
+    VecList one;
+    DD_CUDA(cudaMemsetAsync(z, 0, vbytes, st));
+    DD_CUDA(cudaMemcpyAsync(cr.ptr, v, vbytes, cudaMemcpyDeviceToDevice, st));
+    DD_TRY(apply_op(cr.ptr, cz.ptr, true, st));  // A^H r
+    DD_CUDA(cudaMemcpyAsync(cp.ptr, cz.ptr, vbytes, cudaMemcpyDeviceToDevice, st));
+    one.p[0] = cz.ptr;
+    DD_TRY(dots(one, 1, cz.ptr, g[0], 0, st));
+    for (int i = 0; i < cg_iters; ++i) {
+      DD_TRY(apply_op(cp.ptr, w.ptr, false, st));  // w = A p
+      one.p[0] = w.ptr;
+      DD_TRY(dots(one, 1, w.ptr, nw, 0, st));
+      if (pv == P64)
+        DD_TRY(blas_cg_xr<P64>(z, cr.ptr, cp.ptr, w.ptr, g[i & 1], nw, L, N, st));
+      else
+        DD_TRY(blas_cg_xr<P32>(z, cr.ptr, cp.ptr, w.ptr, g[i & 1], nw, L, N, st));
+      if (i + 1 == cg_iters) break;  // the last direction update is not needed
+      DD_TRY(apply_op(cr.ptr, cz.ptr, true, st));  // z' = A^H r
+      one.p[0] = cz.ptr;
+      DD_TRY(dots(one, 1, cz.ptr, g[(i + 1) & 1], 0, st));
+      if (pv == P64)
+        DD_TRY(blas_cg_p<P64>(cp.ptr, cz.ptr, g[(i + 1) & 1], g[i & 1], L, N, st));
+      else
+        DD_TRY(blas_cg_p<P32>(cp.ptr, cz.ptr, g[(i + 1) & 1], g[i & 1], L, N, st));
+    }
+    return DD_OK;
   }
 
   int dots(const VecList& vs, int J, const void* x, double2* out, int add, cudaStream_t st) {
@@ -184,7 +237,12 @@ struct Inner {
       int jmax = 0;
       for (int j = 0; j < m; ++j) {
         ++steps;
-        DD_TRY(apply(V(j), w.ptr, st));  // line 9 (z_j = v_j)
+        if (mode == DD_PRECOND_CGNR) {
+          DD_TRY(cgnr(V(j), Zb(j), st));             // line 8: z_j = M_j^{-1} v_j
+          DD_TRY(apply_op(Zb(j), w.ptr, false, st));  // line 9
+        } else {
+          DD_TRY(apply(V(j), w.ptr, st));  // line 9 (z_j = v_j, or A^H v_j for the fixed preconditioner)
+        }
         VecList vs;
         for (int i = 0; i <= j; ++i) vs.p[i] = V(i);
         // lines 10-13: classical Gram-Schmidt (one pass, or two when
@@ -273,9 +331,9 @@ struct Inner {
         }
       DD_CUDA(cudaMemcpyAsync(dcoef, hc, (size_t)jmax * N * sizeof(double2), cudaMemcpyHostToDevice, st));
       VecList vs;
-      for (int i = 0; i < jmax; ++i) vs.p[i] = V(i);
+      for (int i = 0; i < jmax; ++i) vs.p[i] = mode == DD_PRECOND_CGNR ? Zb(i) : V(i);
       if (!normal) {
-        DD_TRY(axpys(vs, jmax, dcoef, 1.0, e, st));  // line 19 with z_j = v_j
+        DD_TRY(axpys(vs, jmax, dcoef, 1.0, e, st));  // line 19: e += Z_m y (Z_m = V_m without preconditioner)
       } else {
         // fixed preconditioner: e += M^{-1} (V y) (line 19 of Algorithm 1)
         DD_CUDA(cudaMemsetAsync(ut.ptr, 0, vbytes, st));
@@ -489,7 +547,8 @@ int solve_schur(dd_clover* op, const dd_solve_params* prm, const double* b, doub
   double worst = 0.0;
   for (int r0 = 0; r0 < N; r0 += nbmax) {
     const int nb = std::min(nbmax, N - r0);
-    DD_TRY(inner.init(op, pin, pv, true, nb, prm->restart, prm->precond == DD_PRECOND_NORMAL));
+    DD_TRY(inner.init(op, pin, pv, true, nb, prm->restart, prm->precond));
+    inner.cg_iters = prm->precond_iters;
     inner.verbose = prm->verbose;
     inner.gs_passes = prm->gs_passes;
     const size_t off = (size_t)r0 * lat->V * 24;  // doubles per RHS: V sites x 12 complex
@@ -548,7 +607,8 @@ int solve(dd_clover* op, const dd_solve_params* prm, const double* b_canon, doub
   for (int r = 0; r < N; ++r)
     if (!std::isfinite(bnorm[r])) return fail(DD_ERR_ARG, "right-hand side contains NaN or Inf");
   Inner inner;
-  DD_TRY(inner.init(op, pg, pv, eo, N, prm->restart, prm->precond == DD_PRECOND_NORMAL));
+  DD_TRY(inner.init(op, pg, pv, eo, N, prm->restart, prm->precond));
+  inner.cg_iters = prm->precond_iters;
   inner.verbose = prm->verbose;
   inner.gs_passes = prm->gs_passes;
   dd_stats s{};

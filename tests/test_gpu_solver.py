@@ -38,12 +38,13 @@ def oracle_residual(U, A, dims, b, x):
 
 @pytest.mark.parametrize("inner", [dd.DD_PREC_F64, dd.DD_PREC_F32, dd.DD_PREC_F16])
 @pytest.mark.parametrize("even_odd", [1, 0])
-@pytest.mark.parametrize("precond", [dd.DD_PRECOND_NONE, dd.DD_PRECOND_NORMAL])
+@pytest.mark.parametrize("precond", [dd.DD_PRECOND_NONE, dd.DD_PRECOND_NORMAL, dd.DD_PRECOND_CGNR])
 def test_solve_to_1e10(sys44, inner, even_odd, precond):
     dims, U, A, op, b, xref, _ = sys44
     bt = torch.from_numpy(b[:1]).cuda()
     x = torch.zeros_like(bt)
-    status, st = op.solve(bt, x, 1, tol=1e-10, inner_prec=inner, even_odd=even_odd, restart=30, precond=precond)
+    status, st = op.solve(bt, x, 1, tol=1e-10, inner_prec=inner, even_odd=even_odd, restart=30, precond=precond,
+                          precond_iters=8)
     assert status == 0, st
     assert st["converged"] == 1 and st["true_residual"] < 1e-10
     xn = x.cpu().numpy()[0]
@@ -63,10 +64,10 @@ def test_multi_rhs_solve(sys44):
     for r in range(3):
         assert oracle_residual(U, A, dims, b[r], xn[r]) < 1e-10
     # the same right-hand sides solved in batches of 2 and 1, on host buffers
-    for batch in (2, 1):
+    for batch, pc in ((2, dd.DD_PRECOND_NORMAL), (1, dd.DD_PRECOND_CGNR)):
         xh = np.zeros_like(b)
         status, st = op.solve(np.ascontiguousarray(b), xh, 3, layout=dd.DD_LAYOUT_CANONICAL_HOST, tol=1e-10,
-                              rhs_batch=batch, precond=dd.DD_PRECOND_NORMAL)
+                              rhs_batch=batch, precond=pc, precond_iters=6, restart=8)
         assert status == 0, st
         for r in range(3):
             assert oracle_residual(U, A, dims, b[r], xh[r]) < 1e-10
