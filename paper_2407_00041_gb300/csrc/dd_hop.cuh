@@ -432,6 +432,7 @@ cudaError_t launch_hop(const HopArgs& a, bool dagger, int epi, cudaStream_t st) 
   // several right-hand sides: RHS-blocked variant (not for FP64, which is
   // bound by the FP64 pipe, nor for the residual / add epilogues)
   const int rbmax = rhs_block_limit();
+
   if (PG != P64 && rbmax >= 2 && (epi == EPI_D || epi == EPI_AINV) && a.nrhs >= 2 && a.nrhs % 2 == 0) {
     // measured on 32^4: blocks of 4 win from 16 RHS up, blocks of 2 below
     const int NBsel = (a.nrhs % 4 == 0 && a.nrhs >= 16 && rbmax >= 4) ? 4 : 2;
