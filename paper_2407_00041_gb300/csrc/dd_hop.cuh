@@ -114,40 +114,133 @@ __device__ __forceinline__ void hop_regs(cx<R> acc[12], const cx<R> psi[12], con
   }
 }
 
-// The same with the link read from its native layout (element stride Vh).
-template <int PG, int MU, int T, bool ADJ, typename R>
-__device__ __forceinline__ void hop(cx<R> acc[12], const cx<R> psi[12], const typename Store<PG>::elem* U,
-                                    int64_t Vh, R sign) {
-  cx<R> u[9];
+// Link storage: the 36 elements of a site's four links (direction-major,
+// 3x3 row-major) are stored in 16-byte groups [group][Vh] per parity: FP64
+// one element per group, FP32 two, FP16 four.  Direction mu uses elements
+// 9 mu .. 9 mu + 8, i.e. 9, 5 or 3 group loads; a group shared by two
+// directions is read twice (the second time from cache).
+template <int PG, typename R>
+__device__ __forceinline__ void load_link(const void* Ubase, int64_t s, int64_t Vh, int mu, cx<R> u[9]) {
+  if constexpr (PG == P64) {
+    const double2* p = reinterpret_cast<const double2*>(Ubase) + (int64_t)(9 * mu) * Vh + s;
 #pragma unroll
-  for (int e = 0; e < 9; ++e) u[e] = ld_elem<PG>(U + e * Vh);
+    for (int e = 0; e < 9; ++e) {
+      const double2 v = __ldg(p + e * Vh);
+      u[e] = mk<R>(v.x, v.y);
+    }
+  } else if constexpr (PG == P32) {
+    const float4* p = reinterpret_cast<const float4*>(Ubase) + s;
+    const int g0 = (9 * mu) >> 1, off = (9 * mu) & 1;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const float4 v = __ldg(p + (int64_t)(g0 + k) * Vh);
+      const int e0 = 2 * k - off;  // element index of v.xy within this link
+      if (e0 >= 0 && e0 < 9) u[e0] = mk<R>(v.x, v.y);
+      if (e0 + 1 >= 0 && e0 + 1 < 9) u[e0 + 1] = mk<R>(v.z, v.w);
+    }
+  } else {
+    const uint4* p = reinterpret_cast<const uint4*>(Ubase) + s;
+    const int g0 = (9 * mu) >> 2, off = (9 * mu) & 3;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const uint4 v = __ldg(p + (int64_t)(g0 + k) * Vh);
+      unsigned int w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int e = 4 * k + q - off;
+        if (e >= 0 && e < 9) {
+          const float2 f = __half22float2(*reinterpret_cast<__half2*>(&w[q]));
+          u[e] = mk<R>(f.x, f.y);
+        }
+      }
+    }
+  }
+}
+
+// The same with the link read from its native layout.
+template <int PG, int MU, int T, bool ADJ, typename R>
+__device__ __forceinline__ void hop(cx<R> acc[12], const cx<R> psi[12], const void* Ubase, int64_t s, int64_t Vh,
+                                    R sign) {
+  cx<R> u[9];
+  load_link<PG, R>(Ubase, s, Vh, MU, u);
   hop_regs<MU, T, ADJ, R>(acc, psi, u, sign);
 }
 
-// out = M x for the two Hermitian 6x6 blocks stored as 18 elements each:
-// elements 0..2 hold the real diagonal in pairs (d0, d1), (d2, d3), (d4, d5);
-// elements 3..17 the strict upper triangle row by row.
+// Self-coupling / A_ee^{-1} storage: two Hermitian 6x6 blocks per site, 18
+// elements each: elements 0..2 hold the real diagonal in pairs (d0, d1),
+// (d2, d3), (d4, d5); elements 3..17 the strict upper triangle row by row.
+// The 36 elements of a site are stored in 16-byte groups, [group][Vh]:
+// FP64 one element per group (double2), FP32 two (float4), FP16 four
+// (8 halves), so a site's blocks take 36, 18 or 9 loads.
+template <int PG>
+struct BlockGroups {
+  static constexpr int PER = PG == P64 ? 1 : PG == P32 ? 2 : 4;  // elements per group
+};
+
+// (i, j) of the strict upper-triangle element o = 0..14 of a 6x6 block
+__device__ __forceinline__ void tri_ij(int o, int& i, int& j) {
+  i = o < 5 ? 0 : o < 9 ? 1 : o < 12 ? 2 : o < 14 ? 3 : 4;
+  const int start = i == 0 ? 0 : i == 1 ? 5 : i == 2 ? 9 : i == 3 ? 12 : 14;
+  j = i + 1 + (o - start);
+}
+
+// group g of site s: the PER elements it holds
 template <int PG, typename R>
-__device__ __forceinline__ void block_apply(const typename Store<PG>::elem* M, int64_t Vh, const cx<R> x[12],
-                                            cx<R> out[12]) {
+__device__ __forceinline__ void load_block_group(const void* M, int64_t s, int64_t Vh, int g, cx<R> e[4],
+                                                 bool streaming) {
+  if constexpr (PG == P64) {
+    const double2* p = reinterpret_cast<const double2*>(M) + (int64_t)g * Vh + s;
+    const double2 v = streaming ? __ldcs(p) : __ldg(p);
+    e[0] = mk<R>(v.x, v.y);
+  } else if constexpr (PG == P32) {
+    const float4* p = reinterpret_cast<const float4*>(M) + (int64_t)g * Vh + s;
+    const float4 v = streaming ? __ldcs(p) : __ldg(p);
+    e[0] = mk<R>(v.x, v.y);
+    e[1] = mk<R>(v.z, v.w);
+  } else {
+    const uint4* p = reinterpret_cast<const uint4*>(M) + (int64_t)g * Vh + s;
+    const uint4 v = streaming ? __ldcs(p) : __ldg(p);
+    unsigned int w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-  for (int b = 0; b < 2; ++b) {
-    const typename Store<PG>::elem* m = M + (int64_t)18 * b * Vh;
-    cx<R> d01 = ld_elem_stream<PG>(m), d23 = ld_elem_stream<PG>(m + Vh), d45 = ld_elem_stream<PG>(m + 2 * Vh);
-    const R d[6] = {d01.re, d01.im, d23.re, d23.im, d45.re, d45.im};
-#pragma unroll
-    for (int i = 0; i < 6; ++i) out[6 * b + i] = d[i] * x[6 * b + i];
-    int k = 3;
-#pragma unroll
-    for (int i = 0; i < 6; ++i)
-#pragma unroll
-      for (int j = i + 1; j < 6; ++j) {
-        cx<R> a = ld_elem_stream<PG>(m + k * Vh);
-        ++k;
-        out[6 * b + i] = cfma(a, x[6 * b + j], out[6 * b + i]);
-        out[6 * b + j] = cfmac(a, x[6 * b + i], out[6 * b + j]);
-      }
+    for (int q = 0; q < 4; ++q) {
+      const float2 f = __half22float2(*reinterpret_cast<__half2*>(&w[q]));
+      e[q] = mk<R>(f.x, f.y);
+    }
   }
+}
+
+// out (+)= M x for the two blocks of site s (ADD = false overwrites out).
+template <int PG, bool ADD, typename R>
+__device__ __forceinline__ void block_apply_g(const void* M, int64_t s, int64_t Vh, const cx<R> x[12], cx<R> out[12],
+                                              bool streaming) {
+  constexpr int PER = BlockGroups<PG>::PER;
+  cx<R> grp[4];
+#pragma unroll
+  for (int E = 0; E < 36; ++E) {
+    if (E % PER == 0) load_block_group<PG, R>(M, s, Vh, E / PER, grp, streaming);
+    const cx<R> m = grp[E % PER];
+    const int b = E / 18, k = E % 18;
+    if (k < 3) {
+      if (ADD) {
+        out[6 * b + 2 * k] = out[6 * b + 2 * k] + m.re * x[6 * b + 2 * k];
+        out[6 * b + 2 * k + 1] = out[6 * b + 2 * k + 1] + m.im * x[6 * b + 2 * k + 1];
+      } else {
+        out[6 * b + 2 * k] = m.re * x[6 * b + 2 * k];
+        out[6 * b + 2 * k + 1] = m.im * x[6 * b + 2 * k + 1];
+      }
+    } else {
+      int i, j;
+      tri_ij(k - 3, i, j);
+      out[6 * b + i] = cfma(m, x[6 * b + j], out[6 * b + i]);
+      out[6 * b + j] = cfmac(m, x[6 * b + i], out[6 * b + j]);
+    }
+  }
+}
+
+// out = M x with M the parity base pointer of the block array and s the site
+template <int PG, typename R>
+__device__ __forceinline__ void block_apply(const void* M, int64_t s, int64_t Vh, const cx<R> x[12], cx<R> out[12]) {
+  block_apply_g<PG, false, R>(M, s, Vh, x, out, true);
 }
 
 // The work of one thread: output slot `tid` in [0, npar * Vh * nrhs).
@@ -182,20 +275,17 @@ __device__ __forceinline__ void hop_thread(const HopArgs& a, int64_t tid) {
 #pragma unroll
   for (int c = 0; c < 12; ++c) acc[c] = zero<R>();
 
-  const E* Up = reinterpret_cast<const E*>(a.U[p]);
-  const E* Uq = reinterpret_cast<const E*>(a.U[q]);
-
 #define DD_HOP_DIR(MU)                                                                     \
   {                                                                                        \
     cx<R> psi[12];                                                                         \
     int nl = nb_fwd(a.g, sc, MU);                                                          \
     R sg = (MU == 0 && sc.c[0] == a.g.n[0] - 1) ? (R)a.g.t_bc : (R)1;                      \
     load_spinor<PIN, R>(a.in[q], a.gstride, (int64_t)(nl >> 1) * a.nrhs + r, psi);         \
-    hop<PG, MU, TF, false, R>(acc, psi, Up + (int64_t)(MU * 9) * Vh + s, Vh, sg);          \
+    hop<PG, MU, TF, false, R>(acc, psi, a.U[p], s, Vh, sg);                                \
     nl = nb_bwd(a.g, sc, MU);                                                              \
     sg = (MU == 0 && sc.c[0] == 0) ? (R)a.g.t_bc : (R)1;                                   \
     load_spinor<PIN, R>(a.in[q], a.gstride, (int64_t)(nl >> 1) * a.nrhs + r, psi);         \
-    hop<PG, MU, TB, true, R>(acc, psi, Uq + (int64_t)(MU * 9) * Vh + (nl >> 1), Vh, sg);   \
+    hop<PG, MU, TB, true, R>(acc, psi, a.U[q], nl >> 1, Vh, sg);                           \
   }
   DD_HOP_DIR(0)
   DD_HOP_DIR(1)
@@ -205,7 +295,7 @@ __device__ __forceinline__ void hop_thread(const HopArgs& a, int64_t tid) {
 
   const R beta = (R)a.beta;
   const int64_t i = (int64_t)s * a.nrhs + r;
-  const E* M = reinterpret_cast<const E*>(a.M[p]);
+  const void* M = a.M[p];
   cx<R> res[12];
   if constexpr (EPI == EPI_D || EPI == EPI_RESID) {
     cx<R> y[12];
@@ -213,7 +303,7 @@ __device__ __forceinline__ void hop_thread(const HopArgs& a, int64_t tid) {
       load_spinor<PIN, R>(a.y[p], a.gstride, i, y);
     else
       load_spinor<POUT, R>(a.y[p], a.gstride, i, y);
-    block_apply<PG, R>(M + s, Vh, y, res);
+    block_apply<PG, R>(M, s, Vh, y, res);
 #pragma unroll
     for (int c = 0; c < 12; ++c) {
       res[c].re = ffma(beta, acc[c].re, res[c].re);
@@ -228,7 +318,7 @@ __device__ __forceinline__ void hop_thread(const HopArgs& a, int64_t tid) {
   } else if constexpr (EPI == EPI_AINV) {
 #pragma unroll
     for (int c = 0; c < 12; ++c) acc[c] = beta * acc[c];
-    block_apply<PG, R>(M + s, Vh, acc, res);
+    block_apply<PG, R>(M, s, Vh, acc, res);
   } else if constexpr (EPI == EPI_ADD) {
     load_spinor<POUT, R>(a.y[p], a.gstride, i, res);
 #pragma unroll
@@ -244,7 +334,7 @@ __device__ __forceinline__ void hop_thread(const HopArgs& a, int64_t tid) {
       y[c].re = ffma(beta, acc[c].re, y[c].re);
       y[c].im = ffma(beta, acc[c].im, y[c].im);
     }
-    block_apply<PG, R>(M + s, Vh, y, res);
+    block_apply<PG, R>(M, s, Vh, y, res);
   }
   store_spinor<POUT, R>(a.out[p], a.gstride, i, res);
 }
@@ -256,33 +346,6 @@ __device__ __forceinline__ void hop_thread(const HopArgs& a, int64_t tid) {
 // on consecutive addresses.  EPI_D builds A(x) psi(x) first and folds beta
 // into the hops; EPI_AINV applies the block to beta * acc at the end.  The
 // self-coupling elements are re-read from L1 for each of the NB spinors.
-template <int PG, int R_, int NB>
-__device__ __forceinline__ void block_apply_add(const typename Store<PG>::elem* M, int64_t Vh,
-                                                const cx<typename Store<PG>::real> x[12],
-                                                cx<typename Store<PG>::real> out[12]) {
-  using R = typename Store<PG>::real;
-#pragma unroll
-  for (int b = 0; b < 2; ++b) {
-    const typename Store<PG>::elem* m = M + (int64_t)18 * b * Vh;
-#pragma unroll
-    for (int w = 0; w < 3; ++w) {
-      const cx<R> d = ld_elem<PG>(m + w * Vh);
-      out[6 * b + 2 * w] = out[6 * b + 2 * w] + d.re * x[6 * b + 2 * w];
-      out[6 * b + 2 * w + 1] = out[6 * b + 2 * w + 1] + d.im * x[6 * b + 2 * w + 1];
-    }
-    int e = 3;
-#pragma unroll
-    for (int i = 0; i < 6; ++i)
-#pragma unroll
-      for (int j = i + 1; j < 6; ++j) {
-        const cx<R> mm = ld_elem<PG>(m + e * Vh);
-        ++e;
-        out[6 * b + i] = cfma(mm, x[6 * b + j], out[6 * b + i]);
-        out[6 * b + j] = cfmac(mm, x[6 * b + i], out[6 * b + j]);
-      }
-  }
-}
-
 template <int PG, int PIN, int POUT, bool DAG, int EPI, int NB>
 __device__ __forceinline__ void hop_thread_rb(const HopArgs& a, int64_t tid) {
   using R = typename Store<PG>::real;
@@ -307,9 +370,7 @@ __device__ __forceinline__ void hop_thread_rb(const HopArgs& a, int64_t tid) {
   constexpr int TF = DAG ? +1 : -1;
   constexpr int TB = -TF;
   const R beta = (R)a.beta;
-  const E* Up = reinterpret_cast<const E*>(a.U[p]);
-  const E* Uq = reinterpret_cast<const E*>(a.U[q]);
-  const E* M = reinterpret_cast<const E*>(a.M[p]) + s;
+  const void* M = a.M[p];
   const int64_t ibase = (int64_t)s * a.nrhs + rb;
 
   cx<R> res[NB][12];
@@ -320,7 +381,7 @@ __device__ __forceinline__ void hop_thread_rb(const HopArgs& a, int64_t tid) {
     if constexpr (EPI == EPI_D) {
       cx<R> y[12];
       load_spinor<PIN, R>(a.y[p], a.gstride, ibase + k * nrb, y);
-      block_apply_add<PG, 0, NB>(M, Vh, y, res[k]);
+      block_apply_g<PG, true, R>(M, s, Vh, y, res[k], false);
     }
   }
   const R hop_scale = EPI == EPI_D ? beta : (R)1;
@@ -330,9 +391,8 @@ __device__ __forceinline__ void hop_thread_rb(const HopArgs& a, int64_t tid) {
     const int nl = FWD ? nb_fwd(a.g, sc, MU) : nb_bwd(a.g, sc, MU);                                 \
     R sg = hop_scale;                                                                               \
     if (MU == 0 && sc.c[0] == (FWD ? a.g.n[0] - 1 : 0)) sg = sg * (R)a.g.t_bc;                      \
-    const E* U = FWD ? Up + (int64_t)(MU * 9) * Vh + s : Uq + (int64_t)(MU * 9) * Vh + (nl >> 1);   \
     cx<R> u[9];                                                                                     \
-    _Pragma("unroll") for (int e = 0; e < 9; ++e) u[e] = ld_elem<PG>(U + e * Vh);                   \
+    load_link<PG, R>(FWD ? a.U[p] : a.U[q], FWD ? (int64_t)s : (int64_t)(nl >> 1), Vh, MU, u);     \
     const int64_t ib = (int64_t)(nl >> 1) * a.nrhs + rb;                                            \
     _Pragma("unroll") for (int k = 0; k < NB; ++k) {                                                \
       cx<R> psi[12];                                                                                \
@@ -359,7 +419,7 @@ __device__ __forceinline__ void hop_thread_rb(const HopArgs& a, int64_t tid) {
       cx<R> out[12];
 #pragma unroll
       for (int c = 0; c < 12; ++c) out[c] = zero<R>();
-      block_apply_add<PG, 0, NB>(M, Vh, res[k], out);
+      block_apply_g<PG, true, R>(M, s, Vh, res[k], out, false);
       store_spinor<POUT, R>(a.out[p], a.gstride, ibase + k * nrb, out);
     } else {
       store_spinor<POUT, R>(a.out[p], a.gstride, ibase + k * nrb, res[k]);
@@ -405,7 +465,7 @@ __global__ void __launch_bounds__(128) k_block(const BlockArgs a) {
   const int s = (int)(tid / a.nrhs);
   cx<R> y[12], res[12];
   load_spinor<PIN, R>(a.y[p], a.gstride, tid, y);
-  block_apply<PG, R>(reinterpret_cast<const E*>(a.M[p]) + s, a.Vh, y, res);
+  block_apply<PG, R>(a.M[p], s, a.Vh, y, res);
   store_spinor<POUT, R>(a.out[p], a.gstride, tid, res);
 }
 

@@ -49,12 +49,15 @@ __global__ void k_links_to_native(LexGeom g, const double2* __restrict__ Uc, dou
   const int p = (c[0] + c[1] + c[2] + c[3]) & 1;
   const int64_t s = lex >> 1;
   const int64_t base = (int64_t)p * 36 * g.Vh + (int64_t)mu * 9 * g.Vh + s;
+  // FP32 / FP16 copies: element E = 9 mu + e in 16-byte groups of 2 / 4
+  const int64_t pbase = (int64_t)p * 36 * g.Vh;
 #pragma unroll
   for (int e = 0; e < 9; ++e) {
     double2 v = Uc[t * 9 + e];
     U64[base + e * g.Vh] = v;
-    if (U32) U32[base + e * g.Vh] = make_float2((float)v.x, (float)v.y);
-    if (U16) U16[base + e * g.Vh] = __floats2half2_rn((float)v.x, (float)v.y);
+    const int E = 9 * mu + e;
+    if (U32) U32[pbase + ((int64_t)(E >> 1) * g.Vh + s) * 2 + (E & 1)] = make_float2((float)v.x, (float)v.y);
+    if (U16) U16[pbase + ((int64_t)(E >> 2) * g.Vh + s) * 4 + (E & 3)] = __floats2half2_rn((float)v.x, (float)v.y);
   }
 }
 
@@ -295,13 +298,26 @@ __global__ void k_clover_invert(int64_t Vh, const double2* __restrict__ clov_eve
   }
 }
 
-__global__ void k_demote32(const double2* __restrict__ in, float2* out, int64_t n) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = make_float2((float)in[i].x, (float)in[i].y);
+// Block arrays [nsets][36 elements][Vh] (FP64) -> 16-byte groups
+// [nsets][36 / PER][Vh] with PER = 2 (FP32, float4) or 4 (FP16, 8 halves).
+__global__ void k_group32(const double2* __restrict__ in, float4* out, int64_t nsets, int64_t Vh) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // over nsets * 18 * Vh
+  if (t >= nsets * 18 * Vh) return;
+  const int64_t s = t % Vh, g = (t / Vh) % 18, set = t / (18 * Vh);
+  const double2 a = in[(set * 36 + 2 * g) * Vh + s], b = in[(set * 36 + 2 * g + 1) * Vh + s];
+  out[t] = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
 }
-__global__ void k_demote16(const double2* __restrict__ in, __half2* out, int64_t n) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = __floats2half2_rn((float)in[i].x, (float)in[i].y);
+__global__ void k_group16(const double2* __restrict__ in, uint4* out, int64_t nsets, int64_t Vh) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // over nsets * 9 * Vh
+  if (t >= nsets * 9 * Vh) return;
+  const int64_t s = t % Vh, g = (t / Vh) % 9, set = t / (9 * Vh);
+  unsigned int w[4];
+  for (int q = 0; q < 4; ++q) {
+    const double2 v = in[(set * 36 + 4 * g + q) * Vh + s];
+    __half2 h = __floats2half2_rn((float)v.x, (float)v.y);
+    w[q] = *reinterpret_cast<unsigned int*>(&h);
+  }
+  out[t] = make_uint4(w[0], w[1], w[2], w[3]);
 }
 
 __global__ void k_clover_dense(LexGeom g, const double2* __restrict__ clov, double2* A) {
@@ -449,14 +465,14 @@ int clover_build(dd_clover* op, cudaStream_t st) {
   if (op->prec_mask & P32) {
     DD_TRY(op->clov[1].alloc(nclov * sizeof(float2)));
     DD_TRY(op->ainv[1].alloc(nainv * sizeof(float2)));
-    k_demote32<<<nblk(nclov, 256), 256, 0, st>>>((const double2*)op->clov[0].ptr, (float2*)op->clov[1].ptr, nclov);
-    k_demote32<<<nblk(nainv, 256), 256, 0, st>>>((const double2*)op->ainv[0].ptr, (float2*)op->ainv[1].ptr, nainv);
+    k_group32<<<nblk(2 * 18 * Vh, 256), 256, 0, st>>>((const double2*)op->clov[0].ptr, (float4*)op->clov[1].ptr, 2, Vh);
+    k_group32<<<nblk(18 * Vh, 256), 256, 0, st>>>((const double2*)op->ainv[0].ptr, (float4*)op->ainv[1].ptr, 1, Vh);
   }
   if (op->prec_mask & P16) {
     DD_TRY(op->clov[2].alloc(nclov * sizeof(__half2)));
     DD_TRY(op->ainv[2].alloc(nainv * sizeof(__half2)));
-    k_demote16<<<nblk(nclov, 256), 256, 0, st>>>((const double2*)op->clov[0].ptr, (__half2*)op->clov[2].ptr, nclov);
-    k_demote16<<<nblk(nainv, 256), 256, 0, st>>>((const double2*)op->ainv[0].ptr, (__half2*)op->ainv[2].ptr, nainv);
+    k_group16<<<nblk(2 * 9 * Vh, 256), 256, 0, st>>>((const double2*)op->clov[0].ptr, (uint4*)op->clov[2].ptr, 2, Vh);
+    k_group16<<<nblk(9 * Vh, 256), 256, 0, st>>>((const double2*)op->ainv[0].ptr, (uint4*)op->ainv[2].ptr, 1, Vh);
   }
   DD_CUDA(cudaGetLastError());
   return DD_OK;
