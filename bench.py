@@ -619,7 +619,11 @@ def main():
         # FGMRES(8) with the flexible preconditioner M_j = 64 CG steps on the
         # normal equations of Dhat: plain restarted FGMRES stalls near 2.5e-3
         # on this lattice at m0 = -0.4
-        for name, inner, restart in (("mixed", PREC[args.solve_inner], 8), ("fp64", PREC["f64"], 8)):
+        legs = [("mixed", PREC[args.solve_inner], 8), ("fp64", PREC["f64"], 8)]
+        if args.solve_inner != "f16":
+            # FP16 links and clover with FP32 vectors inside, same FP64 refinement
+            legs.insert(1, ("mixed_f16", PREC["f16"], 8))
+        for name, inner, restart in legs:
             x = torch.zeros_like(b)
             log(f"solve {name}")
             barrier(tdist)
@@ -634,11 +638,15 @@ def main():
                            "true_residual": st["true_residual"], "outer": st["outer_iterations"],
                            "inner_steps": st["inner_iterations"], "applies_inner": st["applies_inner"],
                            "applies_fp64": st["applies_fp64"],
-                           "inner_prec": {1: "f64", 2: "f32", 4: "f16"}[inner],
+                           "inner_prec": {1: "f64", 2: "f32", 4: "f16 links/clover, f32 vectors"}[inner],
                            "method": "even-odd FGMRES(8), M_j = 64 CG steps on Dhat^H Dhat, FP64 refinement"}
         d = (sols["mixed"] - sols["fp64"]).norm().item() / sols["fp64"].norm().item()
         solve["mixed_vs_fp64_solution_rel_diff"] = d
         solve["speedup_mixed_over_fp64"] = solve["fp64"]["seconds"] / solve["mixed"]["seconds"]
+        if "mixed_f16" in solve:
+            solve["mixed_f16_vs_fp64_solution_rel_diff"] = \
+                (sols["mixed_f16"] - sols["fp64"]).norm().item() / sols["fp64"].norm().item()
+            solve["speedup_mixed_f16_over_fp64"] = solve["fp64"]["seconds"] / solve["mixed_f16"]["seconds"]
 
     extra = None
     if not args.no_extra:

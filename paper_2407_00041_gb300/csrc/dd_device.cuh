@@ -56,6 +56,13 @@ __device__ __forceinline__ cx<R> cfmac(cx<R> a, cx<R> b, cx<R> acc) {
   acc.im = fma(-a.im, b.re, acc.im);
   return acc;
 }
+// acc + s * a (s real)
+template <typename R>
+__device__ __forceinline__ cx<R> caxpy(R s, cx<R> a, cx<R> acc) {
+  acc.re = fma(s, a.re, acc.re);
+  acc.im = fma(s, a.im, acc.im);
+  return acc;
+}
 // i * a, -i * a
 template <typename R>
 __device__ __forceinline__ cx<R> mul_i(cx<R> a) {
@@ -212,6 +219,31 @@ __device__ __forceinline__ void load_spinor(const HalfField& f, int64_t gstride,
         v[4 * g + k] = mk<R>(ff.x * s, ff.y * s);
       }
     }
+  }
+}
+
+// A neighbour spinor for the hopping term: FP16 values are returned without
+// their per-site scale, which is returned instead (and folded by the caller
+// into the hop's accumulation); FP32 / FP64 return 1.
+template <int P, typename R>
+__device__ __forceinline__ R load_spinor_unscaled(const HalfField& f, int64_t gstride, int64_t i, cx<R> v[12]) {
+  if constexpr (P == P16) {
+    const uint4* b = reinterpret_cast<const uint4*>(f.base) + i;
+    const float s = __ldg(f.scale + i);
+#pragma unroll
+    for (int g = 0; g < 3; ++g) {
+      uint4 t = __ldg(b + g * gstride);
+      unsigned int w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float2 ff = __half22float2(*reinterpret_cast<__half2*>(&w[k]));
+        v[4 * g + k] = mk<R>(ff.x, ff.y);
+      }
+    }
+    return (R)s;
+  } else {
+    load_spinor<P, R>(f, gstride, i, v);
+    return (R)1;
   }
 }
 

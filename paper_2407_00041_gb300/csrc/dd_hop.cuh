@@ -79,8 +79,6 @@ __device__ __forceinline__ void hop_regs(cx<R> acc[12], const cx<R> psi[12], con
       h0[c] = psi[c] - b0;
       h1[c] = psi[3 + c] - b1;
     }
-    h0[c] = sign * h0[c];
-    h1[c] = sign * h1[c];
   }
   cx<R> g0[3], g1[3];
 #pragma unroll
@@ -100,17 +98,13 @@ __device__ __forceinline__ void hop_regs(cx<R> acc[12], const cx<R> psi[12], con
   }
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    acc[c] = acc[c] + g0[c];
-    acc[3 + c] = acc[3 + c] + g1[c];
+    acc[c] = caxpy(sign, g0[c], acc[c]);
+    acc[3 + c] = caxpy(sign, g1[c], acc[3 + c]);
     cx<R> b0, b1;
     bh_times<MU>(g0[c], g1[c], b0, b1);
-    if constexpr (T > 0) {
-      acc[6 + c] = acc[6 + c] + b0;
-      acc[9 + c] = acc[9 + c] + b1;
-    } else {
-      acc[6 + c] = acc[6 + c] - b0;
-      acc[9 + c] = acc[9 + c] - b1;
-    }
+    const R sb = T > 0 ? sign : -sign;
+    acc[6 + c] = caxpy(sb, b0, acc[6 + c]);
+    acc[9 + c] = caxpy(sb, b1, acc[9 + c]);
   }
 }
 
@@ -280,11 +274,11 @@ __device__ __forceinline__ void hop_thread(const HopArgs& a, int64_t tid) {
     cx<R> psi[12];                                                                         \
     int nl = nb_fwd(a.g, sc, MU);                                                          \
     R sg = (MU == 0 && sc.c[0] == a.g.n[0] - 1) ? (R)a.g.t_bc : (R)1;                      \
-    load_spinor<PIN, R>(a.in[q], a.gstride, (int64_t)(nl >> 1) * a.nrhs + r, psi);         \
+    sg *= load_spinor_unscaled<PIN, R>(a.in[q], a.gstride, (int64_t)(nl >> 1) * a.nrhs + r, psi); \
     hop<PG, MU, TF, false, R>(acc, psi, a.U[p], s, Vh, sg);                                \
     nl = nb_bwd(a.g, sc, MU);                                                              \
     sg = (MU == 0 && sc.c[0] == 0) ? (R)a.g.t_bc : (R)1;                                   \
-    load_spinor<PIN, R>(a.in[q], a.gstride, (int64_t)(nl >> 1) * a.nrhs + r, psi);         \
+    sg *= load_spinor_unscaled<PIN, R>(a.in[q], a.gstride, (int64_t)(nl >> 1) * a.nrhs + r, psi); \
     hop<PG, MU, TB, true, R>(acc, psi, a.U[q], nl >> 1, Vh, sg);                           \
   }
   DD_HOP_DIR(0)
@@ -396,8 +390,8 @@ __device__ __forceinline__ void hop_thread_rb(const HopArgs& a, int64_t tid) {
     const int64_t ib = (int64_t)(nl >> 1) * a.nrhs + rb;                                            \
     _Pragma("unroll") for (int k = 0; k < NB; ++k) {                                                \
       cx<R> psi[12];                                                                                \
-      load_spinor<PIN, R>(a.in[q], a.gstride, ib + k * nrb, psi);                                   \
-      hop_regs<MU, FWD ? TF : TB, !FWD, R>(res[k], psi, u, sg);                                     \
+      const R sk = sg * load_spinor_unscaled<PIN, R>(a.in[q], a.gstride, ib + k * nrb, psi);        \
+      hop_regs<MU, FWD ? TF : TB, !FWD, R>(res[k], psi, u, sk);                                     \
     }                                                                                               \
   }
   DD_RB_HOP(0, true)
