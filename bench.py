@@ -502,6 +502,7 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the multi-RHS, batch, Dhat and adjoint lines")
     ap.add_argument("--solve-inner", default="f32", choices=["f32", "f16"])
     ap.add_argument("--dims", default="96x48x48x48", help="nT x nZ x nY x nX (a smaller lattice for profiling)")
+    ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides of the timed D psi (profiling)")
     ap.add_argument("--config5", action="store_true", help="run the 64^3x128, 8-RHS memory-fitted solve instead")
     ap.add_argument("--c5-batch", type=int, default=2)
     ap.add_argument("--c5-restart", type=int, default=8)
@@ -532,7 +533,8 @@ def main():
     V = int(np.prod(dims))
     log("generating links and spinor")
     U = synthetic.gauge(dims, eps=EPS)
-    psi = synthetic.spinor(dims, nrhs=1)
+    N = args.nrhs
+    psi = synthetic.spinor(dims, nrhs=N)
     log("building gauge and operator handles")
     lat = dd.Lattice(dims, -1)
     gauge = dd.Gauge(lat, U)
@@ -553,13 +555,13 @@ def main():
     head = None
     for prec in order:
         p = PREC[prec]
-        nbytes = op.field_bytes(p, 0, 1)
+        nbytes = op.field_bytes(p, 0, N)
         xin = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
         xout = torch.empty_like(xin)
-        op.pack(p, 0, psi_dev, xin, 1)
+        op.pack(p, 0, psi_dev, xin, N)
 
         def step():
-            dd.check(dd.lib.dd_apply(op.h, dd.DD_OP_D, p, xin.data_ptr(), xout.data_ptr(), 1,
+            dd.check(dd.lib.dd_apply(op.h, dd.DD_OP_D, p, xin.data_ptr(), xout.data_ptr(), N,
                                      dd.DD_LAYOUT_NATIVE, stream.cuda_stream), "dd_apply")
 
         log(f"timing D psi in {prec}")
@@ -568,21 +570,21 @@ def main():
         if prec == args.prec:
             gpu_launches += steps
         ms = total / steps * 1e3
-        gbs = aggregate_gbs(bytes_per_site(prec), V, world, total / steps)
+        gbs = aggregate_gbs(bytes_per_site(prec, N), V, world, total / steps)
         kern = statistics.mean(per)
-        achieved = bytes_per_site(prec) * V / kern / 1e9
-        gflops = FLOPS_PER_SITE * V / kern / 1e9
+        achieved = bytes_per_site(prec, N) * V / kern / 1e9
+        gflops = FLOPS_PER_SITE * N * V / kern / 1e9
         bound = "hbm"
         peak, unit, frac = peaks["hbm_gbs"], "GB/s", achieved / peaks["hbm_gbs"]
         alu_peak = f64_peak if prec == "f64" else f32_peak
         if gflops * 1e9 / alu_peak > frac:  # the arithmetic pipe is the closer roof
             bound, peak, unit, frac = "alu", alu_peak / 1e12, "TFLOP/s", gflops * 1e9 / alu_peak
             achieved = gflops / 1e3
-        variants[prec] = {"gbs": gbs, "ms_per_apply": ms, "hbm_frac": bytes_per_site(prec) * V / kern / 1e9 /
+        variants[prec] = {"gbs": gbs, "ms_per_apply": ms, "hbm_frac": bytes_per_site(prec, N) * V / kern / 1e9 /
                           peaks["hbm_gbs"], "gflops_nominal": gflops, "bound": bound,
-                          "roof_frac": frac, "bytes_per_site": bytes_per_site(prec)}
+                          "roof_frac": frac, "bytes_per_site": bytes_per_site(prec, N)}
         if prec == args.prec:
-            traffic = profile_traffic(prec)
+            traffic = profile_traffic(prec) if N == 1 else None
             head = {"value": gbs, "ms": ms, "kernel_s": kern,
                     "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": frac,
                                  "traffic": traffic,
@@ -590,7 +592,7 @@ def main():
                                  else "FMA-chain probe dd_probe_flops on this GPU"}}
             # parity of the timed launch configuration on a sample of sites
             out_c = torch.empty_like(psi_dev)
-            op.unpack(p, 0, xout, out_c, 1)
+            op.unpack(p, 0, xout, out_c, N)
             head["_out"] = out_c
         del xin, xout
 
@@ -600,21 +602,21 @@ def main():
     hout = torch.empty_like(hin).pin_memory()
 
     def e2e_step():
-        dd.check(dd.lib.dd_apply(op.h, dd.DD_OP_D, p, hin.data_ptr(), hout.data_ptr(), 1,
+        dd.check(dd.lib.dd_apply(op.h, dd.DD_OP_D, p, hin.data_ptr(), hout.data_ptr(), N,
                                  dd.DD_LAYOUT_CANONICAL_HOST, stream.cuda_stream), "dd_apply host")
 
     log("timing the host-buffer path")
     e2e_steps = max(3, min(args.steps, 20))
     e_total, _ = time_steps(e2e_step, e2e_steps, 1, stream, tdist, None)
-    e2e = {"value": bytes_per_site(args.prec) * V * world / (e_total / e2e_steps) / 1e9, "unit": "GB/s",
-           "h2d_bytes_per_step": V * 12 * 16, "d2h_bytes_per_step": V * 12 * 16,
+    e2e = {"value": bytes_per_site(args.prec, N) * V * world / (e_total / e2e_steps) / 1e9, "unit": "GB/s",
+           "h2d_bytes_per_step": V * 12 * 16 * N, "d2h_bytes_per_step": V * 12 * 16 * N,
            "ms_per_step": e_total / e2e_steps * 1e3}
 
     # solves: mixed-precision vs plain FP64, time to ||b - D x|| < 1e-10 ||b||
     solve = None
     if not args.no_solve:
         solve = {}
-        b = psi_dev
+        b = psi_dev[:1].contiguous()
         sols = {}
         # FGMRES(8) with the flexible preconditioner M_j = 64 CG steps on the
         # normal equations of Dhat: plain restarted FGMRES stalls near 2.5e-3
@@ -677,8 +679,9 @@ def main():
         "value": head["value"], "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"f64": "f64", "f32": "f32", "f16": "f32 (fp16 storage)"}[args.prec], "data": "synthetic",
-        "config": {"workload": WORKLOAD if dims == DIMS else WORKLOAD.replace("48^3x96", args.dims),
-                   "precision": args.prec, "nrhs": 1, "sites": V,
+        "config": {"workload": (WORKLOAD if dims == DIMS else WORKLOAD.replace("48^3x96", args.dims)).replace(
+                       "1 RHS", f"{N} RHS"),
+                   "precision": args.prec, "nrhs": N, "sites": V,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "inputs (>8 GB) larger than L2; no flush"},
         "roofline": head["roofline"], "variants": variants, "e2e": e2e, "solve": solve,
