@@ -184,6 +184,14 @@ def aggregate_gbs(bytes_per_unit, units_per_rank, world, seconds_max):
 
 
 # ---------------------------------------------------------------- timing
+def device_status(dd):
+    """The library's device flag for expired waits (0: none since the last read)."""
+    import ctypes
+    f = ctypes.c_int(-1)
+    dd.check(dd.lib.dd_device_status(ctypes.byref(f)), "dd_device_status")
+    return f.value
+
+
 def time_steps(fn, steps, warmup, stream, tdist, clocks):
     """W untimed steps, then exactly K timed steps bracketed by barrier + sync.
     Returns (total seconds max over ranks, per-step seconds list)."""
@@ -567,6 +575,8 @@ def main():
         log(f"timing D psi in {prec}")
         steps = args.steps if prec == args.prec else max(10, min(args.steps, 50))
         total, per = time_steps(step, steps, args.warmup, stream, tdist, clocks if prec == args.prec else None)
+        log(f"  {prec}: per-step ms min {min(per) * 1e3:.4f} max {max(per) * 1e3:.4f}; "
+            f"device wait status {device_status(dd)}")
         if prec == args.prec:
             gpu_launches += steps
         ms = total / steps * 1e3

@@ -287,6 +287,16 @@ int dd_dot_noalloc(const double* a, const double* b, int64_t nsites, int nrhs, d
  * Synchronises `stream`. */
 int dd_probe_flops(int prec, double* flops_per_second, void* stream);
 
+/* ---- device wait status ----
+ * Kernels that wait on asynchronous copies (the row-staged stencil of
+ * dd_apply, which moves neighbour rows into shared memory with bulk copies
+ * completing on mbarriers) bound every wait in time; a wait that expires
+ * makes the kernel record it in a device flag, skip the rest of its work and
+ * return.  This call synchronises the device, writes the flag to *flags_out
+ * (0: no wait has expired since the last call) and clears it.  The thesis has
+ * no counterpart; the outputs of a launch that set the flag are invalid. */
+int dd_device_status(int* flags_out);
+
 #ifdef __cplusplus
 }
 #endif

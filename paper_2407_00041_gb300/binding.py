@@ -77,6 +77,7 @@ SIGNATURES = {
     "dd_apply_batched_graph": (_I, [_P, _P, _P, _P]),
     "dd_dot": (_I, [_P, _P, _L, _I, _P, _P]),
     "dd_probe_flops": (_I, [_I, _P, _P]),
+    "dd_device_status": (_I, [_P]),
     "dd_dot_noalloc": (_I, [_P, _P, _L, _I, _P, _P]),
 }
 

@@ -5,6 +5,7 @@
 
 #include "dd_blas.h"
 #include "dd_internal.h"
+#include "dd_ops.h"
 
 namespace dd {
 const char* last_error();
@@ -57,6 +58,16 @@ const char* dd_error_string(int status) {
 const char* dd_last_error_detail(void) { return last_error(); }
 
 int dd_version(void) { return 100; }
+
+int dd_device_status(int* flags_out) {
+  if (!flags_out) return fail(DD_ERR_ARG, "null flags_out");
+  int* flag = device_error_flag();
+  if (!flag) return fail(DD_ERR_CUDA, "device status flag unavailable");
+  DD_CUDA(cudaDeviceSynchronize());
+  DD_CUDA(cudaMemcpy(flags_out, flag, sizeof(int), cudaMemcpyDeviceToHost));
+  DD_CUDA(cudaMemset(flag, 0, sizeof(int)));
+  return DD_OK;
+}
 
 int dd_lattice_create(const int dims[4], int t_bc, dd_lattice** out) {
   if (!dims || !out) return fail(DD_ERR_ARG, "null argument");

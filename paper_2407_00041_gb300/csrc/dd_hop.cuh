@@ -475,6 +475,12 @@ inline int rhs_block_limit() {
   return v;
 }
 
+}  // namespace dd
+
+#include "dd_stage.cuh"
+
+namespace dd {
+
 // Host launchers; the instantiation units explicitly instantiate one
 // precision triple each, other units only see the declarations in dd_ops.h.
 template <int PG, int PIN, int POUT>
@@ -486,6 +492,11 @@ cudaError_t launch_hop(const HopArgs& a, bool dagger, int epi, cudaStream_t st) 
   // several right-hand sides: RHS-blocked variant (not for FP64, which is
   // bound by the FP64 pipe, nor for the residual / add epilogues)
   const int rbmax = rhs_block_limit();
+
+  if constexpr (PIN == P32 && POUT == P32 && PG != P64) {
+    cudaError_t e = cudaSuccess;
+    if (epi == EPI_D && launch_stage<PG>(a, dagger, st, &e)) return e;
+  }
 
   if (PG != P64 && rbmax >= 2 && (epi == EPI_D || epi == EPI_AINV) && a.nrhs >= 2 && a.nrhs % 2 == 0) {
     // measured on 32^4: blocks of 4 win from 16 RHS up, blocks of 2 below

@@ -1,6 +1,7 @@
 // Operator layer: D, D^H, D_sc and the even-odd pieces built from the fused
 // stencil kernel, plus handle helpers and error reporting.
 #include <cstdio>
+#include <mutex>
 #include <string>
 
 #include "dd_internal.h"
@@ -95,6 +96,17 @@ int64_t stencil_bytes_per_site(int pg, int nrhs) {
 // stencil (bytes_per_site per site), well inside L2; DD_ZBLOCK overrides
 // (0 = no slabs).  Measured at 48^3 x 96: 16 for FP32 with one RHS (+4%);
 // at 32^4 with 12 RHS: 8 (+13%).
+int* device_error_flag() {
+  static int* flag = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    if (cudaMalloc(&p, sizeof(int)) == cudaSuccess && cudaMemset(p, 0, sizeof(int)) == cudaSuccess)
+      flag = static_cast<int*>(p);
+  });
+  return flag;
+}
+
 int zblock_for(const int dims[4], int64_t bytes_per_site) {
   static int forced = -2;
   if (forced == -2) {

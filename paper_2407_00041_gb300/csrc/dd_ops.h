@@ -45,6 +45,9 @@ template <int PG, int PIN, int POUT>
 cudaError_t launch_hop(const HopArgs& a, bool dagger, int epi, cudaStream_t st);
 // traversal slab depth for a lattice and the bytes per site of the stencil (dd_ops.cu)
 int zblock_for(const int dims[4], int64_t bytes_per_site);
+// Device flag that kernels with bounded waits set when a wait expires (one
+// int, allocated and zeroed on first use; nullptr if that fails).
+int* device_error_flag();
 int64_t stencil_bytes_per_site(int pg, int nrhs);
 template <int PG, int PIN, int POUT>
 cudaError_t launch_block(const BlockArgs& a, cudaStream_t st);

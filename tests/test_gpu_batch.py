@@ -18,6 +18,18 @@ def _arr(vals, t=ctypes.c_void_p):
     return (t * len(vals))(*vals)
 
 
+def _close(op, prec, a, b, n):
+    if prec == dd.DD_PREC_F16:
+        return torch.equal(a, b)  # FP16 storage: the same kernel body on both paths
+    shape = (n, op.lattice.V, 12)
+    ua = torch.empty(shape, dtype=torch.complex128, device="cuda")
+    ub = torch.empty_like(ua)
+    op.unpack(prec, 0, a, ua, n)
+    op.unpack(prec, 0, b, ub, n)
+    torch.cuda.synchronize()
+    return ((ua - ub).norm() / ub.norm()).item() < 1e-6
+
+
 @pytest.mark.parametrize("prec", [dd.DD_PREC_F32, dd.DD_PREC_F16])
 def test_batched_matches_single_and_oracle(prec):
     shapes = [(4, 4, 4, 4), (2, 4, 6, 8), (8, 8, 8, 8), (6, 4, 4, 2)]
@@ -47,8 +59,11 @@ def test_batched_matches_single_and_oracle(prec):
     try:
         dd.check(dd.lib.dd_apply_batched(b, pin, pout, st), "dd_apply_batched")
         torch.cuda.synchronize()
-        for o, r in zip(outs, refs):
-            assert torch.equal(o, r)  # same kernel body, same arithmetic: bit-identical
+        first = [o.clone() for o in outs]
+        for o, r, op, n in zip(outs, refs, ops, nrhs):
+            # single applies of FP32 fields run the row-staged kernel, which
+            # sums the same terms in another rounding order
+            assert _close(op, prec, o, r, n)
         chosen = (ctypes.c_int * 3)()
         dd.check(dd.lib.dd_batch_tune(b, pin, pout, st, chosen), "dd_batch_tune")
         assert chosen[0] in (64, 128, 256) and chosen[2] >= 0  # 0: one CTA per work item
@@ -57,8 +72,8 @@ def test_batched_matches_single_and_oracle(prec):
         dd.check(dd.lib.dd_apply_batched_graph(b, pin, pout, st), "graph capture")
         dd.check(dd.lib.dd_apply_batched_graph(b, pin, pout, st), "graph replay")
         torch.cuda.synchronize()
-        for o, r in zip(outs, refs):
-            assert torch.equal(o, r)
+        for o, f in zip(outs, first):
+            assert torch.equal(o, f)  # the tuned and replayed launch: same arithmetic, same bits
         # wrong pointers for a captured graph are refused
         bad = _arr([x.data_ptr() for x in refs])
         assert dd.lib.dd_apply_batched_graph(b, pin, bad, st) == dd.DD_ERR_ARG

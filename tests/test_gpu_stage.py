@@ -1,0 +1,92 @@
+"""The row-staged stencil (neighbour rows moved into shared memory by bulk
+asynchronous copies; opt-in with DD_STAGE=1) against the CPU oracle and
+against the per-thread-load kernels, on lattices where every CTA walks
+several tiles, with one row of outputs per CTA from 1 x 1 up to the
+512-thread limit; and the device wait status stays clear.  The library reads
+DD_STAGE once per process, so the staged runs happen in child processes."""
+import ctypes
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+import paper_2407_00041_gb300 as dd
+from tests._gpu import CSW, M0, TOL, apply, make, rel
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+# (dims, nrhs): hx * nrhs outputs per tile
+CASES = [
+    ((16, 8, 8, 16), 12),  # 96 threads, 2048 tiles: several per CTA
+    ((8, 4, 6, 2), 5),  # hx = 1: both X neighbours are the same site
+    ((4, 4, 4, 64), 16),  # 512 threads (wide kernel)
+    ((6, 8, 4, 8), 1),  # one RHS, 4 outputs per tile
+]
+
+
+def _device_status():
+    f = ctypes.c_int(-1)
+    dd.check(dd.lib.dd_device_status(ctypes.byref(f)), "dd_device_status")
+    return f.value
+
+
+STAGED = os.environ.get("DD_STAGE") == "1"
+
+
+def test_staged_kernel_parity_in_child_process():
+    env = dict(os.environ, DD_STAGE="1")
+    res = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "tests/test_gpu_stage.py", "-k",
+                          "match_oracle"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert res.returncode == 0, res.stdout[-2000:] + res.stderr[-2000:]
+    assert "4 passed" in res.stdout, res.stdout[-500:]
+
+
+@pytest.mark.skipif(not STAGED, reason="runs in the child process with DD_STAGE=1")
+@pytest.mark.parametrize("dims,nrhs", CASES, ids=lambda v: "x".join(map(str, v)) if isinstance(v, tuple) else str(v))
+@pytest.mark.parametrize("prec", [dd.DD_PREC_F32])
+def test_staged_D_and_DH_match_oracle(dims, nrhs, prec):
+    U, lat, g, op = make(dims)
+    A = oracle.clover(U, dims, M0, CSW)
+    psi = synthetic.spinor(dims, nrhs=nrhs)
+    got = apply(op, dd.DD_OP_D, prec, psi)
+    gotH = apply(op, dd.DD_OP_DH, prec, psi)
+    for r in range(nrhs):
+        x = psi[r].reshape(-1, 12)
+        assert rel(got[r], oracle.apply_D(U, A, x, dims)) < TOL[prec]
+        assert rel(gotH[r], oracle.apply_DH(U, A, x, dims)) < TOL[prec]
+    assert _device_status() == 0
+
+
+def test_staged_matches_unstaged_kernels(tmp_path):
+    """Same inputs through the staged kernel and (DD_STAGE=0) the per-thread
+    load kernels: FP32 results agree to rounding."""
+    script = tmp_path / "run.py"
+    script.write_text(
+        "import sys, numpy as np\n"
+        f"sys.path.insert(0, {ROOT!r})\n"
+        "import synthetic, paper_2407_00041_gb300 as dd\n"
+        "from tests._gpu import make, apply\n"
+        "out = []\n"
+        "for dims, n in (((16, 8, 8, 16), 12), ((8, 8, 8, 8), 1)):\n"
+        "    U, lat, g, op = make(dims)\n"
+        "    psi = synthetic.spinor(dims, nrhs=n)\n"
+        "    out.append(apply(op, dd.DD_OP_D, dd.DD_PREC_F32, psi))\n"
+        "    out.append(apply(op, dd.DD_OP_DH, dd.DD_PREC_F16, psi))\n"
+        "np.savez(sys.argv[1], *out)\n")
+    res = {}
+    for flag in ("1", "0"):  # staged, then the default kernels
+        path = tmp_path / f"out{flag}.npz"
+        env = dict(os.environ, DD_STAGE=flag)
+        p = subprocess.run([sys.executable, str(script), str(path)], cwd=ROOT, env=env, capture_output=True,
+                           text=True, timeout=600)
+        assert p.returncode == 0, p.stdout[-2000:] + p.stderr[-2000:]
+        res[flag] = np.load(path)
+    for k in res["1"].files:
+        a, b = res["1"][k], res["0"][k]
+        assert rel(a, b) < 1e-6, k
