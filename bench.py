@@ -53,6 +53,10 @@ WORKLOAD = "48^3x96 Wilson-clover D.psi, 1 RHS, eps=0.3 SU(3) links, m0=-0.4, c_
 BYTES = {"f64": (1152, 384), "f32": (576, 192), "f16": (288, 104)}
 PREC = {"f64": 1, "f32": 2, "f16": 4}
 FLOPS_PER_SITE = 1848  # nominal: hopping 1320 + self coupling 504 + combine 24
+# link force with the clover term, one RHS, as the kernels compute it (an FMA
+# counts 2): hopping outer products 4 x 336, clover leaf derivatives 6 planes x
+# (T 720 + T' 36 + 4 leaves x 8 products x 216), su(3) projection 4 x 242
+FORCE_FLOPS_PER_SITE = 4 * 336 + 6 * (720 + 36 + 4 * 8 * 216) + 4 * 242
 
 
 _T0 = time.time()
@@ -344,7 +348,7 @@ def _time_fn(fn, reps, warmup=3):
     return e0.elapsed_time(e1) / reps * 1e-3
 
 
-def extra_measurements(dd, torch, stream, op48, psi48, V48, tdist, clocks):
+def extra_measurements(dd, torch, stream, op48, psi48, V48, tdist, clocks, alu_peaks):
     """Multi-RHS D psi at 32^4 x 12 RHS, the batched uneven-lattice launch
     (8^4 x 1, 16^4 x 5, 24^4 x 17, 32^4 x 32 RHS) against one launch per
     lattice, Dhat at 48^3 x 96, and the autograd adjoint at 24^4."""
@@ -431,7 +435,11 @@ def extra_measurements(dd, torch, stream, op48, psi48, V48, tdist, clocks):
         t_f = _time_fn(lambda: o24.force(p, phi, ps, 1, True, G=G, F=F), 5, warmup=1)
         tmp = torch.empty_like(phi)
         t_dh = _time_fn(lambda: o24.apply(dd.DD_OP_DH, p, phi, tmp, 1), 10)
-        out[f"adjoint_24x4_{name}"] = {"ms_link_force_with_clover": t_f * 1e3, "ms_DH_canonical": t_dh * 1e3}
+        peak = alu_peaks[name]
+        out[f"adjoint_24x4_{name}"] = {"ms_link_force_with_clover": t_f * 1e3, "ms_DH_canonical": t_dh * 1e3,
+                                      "force_gflops_nominal": FORCE_FLOPS_PER_SITE * V24 / t_f / 1e9,
+                                      "force_alu_frac": FORCE_FLOPS_PER_SITE * V24 / t_f / peak,
+                                      "force_flops_per_site": FORCE_FLOPS_PER_SITE}
     return out
 
 
@@ -663,7 +671,8 @@ def main():
     extra = None
     if not args.no_extra:
         log("extra measurements (multi-RHS, batch, Dhat, adjoint)")
-        extra = extra_measurements(dd, torch, stream, op, psi_dev, V, tdist, clocks)
+        extra = extra_measurements(dd, torch, stream, op, psi_dev, V, tdist, clocks,
+                                   {"f64": f64_peak, "f32": f32_peak})
 
     rows = clocks.stop()
     clk = clocks.summary(rows)

@@ -46,9 +46,12 @@ namespace dd {
 
 namespace {
 
+// Resident CTAs asked of the compiler: about 168 registers per thread for 64
+// and 128 threads (the RHS-blocked body holds two sets of accumulators; fewer
+// registers spill hundreds of bytes), 128 for 256 threads.
 template <int THREADS>
 struct BatchMinBlocks {
-  static constexpr int value = THREADS >= 256 ? 2 : 640 / THREADS;
+  static constexpr int value = THREADS >= 256 ? 2 : 384 / THREADS;
 };
 
 template <int P, int THREADS>
@@ -60,7 +63,7 @@ __global__ void __launch_bounds__(THREADS, BatchMinBlocks<THREADS>::value)
     while (l + 1 < count && item >= item_start[l + 1]) ++l;  // items only grow within a CTA
     const HopArgs& a = args[l];
     const int64_t tid = (item - item_start[l]) * THREADS + threadIdx.x;
-    if (tid < (int64_t)a.g.Vh * (a.nrhs / a.rhs_block) * a.npar) {
+    if (tid < (int64_t)a.g.Vh * ((a.nrhs + a.rhs_block - 1) / a.rhs_block) * a.npar) {
       if (a.rhs_block == 2)
         hop_thread_rb<P, P, P, false, EPI_D, 2>(a, tid);
       else
@@ -82,7 +85,7 @@ int stage(dd_batch* b, const void* const* ins, void* const* outs, cudaStream_t s
     HopArgs& a = b->h_args[i];
     a.g = lat->geom();
     a.g.zblock = zblock_for(lat->dims, stencil_bytes_per_site(b->prec, b->nrhs[i]));
-    a.rhs_block = b->nrhs[i] % 2 == 0 ? 2 : 1;
+    a.rhs_block = rb_worth(b->nrhs[i]) ? 2 : 1;
     a.nrhs = b->nrhs[i];
     a.p0 = 0;
     a.npar = 2;
@@ -98,7 +101,7 @@ int stage(dd_batch* b, const void* const* ins, void* const* outs, cudaStream_t s
       a.M[p] = op->M(pi, p);
     }
     a.beta = -0.5;
-    const int64_t slots = 2 * lat->Vh * (b->nrhs[i] / a.rhs_block);
+    const int64_t slots = 2 * lat->Vh * ((b->nrhs[i] + a.rhs_block - 1) / a.rhs_block);
     starts[i + 1] = starts[i] + (slots + b->tile - 1) / b->tile;
   }
   b->total_items = starts[b->count];

@@ -344,7 +344,7 @@ template <int PG, int PIN, int POUT, bool DAG, int EPI, int NB>
 __device__ __forceinline__ void hop_thread_rb(const HopArgs& a, int64_t tid) {
   using R = typename Store<PG>::real;
   using E = typename Store<PG>::elem;
-  const int nrb = a.nrhs / NB;
+  const int nrb = (a.nrhs + NB - 1) / NB;  // RHS blocks; the last one may be short
   int p, s, rb;
   SiteCoord sc;
   if (a.npar == 2) {
@@ -366,6 +366,11 @@ __device__ __forceinline__ void hop_thread_rb(const HopArgs& a, int64_t tid) {
   const R beta = (R)a.beta;
   const void* M = a.M[p];
   const int64_t ibase = (int64_t)s * a.nrhs + rb;
+  // offset of RHS k of the block; a RHS past the end (N not a multiple of
+  // NB) recomputes RHS rb and is not stored
+  int koff[NB];
+#pragma unroll
+  for (int k = 0; k < NB; ++k) koff[k] = rb + k * nrb < a.nrhs ? k * nrb : 0;
 
   cx<R> res[NB][12];
 #pragma unroll
@@ -374,7 +379,7 @@ __device__ __forceinline__ void hop_thread_rb(const HopArgs& a, int64_t tid) {
     for (int c = 0; c < 12; ++c) res[k][c] = zero<R>();
     if constexpr (EPI == EPI_D) {
       cx<R> y[12];
-      load_spinor<PIN, R>(a.y[p], a.gstride, ibase + k * nrb, y);
+      load_spinor<PIN, R>(a.y[p], a.gstride, ibase + koff[k], y);
       block_apply_g<PG, true, R>(M, s, Vh, y, res[k], false);
     }
   }
@@ -390,7 +395,7 @@ __device__ __forceinline__ void hop_thread_rb(const HopArgs& a, int64_t tid) {
     const int64_t ib = (int64_t)(nl >> 1) * a.nrhs + rb;                                            \
     _Pragma("unroll") for (int k = 0; k < NB; ++k) {                                                \
       cx<R> psi[12];                                                                                \
-      const R sk = sg * load_spinor_unscaled<PIN, R>(a.in[q], a.gstride, ib + k * nrb, psi);        \
+      const R sk = sg * load_spinor_unscaled<PIN, R>(a.in[q], a.gstride, ib + koff[k], psi);        \
       hop_regs<MU, FWD ? TF : TB, !FWD, R>(res[k], psi, u, sk);                                     \
     }                                                                                               \
   }
@@ -406,6 +411,7 @@ __device__ __forceinline__ void hop_thread_rb(const HopArgs& a, int64_t tid) {
 
 #pragma unroll
   for (int k = 0; k < NB; ++k) {
+    if (koff[k] != k * nrb) continue;  // past the last RHS
     if constexpr (EPI == EPI_AINV) {
       // out_k = M (beta acc_k)
 #pragma unroll
@@ -424,7 +430,7 @@ __device__ __forceinline__ void hop_thread_rb(const HopArgs& a, int64_t tid) {
 template <int PG, int PIN, int POUT, bool DAG, int EPI, int NB>
 __global__ void __launch_bounds__(128, NB >= 4 ? 2 : 3) k_hop_rb(const HopArgs a) {
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= (int64_t)a.g.Vh * (a.nrhs / NB) * a.npar) return;
+  if (tid >= (int64_t)a.g.Vh * ((a.nrhs + NB - 1) / NB) * a.npar) return;
   hop_thread_rb<PG, PIN, POUT, DAG, EPI, NB>(a, tid);
 }
 
@@ -481,6 +487,10 @@ inline int rhs_block_limit() {
 
 namespace dd {
 
+// RHS counts that take the RHS-blocked kernel: every even count, and odd
+// counts from 5 up (one thread of every site then carries a short block).
+inline bool rb_worth(int nrhs) { return nrhs >= 2 && (nrhs % 2 == 0 || nrhs >= 5); }
+
 // Host launchers; the instantiation units explicitly instantiate one
 // precision triple each, other units only see the declarations in dd_ops.h.
 template <int PG, int PIN, int POUT>
@@ -498,10 +508,10 @@ cudaError_t launch_hop(const HopArgs& a, bool dagger, int epi, cudaStream_t st) 
     if (epi == EPI_D && launch_stage<PG>(a, dagger, st, &e)) return e;
   }
 
-  if (PG != P64 && rbmax >= 2 && (epi == EPI_D || epi == EPI_AINV) && a.nrhs >= 2 && a.nrhs % 2 == 0) {
+  if (PG != P64 && rbmax >= 2 && (epi == EPI_D || epi == EPI_AINV) && rb_worth(a.nrhs)) {
     // measured on 32^4: blocks of 4 win from 16 RHS up, blocks of 2 below
     const int NBsel = (a.nrhs % 4 == 0 && a.nrhs >= 16 && rbmax >= 4) ? 4 : 2;
-    const int64_t nt = (int64_t)a.g.Vh * (a.nrhs / NBsel) * a.npar;
+    const int64_t nt = (int64_t)a.g.Vh * ((a.nrhs + NBsel - 1) / NBsel) * a.npar;
     const unsigned bl = (unsigned)((nt + threads - 1) / threads);
     const int key = (epi == EPI_D ? 0 : 4) + (dagger ? 2 : 0) + (NBsel == 4 ? 1 : 0);
     switch (key) {
