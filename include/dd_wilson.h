@@ -236,6 +236,9 @@ int dd_solve(dd_clover* op, const dd_solve_params* params, const void* b, void* 
  * with_clover = 0 holds the self coupling fixed (hopping terms only); 1 also
  * differentiates A(x) through Q_munu (Eq. 1.11, 1.12).  prec: DD_PREC_F64 or
  * DD_PREC_F32 (arithmetic precision; outputs are FP64).  Enqueued on stream.
+ * DD_PREC_F32 accumulates in a workspace owned by the operator handle
+ * (80 bytes per link, kept between calls), so FP32 force calls on one handle
+ * must not overlap on the GPU.
  */
 int dd_force(dd_clover* op, int prec, const double* phi, const double* psi, int nrhs, int with_clover, double* G,
              double* F, void* stream);

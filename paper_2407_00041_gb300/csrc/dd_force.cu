@@ -126,10 +126,25 @@ __device__ __forceinline__ void load_canon(const double2* f, int64_t site, cx<R>
   }
 }
 
+// G storage: FP64 as 9 double2 per link; the FP32 path accumulates in 20
+// floats per link (18 used) and converts at the end.
+__device__ __forceinline__ void store_link_g(double2* G, int64_t t, const cx<double> v[9]) {
+#pragma unroll
+  for (int e = 0; e < 9; ++e) G[t * 9 + e] = make_double2(v[e].re, v[e].im);
+}
+__device__ __forceinline__ void store_link_g(float* G, int64_t t, const cx<float> v[9]) {
+  float4* o = reinterpret_cast<float4*>(G + t * 20);
+  o[0] = make_float4(v[0].re, v[0].im, v[1].re, v[1].im);
+  o[1] = make_float4(v[2].re, v[2].im, v[3].re, v[3].im);
+  o[2] = make_float4(v[4].re, v[4].im, v[5].re, v[5].im);
+  o[3] = make_float4(v[6].re, v[6].im, v[7].re, v[7].im);
+  o[4] = make_float4(v[8].re, v[8].im, 0.f, 0.f);
+}
+
 // One thread per link (x, mu): hopping contribution, written (not added).
-template <typename R>
+template <typename R, typename GT>
 __global__ void k_force_hop(FGeom g, const double2* __restrict__ phi, const double2* __restrict__ psi, int nrhs,
-                            double2* G) {
+                            GT* G) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= g.V * 4) return;
   const int x = (int)(t >> 2), mu = (int)(t & 3);
@@ -175,7 +190,8 @@ __global__ void k_force_hop(FGeom g, const double2* __restrict__ phi, const doub
   }
   const R f = (R)(-0.5) * s;
 #pragma unroll
-  for (int e = 0; e < 9; ++e) G[t * 9 + e] = make_double2((double)(f * acc[e].re), (double)(f * acc[e].im));
+  for (int e = 0; e < 9; ++e) acc[e] = f * acc[e];
+  store_link_g(G, t, acc);
 }
 
 __device__ __forceinline__ cx<double> Bm(int mu, int i, int j) {
@@ -216,10 +232,35 @@ __device__ __forceinline__ void atomic_add_m3(double2* G, const M3<R>& m, bool d
     }
 }
 
+// FP32 accumulator: a link's 3x3 complex matrix as 18 floats padded to 20
+// (80 bytes, 16-byte aligned), added with 16-byte vector reductions.
+constexpr int kGf = 20;
+
+__device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d)
+               : "memory");
+}
+
+__device__ __forceinline__ void atomic_add_m3(float* G, const M3<float>& m, bool dagger) {
+  float v[kGf];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const cx<float> e = dagger ? mk(m.m[3 * j + i].re, -m.m[3 * j + i].im) : m.m[3 * i + j];
+      v[2 * (3 * i + j)] = e.re;
+      v[2 * (3 * i + j) + 1] = e.im;
+    }
+  v[18] = v[19] = 0.f;
+#pragma unroll
+  for (int q = 0; q < kGf / 4; ++q) red_add_v4(G + 4 * q, v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+}
+
 // One thread per site: self-coupling contribution, accumulated atomically.
-template <typename R>
+template <typename R, typename GT>
 __global__ void k_force_clover(FGeom g, const double2* __restrict__ U64, const double2* __restrict__ phi,
-                               const double2* __restrict__ psi, int nrhs, double csw, double2* G) {
+                               const double2* __restrict__ psi, int nrhs, double csw, GT* G) {
+  constexpr int kStride = sizeof(GT) == sizeof(float) ? kGf : 9;  // elements of GT per link
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= g.V) return;
   int c[4];
@@ -277,7 +318,7 @@ __global__ void k_force_clover(FGeom g, const double2* __restrict__ U64, const d
         auto emit = [&](int k, const M3<R>& Rk) {
           const int* sc = site[l][k];
           const int lex = ((sc[0] * g.n[1] + sc[1]) * g.n[2] + sc[2]) * g.n[3] + sc[3];
-          atomic_add_m3<R>(G + ((int64_t)lex * 4 + dir[l][k]) * 9, Rk, dag[l][k] == 0);
+          atomic_add_m3(G + ((int64_t)lex * 4 + dir[l][k]) * kStride, Rk, dag[l][k] == 0);
         };
         const M3<R> S2 = mmul(F[3], Tp);
         const M3<R> S1 = mmul(F[2], S2);
@@ -290,16 +331,30 @@ __global__ void k_force_clover(FGeom g, const double2* __restrict__ U64, const d
     }
 }
 
+__device__ __forceinline__ cx<double> load_g(const double2* G, int64_t t, int e) {
+  return mk(G[t * 9 + e].x, G[t * 9 + e].y);
+}
+__device__ __forceinline__ cx<double> load_g(const float* G, int64_t t, int e) {
+  return mk((double)G[t * kGf + 2 * e], (double)G[t * kGf + 2 * e + 1]);
+}
+
+// FP32 accumulator -> the caller's FP64 G
+__global__ void k_force_widen(int64_t nlinks, const float* __restrict__ Gf, double2* G) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nlinks) return;
+  for (int e = 0; e < 9; ++e) G[t * 9 + e] = make_double2((double)Gf[t * kGf + 2 * e], (double)Gf[t * kGf + 2 * e + 1]);
+}
+
 // F = P(G U^H)
-__global__ void k_force_project(FGeom g, const double2* __restrict__ U64, const double2* __restrict__ G,
-                                double2* F) {
+template <typename GT>
+__global__ void k_force_project(FGeom g, const double2* __restrict__ U64, const GT* __restrict__ G, double2* F) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= g.V * 4) return;
   const int x = (int)(t >> 2), mu = (int)(t & 3);
   int c[4];
   coords_of(g, x, c);
   M3<double> u = load_link<double>(g, U64, c, mu), gm;
-  for (int e = 0; e < 9; ++e) gm.m[e] = mk(G[t * 9 + e].x, G[t * 9 + e].y);
+  for (int e = 0; e < 9; ++e) gm.m[e] = load_g(G, t, e);
   M3<double> M = mmul(gm, mdag(u));
   cx<double> f[9];
   for (int i = 0; i < 3; ++i)
@@ -316,35 +371,36 @@ int force(dd_clover* op, int prec, const double* phi, const double* psi, int nrh
           double* F, cudaStream_t st) {
   const dd_lattice* lat = op->lat;
   const FGeom g = fgeom(lat);
-  DevBuf gtmp;
-  double2* Gd = reinterpret_cast<double2*>(G);
-  if (!Gd) {
-    DD_TRY(gtmp.alloc((size_t)lat->V * 4 * 9 * sizeof(double2)));
-    Gd = reinterpret_cast<double2*>(gtmp.ptr);
-  }
   const double2* ph = reinterpret_cast<const double2*>(phi);
   const double2* ps = reinterpret_cast<const double2*>(psi);
   const double2* U64 = reinterpret_cast<const double2*>(op->gauge->links[0].ptr);
   const int64_t nl = lat->V * 4;
   const unsigned bl = (unsigned)((nl + 127) / 128);
-  if (prec == P64)
-    k_force_hop<double><<<bl, 128, 0, st>>>(g, ph, ps, nrhs, Gd);
-  else
-    k_force_hop<float><<<bl, 128, 0, st>>>(g, ph, ps, nrhs, Gd);
+  const unsigned bs = (unsigned)((lat->V + 63) / 64);
+  const bool clover = with_clover && op->csw != 0.0;
+  if (prec == P64) {
+    DevBuf gtmp;
+    double2* Gd = reinterpret_cast<double2*>(G);
+    if (!Gd) {
+      DD_TRY(gtmp.alloc((size_t)nl * 9 * sizeof(double2)));
+      Gd = reinterpret_cast<double2*>(gtmp.ptr);
+    }
+    k_force_hop<double, double2><<<bl, 128, 0, st>>>(g, ph, ps, nrhs, Gd);
+    if (clover) k_force_clover<double, double2><<<bs, 64, 0, st>>>(g, U64, ph, ps, nrhs, op->csw, Gd);
+    if (F) k_force_project<double2><<<bl, 128, 0, st>>>(g, U64, Gd, reinterpret_cast<double2*>(F));
+    DD_CUDA(cudaGetLastError());
+    if (!G) DD_CUDA(cudaStreamSynchronize(st));  // the temporary G is released on return
+    return DD_OK;
+  }
+  // FP32: accumulate in the operator's padded FP32 workspace (vector
+  // reductions), then widen into G and / or project into F
+  DD_TRY(op->ws_force.ensure((size_t)nl * kGf * sizeof(float)));
+  float* Gf = reinterpret_cast<float*>(op->ws_force.ptr);
+  k_force_hop<float, float><<<bl, 128, 0, st>>>(g, ph, ps, nrhs, Gf);
+  if (clover) k_force_clover<float, float><<<bs, 64, 0, st>>>(g, U64, ph, ps, nrhs, op->csw, Gf);
+  if (G) k_force_widen<<<bl, 128, 0, st>>>(nl, Gf, reinterpret_cast<double2*>(G));
+  if (F) k_force_project<float><<<bl, 128, 0, st>>>(g, U64, Gf, reinterpret_cast<double2*>(F));
   DD_CUDA(cudaGetLastError());
-  if (with_clover && op->csw != 0.0) {
-    const unsigned bs = (unsigned)((lat->V + 63) / 64);
-    if (prec == P64)
-      k_force_clover<double><<<bs, 64, 0, st>>>(g, U64, ph, ps, nrhs, op->csw, Gd);
-    else
-      k_force_clover<float><<<bs, 64, 0, st>>>(g, U64, ph, ps, nrhs, op->csw, Gd);
-    DD_CUDA(cudaGetLastError());
-  }
-  if (F) {
-    k_force_project<<<bl, 128, 0, st>>>(g, U64, Gd, reinterpret_cast<double2*>(F));
-    DD_CUDA(cudaGetLastError());
-  }
-  if (!G) DD_CUDA(cudaStreamSynchronize(st));  // the temporary G is released on return
   return DD_OK;
 }
 

@@ -487,8 +487,12 @@ inline int rhs_block_limit() {
 
 namespace dd {
 
-// RHS counts that take the RHS-blocked kernel: every even count, and odd
-// counts from 5 up (one thread of every site then carries a short block).
+// RHS counts for which the batched kernel (one register allocation for all
+// its lattices, sized for blocks of two) takes the RHS-blocked body: every
+// even count, and odd counts from 5 up (one thread of every site then carries
+// a short block).  Separate launches block even counts only: for odd counts
+// the one-thread-per-RHS kernel at its higher occupancy is faster (32^4:
+// 5 RHS 0.57 vs 0.64 ms, 17 RHS 1.68 vs 1.73 ms).
 inline bool rb_worth(int nrhs) { return nrhs >= 2 && (nrhs % 2 == 0 || nrhs >= 5); }
 
 // Host launchers; the instantiation units explicitly instantiate one
@@ -508,7 +512,7 @@ cudaError_t launch_hop(const HopArgs& a, bool dagger, int epi, cudaStream_t st) 
     if (epi == EPI_D && launch_stage<PG>(a, dagger, st, &e)) return e;
   }
 
-  if (PG != P64 && rbmax >= 2 && (epi == EPI_D || epi == EPI_AINV) && rb_worth(a.nrhs)) {
+  if (PG != P64 && rbmax >= 2 && (epi == EPI_D || epi == EPI_AINV) && a.nrhs >= 2 && a.nrhs % 2 == 0) {
     // measured on 32^4: blocks of 4 win from 16 RHS up, blocks of 2 below
     const int NBsel = (a.nrhs % 4 == 0 && a.nrhs >= 16 && rbmax >= 4) ? 4 : 2;
     const int64_t nt = (int64_t)a.g.Vh * ((a.nrhs + NBsel - 1) / NBsel) * a.npar;

@@ -75,6 +75,8 @@ struct dd_clover {
   dd::DevBuf ainv[3];
   // workspace for canonical-layout calls and operator intermediates
   dd::DevBuf ws_in, ws_out, ws_tmp, ws_canon_in, ws_canon_out;
+  // FP32 link-derivative accumulator of dd_force: [V][4][20] floats
+  dd::DevBuf ws_force;
   const void* M(int pi, int parity) const;  // A of a parity
   const void* Ainv(int pi) const;
 };
