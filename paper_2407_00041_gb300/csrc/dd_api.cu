@@ -37,7 +37,91 @@ int stage_in(DevBuf& buf, const void* src, size_t bytes, int layout, const doubl
   return DD_OK;
 }
 
+// D or D^H of a full field in canonical host layout, pipelined over C
+// chunks of time slices: the host-to-device copy of chunk c + 1 (stream
+// s_in), the pack / stencil / unpack of chunk c (the caller's stream) and the
+// device-to-host copy of chunk c - 1 (stream s_out) overlap.  The stencil of
+// a chunk needs the input slices one beyond each end, so the last chunk is
+// copied first and chunk c is computed once chunk c + 1 is packed.
+int apply_host_pipelined(dd_clover* op, int prec, bool dagger, const void* hin, void* hout, int nrhs,
+                         cudaStream_t st) {
+  const dd_lattice* lat = op->lat;
+  const int nT = lat->dims[0];
+  const int C = nT < 8 ? nT : 8;
+  const int64_t slice = (int64_t)lat->dims[1] * lat->dims[2] * lat->dims[3];
+  const size_t row = (size_t)lat->V * 12 * 16;  // one RHS of the canonical array
+  const size_t cb = row * nrhs;
+  const size_t nb = field_bytes(lat, prec, 0, nrhs);
+  DD_TRY(op->ws_canon_in.ensure(cb));
+  DD_TRY(op->ws_canon_out.ensure(cb));
+  DD_TRY(op->ws_in.ensure(nb));
+  DD_TRY(op->ws_out.ensure(nb));
+  DD_TRY(op->pipe.ensure(2 * C + 1));
+  HostPipe& hp = op->pipe;
+  cudaEvent_t start = hp.ev[2 * C];
+  auto t0_of = [&](int c) { return (int)((int64_t)c * nT / C); };
+  auto copy_rows = [&](void* dst, const void* src, int c, cudaMemcpyKind kind, cudaStream_t s) -> cudaError_t {
+    const size_t off = (size_t)t0_of(c) * slice * 12 * 16;
+    const size_t w = (size_t)(t0_of(c + 1) - t0_of(c)) * slice * 12 * 16;
+    return cudaMemcpy2DAsync(static_cast<char*>(dst) + off, row, static_cast<const char*>(src) + off, row, w, nrhs,
+                             kind, s);
+  };
+  const double* cin = reinterpret_cast<const double*>(op->ws_canon_in.ptr);
+  double* cout = reinterpret_cast<double*>(op->ws_canon_out.ptr);
+  Field fin = field_view(lat, prec, 0, op->ws_in.ptr, nrhs);
+  Field fout = field_view(lat, prec, 0, op->ws_out.ptr, nrhs);
+  // the copy streams start after the work already queued on st
+  DD_CUDA(cudaEventRecord(start, st));
+  DD_CUDA(cudaStreamWaitEvent(hp.s_in, start, 0));
+  DD_CUDA(cudaStreamWaitEvent(hp.s_out, start, 0));
+  for (int k = 0; k < C; ++k) {
+    const int c = k == 0 ? C - 1 : k - 1;  // last chunk first
+    DD_CUDA(copy_rows(op->ws_canon_in.ptr, hin, c, cudaMemcpyHostToDevice, hp.s_in));
+    DD_CUDA(cudaEventRecord(hp.ev[c], hp.s_in));
+  }
+  auto pack_chunk = [&](int c) -> int {
+    DD_CUDA(cudaStreamWaitEvent(st, hp.ev[c], 0));
+    return pack(lat, prec, 0, cin, fin, st, t0_of(c), t0_of(c + 1) - t0_of(c));
+  };
+  auto compute_chunk = [&](int c) -> int {
+    const int t0 = t0_of(c), nt = t0_of(c + 1) - t0;
+    DD_TRY(op_D_slices(op, prec, prec, dagger, fin, fout, t0, nt, st));
+    DD_TRY(unpack(lat, prec, 0, fout, cout, st, t0, nt));
+    DD_CUDA(cudaEventRecord(hp.ev[C + c], st));
+    DD_CUDA(cudaStreamWaitEvent(hp.s_out, hp.ev[C + c], 0));
+    DD_CUDA(copy_rows(hout, cout, c, cudaMemcpyDeviceToHost, hp.s_out));
+    return DD_OK;
+  };
+  DD_TRY(pack_chunk(C - 1));
+  for (int c = 0; c < C - 1; ++c) {
+    DD_TRY(pack_chunk(c));
+    if (c >= 1) DD_TRY(compute_chunk(c - 1));
+  }
+  if (C >= 2) DD_TRY(compute_chunk(C - 2));
+  DD_TRY(compute_chunk(C - 1));
+  DD_CUDA(cudaStreamSynchronize(hp.s_out));
+  DD_CUDA(cudaStreamSynchronize(st));
+  return DD_OK;
+}
+
 }  // namespace
+
+dd::HostPipe::~HostPipe() {
+  for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  if (s_in) cudaStreamDestroy(s_in);
+  if (s_out) cudaStreamDestroy(s_out);
+}
+
+int dd::HostPipe::ensure(int nevents) {
+  if (!s_in) DD_CUDA(cudaStreamCreateWithFlags(&s_in, cudaStreamNonBlocking));
+  if (!s_out) DD_CUDA(cudaStreamCreateWithFlags(&s_out, cudaStreamNonBlocking));
+  while ((int)ev.size() < nevents) {
+    cudaEvent_t e;
+    DD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    ev.push_back(e);
+  }
+  return DD_OK;
+}
 
 extern "C" {
 
@@ -214,6 +298,8 @@ int dd_apply(dd_clover* op, int which, int prec, const void* in, void* out, int 
   const int subset = half ? 1 : 0;
   const size_t nb = field_bytes(lat, prec, subset, nrhs);
   const size_t cb = (size_t)(half ? lat->Vh : lat->V) * 12 * 16 * nrhs;
+  if (layout == DD_LAYOUT_CANONICAL_HOST && (which == DD_OP_D || which == DD_OP_DH))
+    return apply_host_pipelined(op, prec, which == DD_OP_DH, in, out, nrhs, st);
   Field fin, fout;
   const double* cin = nullptr;
   if (layout == DD_LAYOUT_NATIVE) {

@@ -289,7 +289,14 @@ struct Geom {
   int Vh;         // sites per parity
   float t_bc;     // sign of hops across the time boundary
   int zblock;     // traversal of full-lattice launches: Z-slabs of this depth (divides nZ)
+  int t0, nt;     // full-lattice launches cover the time slices t0 .. t0 + nt - 1
 };
+
+// Output sites of a launch: both parities of the slices t0 .. t0 + nt - 1,
+// or one parity of the whole lattice.
+__host__ __device__ __forceinline__ int64_t launch_sites(const Geom& g, int npar) {
+  return npar == 2 ? (int64_t)g.nt * g.stride[0] : (int64_t)g.Vh;
+}
 
 struct SiteCoord {
   int c[4];  // t, z, y, x
@@ -337,8 +344,8 @@ __device__ __forceinline__ SiteCoord traversal_coords(const Geom& g, int k) {
   sc.c[2] = r - r2 * g.n[2];
   r = r2 / g.zblock;
   const int zz = r2 - r * g.zblock;
-  r2 = r / g.n[0];
-  sc.c[0] = r - r2 * g.n[0];
+  r2 = r / g.nt;
+  sc.c[0] = r - r2 * g.nt + g.t0;
   sc.c[1] = r2 * g.zblock + zz;
   sc.lex = ((sc.c[0] * g.n[1] + sc.c[1]) * g.n[2] + sc.c[2]) * g.n[3] + sc.c[3];
   return sc;

@@ -430,7 +430,7 @@ __device__ __forceinline__ void hop_thread_rb(const HopArgs& a, int64_t tid) {
 template <int PG, int PIN, int POUT, bool DAG, int EPI, int NB>
 __global__ void __launch_bounds__(128, NB >= 4 ? 2 : 3) k_hop_rb(const HopArgs a) {
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= (int64_t)a.g.Vh * ((a.nrhs + NB - 1) / NB) * a.npar) return;
+  if (tid >= launch_sites(a.g, a.npar) * ((a.nrhs + NB - 1) / NB)) return;
   hop_thread_rb<PG, PIN, POUT, DAG, EPI, NB>(a, tid);
 }
 
@@ -446,7 +446,7 @@ struct HopMinBlocks {
 template <int PG, int PIN, int POUT, bool DAG, int EPI>
 __global__ void __launch_bounds__(128, HopMinBlocks<PG>::value) k_hop(const HopArgs a) {
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= (int64_t)a.g.Vh * a.nrhs * a.npar) return;
+  if (tid >= launch_sites(a.g, a.npar) * a.nrhs) return;
   hop_thread<PG, PIN, POUT, DAG, EPI>(a, tid);
 }
 
@@ -499,7 +499,7 @@ inline bool rb_worth(int nrhs) { return nrhs >= 2 && (nrhs % 2 == 0 || nrhs >= 5
 // precision triple each, other units only see the declarations in dd_ops.h.
 template <int PG, int PIN, int POUT>
 cudaError_t launch_hop(const HopArgs& a, bool dagger, int epi, cudaStream_t st) {
-  const int64_t n = (int64_t)a.g.Vh * a.nrhs * a.npar;
+  const int64_t n = launch_sites(a.g, a.npar) * a.nrhs;
   if (n == 0) return cudaSuccess;
   const int threads = 128;
   const unsigned blocks = (unsigned)((n + threads - 1) / threads);
@@ -515,7 +515,7 @@ cudaError_t launch_hop(const HopArgs& a, bool dagger, int epi, cudaStream_t st) 
   if (PG != P64 && rbmax >= 2 && (epi == EPI_D || epi == EPI_AINV) && a.nrhs >= 2 && a.nrhs % 2 == 0) {
     // measured on 32^4: blocks of 4 win from 16 RHS up, blocks of 2 below
     const int NBsel = (a.nrhs % 4 == 0 && a.nrhs >= 16 && rbmax >= 4) ? 4 : 2;
-    const int64_t nt = (int64_t)a.g.Vh * ((a.nrhs + NBsel - 1) / NBsel) * a.npar;
+    const int64_t nt = launch_sites(a.g, a.npar) * ((a.nrhs + NBsel - 1) / NBsel);
     const unsigned bl = (unsigned)((nt + threads - 1) / threads);
     const int key = (epi == EPI_D ? 0 : 4) + (dagger ? 2 : 0) + (NBsel == 4 ? 1 : 0);
     switch (key) {

@@ -46,6 +46,18 @@ struct DevBuf {
   void release();
 };
 
+// Copy streams and events of the pipelined host-buffer apply (created on
+// first use, released with the handle).
+struct HostPipe {
+  cudaStream_t s_in = nullptr, s_out = nullptr;
+  std::vector<cudaEvent_t> ev;
+  HostPipe() = default;
+  HostPipe(const HostPipe&) = delete;
+  HostPipe& operator=(const HostPipe&) = delete;
+  ~HostPipe();
+  int ensure(int nevents);
+};
+
 }  // namespace dd
 
 struct dd_lattice {
@@ -77,6 +89,7 @@ struct dd_clover {
   dd::DevBuf ws_in, ws_out, ws_tmp, ws_canon_in, ws_canon_out;
   // FP32 link-derivative accumulator of dd_force: [V][4][20] floats
   dd::DevBuf ws_force;
+  dd::HostPipe pipe;
   const void* M(int pi, int parity) const;  // A of a parity
   const void* Ainv(int pi) const;
 };
@@ -100,6 +113,9 @@ size_t field_bytes(const dd_lattice* lat, int prec, int subset, int nrhs);
 // Precision of the operator handle to use (pg) and of the vectors (pv):
 // (F64, F64), (F32, F32), (F16, F16) or (F16, F32).
 int op_D(const dd_clover* op, int pg, int pv, bool dagger, const Field& in, const Field& out, cudaStream_t st);
+// the same for the output sites of the time slices t0 .. t0 + nt - 1 only
+int op_D_slices(const dd_clover* op, int pg, int pv, bool dagger, const Field& in, const Field& out, int t0, int nt,
+                cudaStream_t st);
 int op_SC(const dd_clover* op, int pg, int pv, const Field& in, const Field& out, cudaStream_t st);
 // out_o = Dhat in_o (odd half fields); tmp_e: even half-field workspace
 int op_Dhat(const dd_clover* op, int pg, int pv, bool dagger, const Field& in, const Field& out, const Field& tmp,
@@ -122,8 +138,11 @@ int links_to_canonical(const dd_gauge* g, double* U_canon_dev, cudaStream_t st);
 int clover_build(dd_clover* op, cudaStream_t st);  // FP64 blocks, A_ee^{-1}, demoted copies
 int clover_to_dense(const dd_clover* op, double* A_dev /*[V][144] complex*/, cudaStream_t st);
 // subset: 0 full; 1 odd / 2 even sites of a half-lattice canonical array
-// [nrhs][V/2][12]; 3 even / 4 odd sites of a full canonical array [nrhs][V][12]
-int pack(const dd_lattice* lat, int prec, int subset, const double* canon, const Field& f, cudaStream_t st);
-int unpack(const dd_lattice* lat, int prec, int subset, const Field& f, double* canon, cudaStream_t st);
+// [nrhs][V/2][12]; 3 even / 4 odd sites of a full canonical array [nrhs][V][12].
+// nt > 0 (subset 0 only): only the time slices t0 .. t0 + nt - 1.
+int pack(const dd_lattice* lat, int prec, int subset, const double* canon, const Field& f, cudaStream_t st,
+         int t0 = 0, int nt = 0);
+int unpack(const dd_lattice* lat, int prec, int subset, const Field& f, double* canon, cudaStream_t st, int t0 = 0,
+           int nt = 0);
 
 }  // namespace dd

@@ -188,6 +188,21 @@ int op_D(const dd_clover* op, int pg, int pv, bool dagger, const Field& in, cons
   return run_hop(pg, pv, a, dagger, EPI_D, st);
 }
 
+int op_D_slices(const dd_clover* op, int pg, int pv, bool dagger, const Field& in, const Field& out, int t0, int nt,
+                cudaStream_t st) {
+  DD_TRY(check_prec(op, pg));
+  if (t0 < 0 || nt < 1 || t0 + nt > op->lat->dims[0]) return fail(DD_ERR_ARG, "bad time-slice range");
+  HopArgs a = base_args(op, pg, in.nrhs);
+  a.g.t0 = t0;
+  a.g.nt = nt;
+  for (int p = 0; p < 2; ++p) {
+    a.in[p] = in.h[p];
+    a.y[p] = in.h[p];
+    a.out[p] = out.h[p];
+  }
+  return run_hop(pg, pv, a, dagger, EPI_D, st);
+}
+
 int run_block(int pg, int pv, const BlockArgs& a, cudaStream_t st) {
   cudaError_t e;
   if (pg == P64 && pv == P64)
@@ -330,6 +345,8 @@ int op_reconstruct(const dd_clover* op, int pg, int pv, const Field& b, const Fi
 dd::Geom dd_lattice::geom() const {
   dd::Geom g;
   g.zblock = dims[1];
+  g.t0 = 0;
+  g.nt = dims[0];
   for (int i = 0; i < 4; ++i) g.n[i] = dims[i];
   g.stride[3] = 1;
   g.stride[2] = dims[3];

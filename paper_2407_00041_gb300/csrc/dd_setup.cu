@@ -345,6 +345,7 @@ struct PackArgs {
   int p0, npar;
   int64_t gstride;
   HalfField h[2];
+  int64_t s0, ns;  // compact sites s0 .. s0 + ns - 1 of each parity (a range of time slices)
 };
 
 __device__ __forceinline__ int64_t canon_offset(const PackArgs& a, int p, int64_t s, int r) {
@@ -366,7 +367,7 @@ __device__ __forceinline__ int64_t canon_offset(const PackArgs& a, int p, int64_
 template <int P>
 __global__ void k_pack(PackArgs a, const double2* __restrict__ canon) {
   using R = typename SpinorStore<P>::real;
-  const int64_t nper = a.g.Vh * a.nrhs;
+  const int64_t nper = a.ns * a.nrhs;
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nper * a.npar) return;
   int p = a.p0;
@@ -374,6 +375,7 @@ __global__ void k_pack(PackArgs a, const double2* __restrict__ canon) {
     t -= nper;
     p ^= 1;
   }
+  t += a.s0 * a.nrhs;
   const int64_t s = t / a.nrhs;
   const int r = (int)(t - s * a.nrhs);
   const double2* src = canon + canon_offset(a, p, s, r);
@@ -389,7 +391,7 @@ __global__ void k_pack(PackArgs a, const double2* __restrict__ canon) {
 template <int P>
 __global__ void k_unpack(PackArgs a, double2* canon) {
   using R = typename SpinorStore<P>::real;
-  const int64_t nper = a.g.Vh * a.nrhs;
+  const int64_t nper = a.ns * a.nrhs;
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nper * a.npar) return;
   int p = a.p0;
@@ -397,6 +399,7 @@ __global__ void k_unpack(PackArgs a, double2* canon) {
     t -= nper;
     p ^= 1;
   }
+  t += a.s0 * a.nrhs;
   const int64_t s = t / a.nrhs;
   const int r = (int)(t - s * a.nrhs);
   cx<R> v[12];
@@ -418,6 +421,8 @@ PackArgs pack_args(const dd_lattice* lat, int subset, const Field& f) {
   a.gstride = lat->Vh * f.nrhs;
   a.h[0] = f.h[0];
   a.h[1] = f.h[1];
+  a.s0 = 0;
+  a.ns = lat->Vh;
   return a;
 }
 
@@ -485,9 +490,15 @@ int clover_to_dense(const dd_clover* op, double* A_dev, cudaStream_t st) {
   return DD_OK;
 }
 
-int pack(const dd_lattice* lat, int prec, int subset, const double* canon, const Field& f, cudaStream_t st) {
+int pack(const dd_lattice* lat, int prec, int subset, const double* canon, const Field& f, cudaStream_t st, int t0,
+         int nt) {
   PackArgs a = pack_args(lat, subset, f);
-  const int64_t n = lat->Vh * f.nrhs * a.npar;
+  if (nt > 0) {  // time slices t0 .. t0 + nt - 1 of a full field
+    const int64_t slice = (int64_t)lat->dims[1] * lat->dims[2] * lat->dims[3];
+    a.s0 = t0 * slice / 2;
+    a.ns = nt * slice / 2;
+  }
+  const int64_t n = a.ns * f.nrhs * a.npar;
   const double2* c = reinterpret_cast<const double2*>(canon);
   if (prec == P64)
     k_pack<P64><<<nblk(n, 128), 128, 0, st>>>(a, c);
@@ -499,9 +510,15 @@ int pack(const dd_lattice* lat, int prec, int subset, const double* canon, const
   return DD_OK;
 }
 
-int unpack(const dd_lattice* lat, int prec, int subset, const Field& f, double* canon, cudaStream_t st) {
+int unpack(const dd_lattice* lat, int prec, int subset, const Field& f, double* canon, cudaStream_t st, int t0,
+           int nt) {
   PackArgs a = pack_args(lat, subset, f);
-  const int64_t n = lat->Vh * f.nrhs * a.npar;
+  if (nt > 0) {
+    const int64_t slice = (int64_t)lat->dims[1] * lat->dims[2] * lat->dims[3];
+    a.s0 = t0 * slice / 2;
+    a.ns = nt * slice / 2;
+  }
+  const int64_t n = a.ns * f.nrhs * a.npar;
   double2* c = reinterpret_cast<double2*>(canon);
   if (prec == P64)
     k_unpack<P64><<<nblk(n, 128), 128, 0, st>>>(a, c);

@@ -311,7 +311,7 @@ template <int PG>
 bool launch_stage(const HopArgs& a, bool dagger, cudaStream_t st, cudaError_t* err_out) {
   static const int enabled = stage_env("DD_STAGE", 0);
   static const int want_slots = stage_env("DD_STAGE_SLOTS", 4);
-  if (!enabled || a.npar != 2) return false;
+  if (!enabled || a.npar != 2 || a.g.t0 != 0 || a.g.nt != a.g.n[0]) return false;
   const int hx = a.g.n[3] / 2;
   const int64_t units = (int64_t)hx * a.nrhs;
   if (units < 1 || units > 512) return false;

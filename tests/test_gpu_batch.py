@@ -19,15 +19,15 @@ def _arr(vals, t=ctypes.c_void_p):
 
 
 def _close(op, prec, a, b, n):
-    if prec == dd.DD_PREC_F16:
-        return torch.equal(a, b)  # FP16 storage: the same kernel body on both paths
+    """Batched and single applies may run different kernel bodies (blocks of
+    RHS, row staging), so they agree to the rounding of the storage format."""
     shape = (n, op.lattice.V, 12)
     ua = torch.empty(shape, dtype=torch.complex128, device="cuda")
     ub = torch.empty_like(ua)
     op.unpack(prec, 0, a, ua, n)
     op.unpack(prec, 0, b, ub, n)
     torch.cuda.synchronize()
-    return ((ua - ub).norm() / ub.norm()).item() < 1e-6
+    return ((ua - ub).norm() / ub.norm()).item() < {dd.DD_PREC_F32: 1e-6, dd.DD_PREC_F16: 5e-3}[prec]
 
 
 @pytest.mark.parametrize("prec", [dd.DD_PREC_F32, dd.DD_PREC_F16])
