@@ -86,6 +86,8 @@ int stage(dd_batch* b, const void* const* ins, void* const* outs, cudaStream_t s
     a.g = lat->geom();
     a.g.zblock = zblock_for(lat->dims, stencil_bytes_per_site(b->prec, b->nrhs[i]));
     a.rhs_block = rb_worth(b->nrhs[i]) ? 2 : 1;
+    prepare_divs(a.g);
+    a.fblk = make_fastdiv((uint32_t)((b->nrhs[i] + a.rhs_block - 1) / a.rhs_block));
     a.nrhs = b->nrhs[i];
     a.p0 = 0;
     a.npar = 2;

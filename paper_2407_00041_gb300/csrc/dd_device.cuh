@@ -283,6 +283,28 @@ __device__ __forceinline__ void store_spinor(const HalfField& f, int64_t gstride
 // Even-odd geometry.  A site of parity p has compact index s = lex / 2
 // (valid because nX is even), so the sites of one parity keep their
 // lexicographic order.
+// Division by a divisor fixed for a launch, by multiply and shift
+// (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", 1994): with l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1, n / d = (mulhi(n, m) + n) >> l, exact
+// for 0 <= n < 2^31 (the sum then stays below 2^32).
+struct FastDiv {
+  uint32_t d, m, l;
+};
+
+inline FastDiv make_fastdiv(uint32_t d) {
+  FastDiv f;
+  f.d = d;
+  f.l = 0;
+  while ((1ull << f.l) < d) ++f.l;
+  f.m = (uint32_t)((((1ull << 32) * ((1ull << f.l) - d)) / d) + 1);
+  return f;
+}
+
+__device__ __forceinline__ int fdiv(int n, const FastDiv& f) {
+  return (int)((__umulhi((uint32_t)n, f.m) + (uint32_t)n) >> f.l);
+}
+
 struct Geom {
   int n[4];       // nT, nZ, nY, nX
   int stride[4];  // lexicographic strides of T, Z, Y, X
@@ -290,7 +312,18 @@ struct Geom {
   float t_bc;     // sign of hops across the time boundary
   int zblock;     // traversal of full-lattice launches: Z-slabs of this depth (divides nZ)
   int t0, nt;     // full-lattice launches cover the time slices t0 .. t0 + nt - 1
+  // divisions by nX, nY, nZ, zblock, nt and nX / 2 (set by prepare_divs)
+  FastDiv fx, fy, fz, fzb, fnt, fhx;
 };
+
+inline void prepare_divs(Geom& g) {
+  g.fx = make_fastdiv((uint32_t)g.n[3]);
+  g.fy = make_fastdiv((uint32_t)g.n[2]);
+  g.fz = make_fastdiv((uint32_t)g.n[1]);
+  g.fzb = make_fastdiv((uint32_t)g.zblock);
+  g.fnt = make_fastdiv((uint32_t)g.nt);
+  g.fhx = make_fastdiv((uint32_t)(g.n[3] / 2));
+}
 
 // Output sites of a launch: both parities of the slices t0 .. t0 + nt - 1,
 // or one parity of the whole lattice.
@@ -306,11 +339,11 @@ struct SiteCoord {
 __device__ __forceinline__ SiteCoord site_coords(const Geom& g, int s, int p) {
   SiteCoord sc;
   const int lex2 = 2 * s;
-  const int r1 = lex2 / g.n[3];
+  const int r1 = fdiv(s, g.fhx);  // = lex2 / nX, nX even
   const int x0 = lex2 - r1 * g.n[3];
-  const int r2 = r1 / g.n[2];
+  const int r2 = fdiv(r1, g.fy);
   sc.c[2] = r1 - r2 * g.n[2];
-  sc.c[0] = r2 / g.n[1];
+  sc.c[0] = fdiv(r2, g.fz);
   sc.c[1] = r2 - sc.c[0] * g.n[1];
   sc.c[3] = x0 + ((p ^ (sc.c[0] + sc.c[1] + sc.c[2])) & 1);
   sc.lex = r1 * g.n[3] + sc.c[3];
@@ -338,13 +371,13 @@ __device__ __forceinline__ SiteCoord lex_coords(const Geom& g, int lex) {
 // reuse inside L2 on large lattices.
 __device__ __forceinline__ SiteCoord traversal_coords(const Geom& g, int k) {
   SiteCoord sc;
-  int r = k / g.n[3];
+  int r = fdiv(k, g.fx);
   sc.c[3] = k - r * g.n[3];
-  int r2 = r / g.n[2];
+  int r2 = fdiv(r, g.fy);
   sc.c[2] = r - r2 * g.n[2];
-  r = r2 / g.zblock;
+  r = fdiv(r2, g.fzb);
   const int zz = r2 - r * g.zblock;
-  r2 = r / g.nt;
+  r2 = fdiv(r, g.fnt);
   sc.c[0] = r - r2 * g.nt + g.t0;
   sc.c[1] = r2 * g.zblock + zz;
   sc.lex = ((sc.c[0] * g.n[1] + sc.c[1]) * g.n[2] + sc.c[2]) * g.n[3] + sc.c[3];

@@ -248,15 +248,15 @@ __device__ __forceinline__ void hop_thread(const HopArgs& a, int64_t tid) {
     // both parities: threads follow the lexicographic site order, so the two
     // uses of every link (forward hop at x, backward hop at x + mu) and the
     // reads of a neighbour spinor fall within about one time slice of traffic
-    const int lex = (int)(tid / a.nrhs);
-    r = (int)(tid - (int64_t)lex * a.nrhs);
+    const int lex = fdiv((int)tid, a.fblk);
+    r = (int)tid - lex * a.nrhs;
     sc = traversal_coords(a.g, lex);
     p = (sc.c[0] + sc.c[1] + sc.c[2] + sc.c[3]) & 1;
     s = sc.lex >> 1;
   } else {
     p = a.p0;
-    s = (int)(tid / a.nrhs);
-    r = (int)(tid - (int64_t)s * a.nrhs);
+    s = fdiv((int)tid, a.fblk);
+    r = (int)tid - s * a.nrhs;
     sc = site_coords(a.g, s, p);
   }
   const int q = p ^ 1;
@@ -348,15 +348,15 @@ __device__ __forceinline__ void hop_thread_rb(const HopArgs& a, int64_t tid) {
   int p, s, rb;
   SiteCoord sc;
   if (a.npar == 2) {
-    const int lex = (int)(tid / nrb);
-    rb = (int)(tid - (int64_t)lex * nrb);
+    const int lex = fdiv((int)tid, a.fblk);
+    rb = (int)tid - lex * nrb;
     sc = traversal_coords(a.g, lex);
     p = (sc.c[0] + sc.c[1] + sc.c[2] + sc.c[3]) & 1;
     s = sc.lex >> 1;
   } else {
     p = a.p0;
-    s = (int)(tid / nrb);
-    rb = (int)(tid - (int64_t)s * nrb);
+    s = fdiv((int)tid, a.fblk);
+    rb = (int)tid - s * nrb;
     sc = site_coords(a.g, s, p);
   }
   const int q = p ^ 1;
@@ -498,9 +498,13 @@ inline bool rb_worth(int nrhs) { return nrhs >= 2 && (nrhs % 2 == 0 || nrhs >= 5
 // Host launchers; the instantiation units explicitly instantiate one
 // precision triple each, other units only see the declarations in dd_ops.h.
 template <int PG, int PIN, int POUT>
-cudaError_t launch_hop(const HopArgs& a, bool dagger, int epi, cudaStream_t st) {
+cudaError_t launch_hop(const HopArgs& args, bool dagger, int epi, cudaStream_t st) {
+  HopArgs a = args;
+  prepare_divs(a.g);
+  a.fblk = make_fastdiv((uint32_t)a.nrhs);
   const int64_t n = launch_sites(a.g, a.npar) * a.nrhs;
   if (n == 0) return cudaSuccess;
+  if (n >= (int64_t)1 << 31) return cudaErrorInvalidValue;  // thread indices are 32-bit
   const int threads = 128;
   const unsigned blocks = (unsigned)((n + threads - 1) / threads);
   // several right-hand sides: RHS-blocked variant (not for FP64, which is
@@ -515,6 +519,7 @@ cudaError_t launch_hop(const HopArgs& a, bool dagger, int epi, cudaStream_t st) 
   if (PG != P64 && rbmax >= 2 && (epi == EPI_D || epi == EPI_AINV) && a.nrhs >= 2 && a.nrhs % 2 == 0) {
     // measured on 32^4: blocks of 4 win from 16 RHS up, blocks of 2 below
     const int NBsel = (a.nrhs % 4 == 0 && a.nrhs >= 16 && rbmax >= 4) ? 4 : 2;
+    a.fblk = make_fastdiv((uint32_t)((a.nrhs + NBsel - 1) / NBsel));
     const int64_t nt = launch_sites(a.g, a.npar) * ((a.nrhs + NBsel - 1) / NBsel);
     const unsigned bl = (unsigned)((nt + threads - 1) / threads);
     const int key = (epi == EPI_D ? 0 : 4) + (dagger ? 2 : 0) + (NBsel == 4 ? 1 : 0);

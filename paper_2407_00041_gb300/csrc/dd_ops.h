@@ -29,6 +29,7 @@ struct HopArgs {
   const void* M[2];  // 6x6 Hermitian blocks by output parity: [36][Vh] elements
   double beta;
   int rhs_block;  // batched launch: right-hand sides per thread (1 or 2)
+  FastDiv fblk;   // division of the thread index by the RHS slots per site (set by the launcher)
 };
 
 // Self-coupling apply without hopping: out = M y on npar parities.
