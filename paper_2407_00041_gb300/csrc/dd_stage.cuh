@@ -25,9 +25,12 @@
 // their stages through a ring of D shared-memory slots: one thread issues the
 // copies of stage k + D into the slot of stage k once every thread has
 // finished stage k (block barrier, then a proxy fence), so D - 1 stages are in
-// flight while one is consumed.  Waits on the mbarriers are bounded in time:
-// on expiry the CTA records the failure in `err`, stops consuming, waits
-// (again bounded) for the copies it has issued, and returns.
+// flight while one is consumed.  Waits on the mbarriers are bounded in time
+// (`budget` clock cycles): on expiry the CTA records the failure in `err`,
+// stops consuming, waits (again bounded) for the copies it has issued, and
+// returns.  `poison` >= 0 names a stage of CTA 0 whose barrier is told to
+// expect 16 bytes more than its copies deliver (every copy still lands), so
+// that the expiry path can be tested.
 #pragma once
 
 #include <algorithm>
@@ -126,7 +129,8 @@ __device__ __forceinline__ int stage_row(const Geom& g, const RowCoord& c, int s
 
 // Issue the copies of local stage k (tile k / 7 of this CTA, stage k % 7)
 // into slot `slot`.  Tile tau: parity tau & 1 of row tau >> 1.
-__device__ __forceinline__ void stage_issue(const HopArgs& a, int64_t k, float4* slot, uint64_t* bar, int hx) {
+__device__ __forceinline__ void stage_issue(const HopArgs& a, int64_t k, float4* slot, uint64_t* bar, int hx,
+                                            unsigned extra_tx = 0) {
   const int64_t tau = blockIdx.x + (k / kStages) * (int64_t)gridDim.x;
   const int st = (int)(k % kStages);
   const int p = (int)(tau & 1), q = p ^ 1;
@@ -134,7 +138,7 @@ __device__ __forceinline__ void stage_issue(const HopArgs& a, int64_t k, float4*
   const int nrow = stage_row(a.g, c, st);
   const int64_t units = (int64_t)hx * a.nrhs;
   const unsigned bytes = (unsigned)(units * 16);
-  mbar_arrive_expect_tx(bar, bytes * kStageGroups);
+  mbar_arrive_expect_tx(bar, bytes * kStageGroups + extra_tx);
   const float4* src = reinterpret_cast<const float4*>(a.in[q].base) + (int64_t)nrow * units;
 #pragma unroll
   for (int gr = 0; gr < kStageGroups; ++gr) bulk_copy_g2s(slot + gr * units, src + gr * a.gstride, bytes, bar);
@@ -174,7 +178,8 @@ __device__ __forceinline__ void stage_hop_l(cx<float> acc[12], const float4* slo
 }
 
 template <int PG, bool DAG, int MINB>
-__global__ void __launch_bounds__(MINB == 1 ? 512 : 256, MINB) k_hop_stage(const HopArgs a, int nslots, int64_t ntiles, int* err) {
+__global__ void __launch_bounds__(MINB == 1 ? 512 : 256, MINB) k_hop_stage(const HopArgs a, int nslots, int64_t ntiles, int* err,
+                                                                     long long budget, int poison) {
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
   float4* slots = reinterpret_cast<float4*>(smem + kStageHeader);
@@ -192,7 +197,6 @@ __global__ void __launch_bounds__(MINB == 1 ? 512 : 256, MINB) k_hop_stage(const
   constexpr int TF = DAG ? +1 : -1;
   constexpr int TB = -TF;
   const float beta = (float)a.beta;
-  const long long budget = 4000000000LL;  // about two seconds at the boost clock
 
   const int64_t my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int64_t K = my_tiles * kStages;
@@ -206,7 +210,8 @@ __global__ void __launch_bounds__(MINB == 1 ? 512 : 256, MINB) k_hop_stage(const
   int64_t issued = 0;
   if (threadIdx.x == 0) {
     for (; issued < K && issued < nslots; ++issued)
-      stage_issue(a, issued, slots + (issued % nslots) * slot_units, &bar[issued % nslots], hx);
+      stage_issue(a, issued, slots + (issued % nslots) * slot_units, &bar[issued % nslots], hx,
+                  blockIdx.x == 0 && issued == poison ? 16u : 0u);
   }
 
   // Per tile: the links of a stage are loaded one stage ahead (before the
@@ -311,6 +316,10 @@ template <int PG>
 bool launch_stage(const HopArgs& a, bool dagger, cudaStream_t st, cudaError_t* err_out) {
   static const int enabled = stage_env("DD_STAGE", 0);
   static const int want_slots = stage_env("DD_STAGE_SLOTS", 4);
+  // DD_STAGE_WAIT_TEST=1 (tests of the expiry path): the first stage of CTA 0
+  // expects 16 bytes more than its copies deliver, so that wait can only
+  // expire; the wait budget drops from about 2 s to 0.1 s.
+  static const int wait_test = stage_env("DD_STAGE_WAIT_TEST", 0);
   if (!enabled || a.npar != 2 || a.g.t0 != 0 || a.g.nt != a.g.n[0]) return false;
   const int hx = a.g.n[3] / 2;
   const int64_t units = (int64_t)hx * a.nrhs;
@@ -344,7 +353,8 @@ bool launch_stage(const HopArgs& a, bool dagger, cudaStream_t st, cudaError_t* e
   const int64_t grid = std::min<int64_t>(ntiles, (int64_t)sms * per_sm);
   int* flag = device_error_flag();
   if (!flag) return false;
-  kern<<<(unsigned)grid, threads, smem, st>>>(a, nslots, ntiles, flag);
+  kern<<<(unsigned)grid, threads, smem, st>>>(a, nslots, ntiles, flag, wait_test ? 200000000LL : 4000000000LL,
+                                                wait_test ? 0 : -1);
   *err_out = cudaGetLastError();
   return true;
 }

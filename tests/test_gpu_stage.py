@@ -90,3 +90,38 @@ def test_staged_matches_unstaged_kernels(tmp_path):
     for k in res["1"].files:
         a, b = res["1"][k], res["0"][k]
         assert rel(a, b) < 1e-6, k
+
+
+def test_expired_wait_is_reported_and_context_stays_usable(tmp_path):
+    """Failure detection without a GPU fault: in a child process with
+    DD_STAGE_WAIT_TEST=1 the first stage of CTA 0 waits on a barrier that its
+    copies cannot complete (it expects 16 bytes more than they deliver, every
+    copy still lands); the wait expires after its short budget, the kernel
+    sets the device flag and returns, dd_device_status reports and clears
+    it, and the same process then applies D on the FP64 path correctly."""
+    script = tmp_path / "expire.py"
+    script.write_text(
+        "import sys, ctypes, numpy as np\n"
+        f"sys.path.insert(0, {ROOT!r})\n"
+        "import oracle, synthetic, paper_2407_00041_gb300 as dd\n"
+        "from tests._gpu import CSW, M0, apply, make, rel\n"
+        "def status():\n"
+        "    f = ctypes.c_int(-1)\n"
+        "    dd.check(dd.lib.dd_device_status(ctypes.byref(f)), 'status')\n"
+        "    return f.value\n"
+        "dims = (8, 4, 4, 8)\n"
+        "U, lat, g, op = make(dims)\n"
+        "psi = synthetic.spinor(dims, nrhs=2)\n"
+        "apply(op, dd.DD_OP_D, dd.DD_PREC_F32, psi)\n"
+        "first, second = status(), status()\n"
+        "A = oracle.clover(U, dims, M0, CSW)\n"
+        "got = apply(op, dd.DD_OP_D, dd.DD_PREC_F64, psi)\n"
+        "err = max(rel(got[r], oracle.apply_D(U, A, psi[r].reshape(-1, 12), dims)) for r in range(2))\n"
+        "print('RESULT', first, second, err)\n")
+    env = dict(os.environ, DD_STAGE="1", DD_STAGE_WAIT_TEST="1")
+    p = subprocess.run([sys.executable, str(script)], cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+    assert p.returncode == 0, p.stdout[-2000:] + p.stderr[-2000:]
+    line = [ln for ln in p.stdout.splitlines() if ln.startswith("RESULT")][-1].split()
+    assert int(line[1]) == 1  # the expired wait was recorded
+    assert int(line[2]) == 0  # and cleared by the read
+    assert float(line[3]) < 1e-13  # the context still computes correctly
