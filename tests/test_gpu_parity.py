@@ -39,7 +39,7 @@ def test_clover_matches_oracle(system):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("nrhs", [1, 3, 4, 5, 6])
+@pytest.mark.parametrize("nrhs", [1, 3, 4, 5, 6, 16])
 def test_D_and_DH(system, prec, nrhs):
     dims, U, A, op, _ = system
     psi = synthetic.spinor(dims, nrhs=nrhs)
@@ -63,7 +63,7 @@ def test_self_coupling(system, prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("nrhs", [1, 2, 4, 5])
+@pytest.mark.parametrize("nrhs", [1, 2, 4, 5, 16])
 def test_Dhat(system, prec, nrhs):
     dims, U, A, op, _ = system
     eo = oracle.EvenOdd(U, A, dims)
