@@ -312,8 +312,13 @@ struct Geom {
   float t_bc;     // sign of hops across the time boundary
   int zblock;     // traversal of full-lattice launches: Z-slabs of this depth (divides nZ)
   int t0, nt;     // full-lattice launches cover the time slices t0 .. t0 + nt - 1
-  // divisions by nX, nY, nZ, zblock, nt and nX / 2 (set by prepare_divs)
-  FastDiv fx, fy, fz, fzb, fnt, fhx;
+  // full-lattice launches take the sites of `rseg` consecutive X-rows
+  // parity by parity (rseg * nX / 2 a multiple of 32 where nY allows), so a
+  // warp reads and writes one parity's arrays only
+  int rseg;
+  // divisions by nX, nY, nZ, zblock, nt, nX / 2 and the segment sizes (set by
+  // prepare_divs)
+  FastDiv fx, fy, fz, fzb, fnt, fhx, fseg;
 };
 
 inline void prepare_divs(Geom& g) {
@@ -322,7 +327,15 @@ inline void prepare_divs(Geom& g) {
   g.fz = make_fastdiv((uint32_t)g.n[1]);
   g.fzb = make_fastdiv((uint32_t)g.zblock);
   g.fnt = make_fastdiv((uint32_t)g.nt);
-  g.fhx = make_fastdiv((uint32_t)(g.n[3] / 2));
+  const int hx = g.n[3] / 2;
+  g.fhx = make_fastdiv((uint32_t)hx);
+  g.rseg = 1;
+  for (int r = 1; r <= g.n[2]; ++r)
+    if (g.n[2] % r == 0 && (r * hx) % 32 == 0) {
+      g.rseg = r;
+      break;
+    }
+  g.fseg = make_fastdiv((uint32_t)(g.rseg * g.n[3]));
 }
 
 // Output sites of a launch: both parities of the slices t0 .. t0 + nt - 1,
@@ -363,16 +376,25 @@ __device__ __forceinline__ SiteCoord lex_coords(const Geom& g, int lex) {
 }
 
 // Traversal order of full-lattice launches: slab b of `zblock` Z-planes is
-// walked time slice by time slice, X fastest:
-//   k = (((b * nT + t) * zblock + zz) * nY + y) * nX + x,  z = b * zblock + zz.
-// Consecutive threads still cover consecutive sites of an X-row, while the
-// hops to t +- 1 find their data after one slab-slice of traffic
-// (zblock * nY * nX sites) instead of a whole time slice, which keeps that
-// reuse inside L2 on large lattices.
+// walked time slice by time slice, rows of X fastest:
+//   row = ((b * nt + t - t0) * zblock + zz) * nY + y,  z = b * zblock + zz,
+// and the rows are taken in segments of `rseg`: first the parity-0 sites of
+// the segment's rows, then its parity-1 sites, so that consecutive threads
+// cover consecutive compact sites of one parity (a warp touches one half
+// field).  The hops to t +- 1 find their data after one slab-slice of
+// traffic (zblock * nY * nX sites) instead of a whole time slice, which
+// keeps that reuse inside L2 on large lattices.
 __device__ __forceinline__ SiteCoord traversal_coords(const Geom& g, int k) {
   SiteCoord sc;
-  int r = fdiv(k, g.fx);
-  sc.c[3] = k - r * g.n[3];
+  // segment of rseg rows: its parity-0 sites, then its parity-1 sites
+  const int hx = g.n[3] >> 1;
+  const int seg = fdiv(k, g.fseg);
+  int w = k - seg * g.rseg * g.n[3];
+  const int half = w >= g.rseg * hx ? 1 : 0;
+  w -= half * g.rseg * hx;
+  const int rr = fdiv(w, g.fhx);
+  const int j = w - rr * hx;
+  int r = seg * g.rseg + rr;  // row index in traversal order
   int r2 = fdiv(r, g.fy);
   sc.c[2] = r - r2 * g.n[2];
   r = fdiv(r2, g.fzb);
@@ -380,6 +402,7 @@ __device__ __forceinline__ SiteCoord traversal_coords(const Geom& g, int k) {
   r2 = fdiv(r, g.fnt);
   sc.c[0] = r - r2 * g.nt + g.t0;
   sc.c[1] = r2 * g.zblock + zz;
+  sc.c[3] = 2 * j + ((half + sc.c[0] + sc.c[1] + sc.c[2]) & 1);
   sc.lex = ((sc.c[0] * g.n[1] + sc.c[1]) * g.n[2] + sc.c[2]) * g.n[3] + sc.c[3];
   return sc;
 }
