@@ -247,18 +247,24 @@ __device__ __forceinline__ R load_spinor_unscaled(const HalfField& f, int64_t gs
   }
 }
 
-template <int P, typename R>
+// STREAM: evict-first stores (outputs the kernel does not read again)
+template <int P, typename R, bool STREAM = false>
 __device__ __forceinline__ void store_spinor(const HalfField& f, int64_t gstride, int64_t i, const cx<R> v[12]) {
   if constexpr (P == P64) {
     double2* b = reinterpret_cast<double2*>(f.base) + i;
 #pragma unroll
-    for (int c = 0; c < 12; ++c) b[c * gstride] = make_double2(v[c].re, v[c].im);
+    for (int c = 0; c < 12; ++c) {
+      const double2 d = make_double2(v[c].re, v[c].im);
+      if (STREAM) __stcs(b + c * gstride, d); else b[c * gstride] = d;
+    }
   } else if constexpr (P == P32) {
     float4* b = reinterpret_cast<float4*>(f.base) + i;
 #pragma unroll
-    for (int g = 0; g < 6; ++g)
-      b[g * gstride] = make_float4((float)v[2 * g].re, (float)v[2 * g].im, (float)v[2 * g + 1].re,
+    for (int g = 0; g < 6; ++g) {
+      const float4 d = make_float4((float)v[2 * g].re, (float)v[2 * g].im, (float)v[2 * g + 1].re,
                                    (float)v[2 * g + 1].im);
+      if (STREAM) __stcs(b + g * gstride, d); else b[g * gstride] = d;
+    }
   } else {
     float m = 0.f;
 #pragma unroll
@@ -273,9 +279,10 @@ __device__ __forceinline__ void store_spinor(const HalfField& f, int64_t gstride
         __half2 h = __floats2half2_rn((float)v[4 * g + k].re * inv, (float)v[4 * g + k].im * inv);
         w[k] = *reinterpret_cast<unsigned int*>(&h);
       }
-      b[g * gstride] = make_uint4(w[0], w[1], w[2], w[3]);
+      const uint4 d = make_uint4(w[0], w[1], w[2], w[3]);
+      if (STREAM) __stcs(b + g * gstride, d); else b[g * gstride] = d;
     }
-    f.scale[i] = m;
+    if (STREAM) __stcs(f.scale + i, m); else f.scale[i] = m;
   }
 }
 

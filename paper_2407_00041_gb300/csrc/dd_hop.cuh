@@ -330,7 +330,7 @@ __device__ __forceinline__ void hop_thread(const HopArgs& a, int64_t tid) {
     }
     block_apply<PG, R>(M, s, Vh, y, res);
   }
-  store_spinor<POUT, R>(a.out[p], a.gstride, i, res);
+  store_spinor<POUT, R, true>(a.out[p], a.gstride, i, res);
 }
 
 // RHS-blocked variant for several right-hand sides: one thread handles NB
@@ -420,9 +420,9 @@ __device__ __forceinline__ void hop_thread_rb(const HopArgs& a, int64_t tid) {
 #pragma unroll
       for (int c = 0; c < 12; ++c) out[c] = zero<R>();
       block_apply_g<PG, true, R>(M, s, Vh, res[k], out, false);
-      store_spinor<POUT, R>(a.out[p], a.gstride, ibase + k * nrb, out);
+      store_spinor<POUT, R, true>(a.out[p], a.gstride, ibase + k * nrb, out);
     } else {
-      store_spinor<POUT, R>(a.out[p], a.gstride, ibase + k * nrb, res[k]);
+      store_spinor<POUT, R, true>(a.out[p], a.gstride, ibase + k * nrb, res[k]);
     }
   }
 }
