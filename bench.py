@@ -12,7 +12,9 @@ flush is needed between steps.
 
 Algorithmic bytes per site for N right-hand sides (every link, clover
 block and spinor read once, the result written once):
-  FP64 1152 + 384 N,  FP32 576 + 192 N,  FP16 storage 288 + 104 N.
+  FP64 1152 + 384 N,  FP32 576 + 192 N (480 + 192 for one RHS when the
+  library reads two-row FP32 links, which it does for SU(3) links),
+  FP16 storage 288 + 104 N.
 
 The JSON line also carries:
   variants    GB/s of the FP64, FP32 and FP16-storage applies, each with its
@@ -66,8 +68,13 @@ def log(msg):
     print(f"[bench {time.time() - _T0:7.1f}s] {msg}", file=sys.stderr, flush=True)
 
 
+LINK_ROWS_F32 = [3]  # rows per FP32 link read by single-RHS applies (set once the gauge exists)
+
+
 def bytes_per_site(prec, nrhs=1):
     a, b = BYTES[prec]
+    if prec == "f32" and nrhs == 1 and LINK_ROWS_F32[0] == 2:
+        a -= 96  # two-row FP32 links: 192 instead of 288 B per site
     return a + b * nrhs
 
 
@@ -366,7 +373,7 @@ def extra_measurements(dd, torch, stream, op48, psi48, V48, tdist, clocks, alu_p
                                                       dd.DD_LAYOUT_NATIVE, st), "Dhat"), 20)
         # two half-lattice hops read every link twice; A_oo and A_ee^-1 once;
         # five half-field spinor passes (psi_o twice, t_e written and read, out_o)
-        link, clov, spin = {"f32": (288, 288, 96), "f16": (144, 144, 52)}[name]
+        link, clov, spin = {"f32": (96 * LINK_ROWS_F32[0], 288, 96), "f16": (144, 144, 52)}[name]
         bytes_ = 2 * link * V48 + clov * V48 + 5 * spin * (V48 // 2)
         out[f"dhat_{name}"] = {"ms": t * 1e3, "gbs_formula": bytes_ / t / 1e9}
     # lattices of config 3
@@ -555,7 +562,10 @@ def main():
     lat = dd.Lattice(dims, -1)
     gauge = dd.Gauge(lat, U)
     op = dd.Operator(gauge, M0, CSW)
-    log("handles ready")
+    # SU(3) links: the FP32 copy keeps two rows per link (192 instead of 288 B)
+    rows32 = dd.lib.dd_gauge_stored_rows(gauge.h, dd.DD_PREC_F32)
+    LINK_ROWS_F32[0] = rows32
+    log(f"handles ready (single-RHS FP32 applies read {rows32} rows per link)")
     psi_dev = torch.from_numpy(psi).to("cuda")
 
     gpu_launches = 0
@@ -700,7 +710,7 @@ def main():
         "dtype": {"f64": "f64", "f32": "f32", "f16": "f32 (fp16 storage)"}[args.prec], "data": "synthetic",
         "config": {"workload": (WORKLOAD if dims == DIMS else WORKLOAD.replace("48^3x96", args.dims)).replace(
                        "1 RHS", f"{N} RHS"),
-                   "precision": args.prec, "nrhs": N, "sites": V,
+                   "precision": args.prec, "nrhs": N, "sites": V, "f32_link_rows_single_rhs": rows32,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "inputs (>8 GB) larger than L2; no flush"},
         "roofline": head["roofline"], "variants": variants, "e2e": e2e, "solve": solve,

@@ -116,6 +116,18 @@ int dd_lattice_create(const int dims[4], int t_bc, dd_lattice** out);
 int dd_lattice_destroy(dd_lattice* lat);
 int64_t dd_lattice_volume(const dd_lattice* lat);
 
+/* Rows per link that single-RHS applies read in precision `prec`
+ * (DD_PREC_F64 / F32 / F16): 3, or 2 for DD_PREC_F32 when every link passed
+ * to dd_gauge_create is an SU(3) matrix to 1e-6 (max of |U U^H - 1| and
+ * |det U - 1|).  The gauge handle then holds a second FP32 copy with rows 0
+ * and 1 only (192 instead of 288 bytes per site), and single-RHS stencils
+ * rebuild row 2 as the complex conjugate of the cross product of rows 0 and
+ * 1, which holds for SU(3) matrices (Section 1.1 of the thesis defines the
+ * links as SU(3) elements); several-RHS launches keep reading three rows.
+ * The environment variable DD_RECON=0, read at gauge creation, skips the
+ * two-row copy.  DD_ERR_UNSUPPORTED if the copy of `prec` was not created. */
+int dd_gauge_stored_rows(const dd_gauge* g, int prec);
+
 /*
  * Gauge field U_mu(x) in SU(3) (Section 1.1), given as complex double
  * [V][4 mu][3][3] (row-major colour matrices; U_mu(x) links x to x + mu).

@@ -78,6 +78,7 @@ SIGNATURES = {
     "dd_dot": (_I, [_P, _P, _L, _I, _P, _P]),
     "dd_probe_flops": (_I, [_I, _P, _P]),
     "dd_device_status": (_I, [_P]),
+    "dd_gauge_stored_rows": (_I, [_P, _I]),
     "dd_dot_noalloc": (_I, [_P, _P, _L, _I, _P, _P]),
 }
 

@@ -1,4 +1,5 @@
 // C ABI entry points (declared in include/dd_wilson.h).
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -201,6 +202,13 @@ int dd_gauge_create(const dd_lattice* lat, const double* U, int location, unsign
     Ud = reinterpret_cast<const double*>(staging.ptr);
   }
   if (s == DD_OK) s = links_to_native(lat, Ud, g, 0);
+  if (s == DD_OK) s = links_su3_deviation(g, &g->su3_deviation, 0);
+  // two-row FP32 links when every link is SU(3) to FP32 accuracy (DD_RECON=0
+  // keeps all three rows)
+  if (s == DD_OK && (g->prec_mask & DD_PREC_F32) && g->su3_deviation < 1e-6) {
+    const char* e = getenv("DD_RECON");
+    if (!e || atoi(e) != 0) s = links_to_recon32(g, 0);
+  }
   if (s == DD_OK && cudaDeviceSynchronize() != cudaSuccess) s = cuda_fail(cudaGetLastError(), "link conversion");
   if (s != DD_OK) {
     delete g;
@@ -208,6 +216,13 @@ int dd_gauge_create(const dd_lattice* lat, const double* U, int location, unsign
   }
   *out = g;
   return DD_OK;
+}
+
+int dd_gauge_stored_rows(const dd_gauge* g, int prec) {
+  if (!g) return fail(DD_ERR_ARG, "null gauge");
+  if (prec != DD_PREC_F64 && prec != DD_PREC_F32 && prec != DD_PREC_F16) return fail(DD_ERR_ARG, "bad precision");
+  if (!(g->prec_mask & (unsigned)prec)) return fail(DD_ERR_UNSUPPORTED, "precision not created in the gauge handle");
+  return prec == DD_PREC_F32 && g->recon32 ? 2 : 3;
 }
 
 int dd_gauge_destroy(dd_gauge* g) {

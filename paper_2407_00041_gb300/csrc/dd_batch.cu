@@ -103,6 +103,7 @@ int stage(dd_batch* b, const void* const* ins, void* const* outs, cudaStream_t s
       a.M[p] = op->M(pi, p);
     }
     a.beta = -0.5;
+    a.recon = 0;  // three-row links (the batch carries several RHS per lattice)
     const int64_t slots = 2 * lat->Vh * ((b->nrhs[i] + a.rhs_block - 1) / a.rhs_block);
     starts[i + 1] = starts[i] + (slots + b->tile - 1) / b->tile;
   }

@@ -113,8 +113,31 @@ __device__ __forceinline__ void hop_regs(cx<R> acc[12], const cx<R> psi[12], con
 // one element per group, FP32 two, FP16 four.  Direction mu uses elements
 // 9 mu .. 9 mu + 8, i.e. 9, 5 or 3 group loads; a group shared by two
 // directions is read twice (the second time from cache).
+// FP32 with `recon`: the copy keeps rows 0 and 1 only ([12 groups][Vh],
+// direction mu in groups 3 mu .. 3 mu + 2) and row 2 of the SU(3) matrix is
+// rebuilt as the complex conjugate of the cross product of rows 0 and 1.
 template <int PG, typename R>
-__device__ __forceinline__ void load_link(const void* Ubase, int64_t s, int64_t Vh, int mu, cx<R> u[9]) {
+__device__ __forceinline__ void load_link(const void* Ubase, int64_t s, int64_t Vh, int mu, cx<R> u[9],
+                                          bool recon = false) {
+  if constexpr (PG == P32) {
+    if (recon) {
+      const float4* p = reinterpret_cast<const float4*>(Ubase) + s;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float4 v = __ldg(p + (int64_t)(3 * mu + k) * Vh);
+        u[2 * k] = mk<R>(v.x, v.y);
+        u[2 * k + 1] = mk<R>(v.z, v.w);
+      }
+      auto cross = [](cx<R> a, cx<R> b, cx<R> c, cx<R> d) {  // conj(a b - c d)
+        const cx<R> t = cfma(neg(c), d, cmul(a, b));
+        return mk(t.re, -t.im);
+      };
+      u[6] = cross(u[1], u[5], u[2], u[4]);
+      u[7] = cross(u[2], u[3], u[0], u[5]);
+      u[8] = cross(u[0], u[4], u[1], u[3]);
+      return;
+    }
+  }
   if constexpr (PG == P64) {
     const double2* p = reinterpret_cast<const double2*>(Ubase) + (int64_t)(9 * mu) * Vh + s;
 #pragma unroll
@@ -154,9 +177,9 @@ __device__ __forceinline__ void load_link(const void* Ubase, int64_t s, int64_t 
 // The same with the link read from its native layout.
 template <int PG, int MU, int T, bool ADJ, typename R>
 __device__ __forceinline__ void hop(cx<R> acc[12], const cx<R> psi[12], const void* Ubase, int64_t s, int64_t Vh,
-                                    R sign) {
+                                    R sign, bool recon) {
   cx<R> u[9];
-  load_link<PG, R>(Ubase, s, Vh, MU, u);
+  load_link<PG, R>(Ubase, s, Vh, MU, u, recon);
   hop_regs<MU, T, ADJ, R>(acc, psi, u, sign);
 }
 
@@ -275,11 +298,11 @@ __device__ __forceinline__ void hop_thread(const HopArgs& a, int64_t tid) {
     int nl = nb_fwd(a.g, sc, MU);                                                          \
     R sg = (MU == 0 && sc.c[0] == a.g.n[0] - 1) ? (R)a.g.t_bc : (R)1;                      \
     sg *= load_spinor_unscaled<PIN, R>(a.in[q], a.gstride, (int64_t)(nl >> 1) * a.nrhs + r, psi); \
-    hop<PG, MU, TF, false, R>(acc, psi, a.U[p], s, Vh, sg);                                \
+    hop<PG, MU, TF, false, R>(acc, psi, a.U[p], s, Vh, sg, a.recon);                       \
     nl = nb_bwd(a.g, sc, MU);                                                              \
     sg = (MU == 0 && sc.c[0] == 0) ? (R)a.g.t_bc : (R)1;                                   \
     sg *= load_spinor_unscaled<PIN, R>(a.in[q], a.gstride, (int64_t)(nl >> 1) * a.nrhs + r, psi); \
-    hop<PG, MU, TB, true, R>(acc, psi, a.U[q], nl >> 1, Vh, sg);                           \
+    hop<PG, MU, TB, true, R>(acc, psi, a.U[q], nl >> 1, Vh, sg, a.recon);                  \
   }
   DD_HOP_DIR(0)
   DD_HOP_DIR(1)
@@ -333,7 +356,7 @@ __device__ __forceinline__ void hop_thread(const HopArgs& a, int64_t tid) {
   store_spinor<POUT, R, true>(a.out[p], a.gstride, i, res);
 }
 
-// RHS-blocked variant for several right-hand sides: one thread handles NB
+// RHS-blocked variant for several right-hand sides (three-row links only): one thread handles NB
 // right-hand sides r = rb + k * (N / NB), k < NB, of one site, so each link
 // element is loaded once per NB spinors (link reuse across RHS in
 // registers).  The strided RHS choice keeps every load instruction of a warp

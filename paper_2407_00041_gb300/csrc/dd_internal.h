@@ -71,9 +71,16 @@ struct dd_gauge {
   const dd_lattice* lat;
   unsigned prec_mask;
   // native links per precision (index 0: F64, 1: F32, 2: F16):
-  // [parity][mu][9][Vh] complex elements
+  // [parity][mu][9][Vh] complex elements, in 16-byte groups for F32 / F16
   dd::DevBuf links[3];
+  // when every link is SU(3): a second FP32 copy with rows 0 and 1 only
+  // ([parity][12 float4 groups][Vh]; the kernels rebuild row 2), used by
+  // single-RHS launches
+  dd::DevBuf links32r;
+  int recon32 = 0;
+  double su3_deviation = 0.0;  // max over links of |U U^H - 1| and |det U - 1|
   const void* U(int pi, int parity) const;
+  const void* U2(int parity) const;  // the two-row FP32 copy
 };
 
 struct dd_clover {
@@ -134,6 +141,10 @@ int op_dhat_residual(const dd_clover* op, int pg, int pv, const Field& bhat, con
 
 // ---- setup kernels (dd_setup.cu) ----
 int links_to_native(const dd_lattice* lat, const double* U_canon_dev, dd_gauge* g, cudaStream_t st);
+// max over links of max(|U U^H - 1|, |det U - 1|) from the FP64 copy (synchronises)
+int links_su3_deviation(const dd_gauge* g, double* dev, cudaStream_t st);
+// build the two-row FP32 copy: [parity][12 groups][Vh] float4
+int links_to_recon32(dd_gauge* g, cudaStream_t st);
 int links_to_canonical(const dd_gauge* g, double* U_canon_dev, cudaStream_t st);
 int clover_build(dd_clover* op, cudaStream_t st);  // FP64 blocks, A_ee^{-1}, demoted copies
 int clover_to_dense(const dd_clover* op, double* A_dev /*[V][144] complex*/, cudaStream_t st);

@@ -171,6 +171,13 @@ HopArgs base_args(const dd_clover* op, int pg, int nrhs) {
   }
   a.beta = -0.5;
   a.rhs_block = 1;
+  // single right-hand side: the two-row FP32 links (fewer bytes; the
+  // RHS-blocked kernels of several RHS are faster with three rows)
+  a.recon = pg == P32 && nrhs == 1 && op->gauge->recon32;
+  if (a.recon) {
+    a.U[0] = op->gauge->U2(0);
+    a.U[1] = op->gauge->U2(1);
+  }
   return a;
 }
 
@@ -361,6 +368,11 @@ const void* dd_gauge::U(int pi, int parity) const {
   if (!links[pi].ptr) return nullptr;
   const size_t elem = pi == 0 ? 16 : pi == 1 ? 8 : 4;
   return reinterpret_cast<const char*>(links[pi].ptr) + (size_t)parity * 36 * lat->Vh * elem;
+}
+
+const void* dd_gauge::U2(int parity) const {
+  if (!links32r.ptr) return nullptr;
+  return reinterpret_cast<const char*>(links32r.ptr) + (size_t)parity * 24 * lat->Vh * sizeof(float2);
 }
 
 const void* dd_clover::M(int pi, int parity) const {

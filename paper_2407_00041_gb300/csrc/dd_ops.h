@@ -30,6 +30,7 @@ struct HopArgs {
   double beta;
   int rhs_block;  // batched launch: right-hand sides per thread (1 or 2)
   FastDiv fblk;   // division of the thread index by the RHS slots per site (set by the launcher)
+  int recon;      // FP32 links stored as rows 0 and 1 (the third row is rebuilt)
 };
 
 // Self-coupling apply without hopping: out = M y on npar parities.

@@ -1,6 +1,8 @@
 // Setup kernels: native link layout, self-coupling construction (Eq. 1.11,
 // 1.12, 2.5) and inversion, precision copies, and canonical <-> native field
 // conversion.
+#include <cstring>
+
 #include "dd_internal.h"
 
 namespace dd {
@@ -58,6 +60,65 @@ __global__ void k_links_to_native(LexGeom g, const double2* __restrict__ Uc, dou
     const int E = 9 * mu + e;
     if (U32) U32[pbase + ((int64_t)(E >> 1) * g.Vh + s) * 2 + (E & 1)] = make_float2((float)v.x, (float)v.y);
     if (U16) U16[pbase + ((int64_t)(E >> 2) * g.Vh + s) * 4 + (E & 3)] = __floats2half2_rn((float)v.x, (float)v.y);
+  }
+}
+
+// max(|U U^H - 1|, |det U - 1|) of every link, reduced with an atomic max on
+// the bit pattern of the (non-negative) float
+__global__ void k_su3_deviation(int64_t nlinks, const double2* __restrict__ U64, int64_t Vh, unsigned* out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float dev = 0.f;
+  if (t < nlinks) {
+    // t = (parity * 4 + mu) * Vh + s
+    const int64_t s = t % Vh, pm = t / Vh;
+    const double2* b = U64 + pm * 9 * Vh + s;
+    double2 u[9];
+    for (int e = 0; e < 9; ++e) u[e] = b[e * Vh];
+    double m = 0.0;
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        double re = 0.0, im = 0.0;  // (U U^H)_ij
+        for (int k = 0; k < 3; ++k) {
+          const double2 a = u[3 * i + k], c = u[3 * j + k];
+          re += a.x * c.x + a.y * c.y;
+          im += a.y * c.x - a.x * c.y;
+        }
+        if (i == j) re -= 1.0;
+        m = fmax(m, fmax(fabs(re), fabs(im)));
+      }
+    auto cm = [](double2 a, double2 c) { return make_double2(a.x * c.x - a.y * c.y, a.x * c.y + a.y * c.x); };
+    auto cs = [](double2 a, double2 c) { return make_double2(a.x - c.x, a.y - c.y); };
+    const double2 m0 = cs(cm(u[4], u[8]), cm(u[5], u[7]));
+    const double2 m1 = cs(cm(u[5], u[6]), cm(u[3], u[8]));
+    const double2 m2 = cs(cm(u[3], u[7]), cm(u[4], u[6]));
+    const double2 det = make_double2(cm(u[0], m0).x + cm(u[1], m1).x + cm(u[2], m2).x,
+                                     cm(u[0], m0).y + cm(u[1], m1).y + cm(u[2], m2).y);
+    m = fmax(m, fmax(fabs(det.x - 1.0), fabs(det.y)));
+    dev = isfinite(m) ? (float)fmin(m, 1e30) : 1e30f;
+  }
+  // block max, then one atomic per block
+  __shared__ float red[256];
+  red[threadIdx.x] = dev;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicMax(out, __float_as_uint(red[0]));
+}
+
+// FP32 copy with rows 0 and 1: element E = 6 mu + e (e < 6) of a site in
+// float4 group E / 2, [parity][12 groups][Vh]
+__global__ void k_links_recon32(int64_t nlinks, const double2* __restrict__ U64, int64_t Vh, float2* U32) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nlinks) return;
+  const int64_t s = t % Vh, pm = t / Vh;
+  const int64_t p = pm / 4, mu = pm % 4;
+  const double2* b = U64 + pm * 9 * Vh + s;
+  for (int e = 0; e < 6; ++e) {
+    const double2 v = b[e * Vh];
+    const int64_t E = 6 * mu + e;
+    U32[p * 24 * Vh + ((E >> 1) * Vh + s) * 2 + (E & 1)] = make_float2((float)v.x, (float)v.y);
   }
 }
 
@@ -434,6 +495,33 @@ int links_to_native(const dd_lattice* lat, const double* Uc, dd_gauge* g, cudaSt
       lex_geom(lat), reinterpret_cast<const double2*>(Uc), reinterpret_cast<double2*>(g->links[0].ptr),
       reinterpret_cast<float2*>(g->links[1].ptr), reinterpret_cast<__half2*>(g->links[2].ptr));
   DD_CUDA(cudaGetLastError());
+  return DD_OK;
+}
+
+int links_su3_deviation(const dd_gauge* g, double* dev, cudaStream_t st) {
+  const int64_t n = g->lat->V * 4;
+  DevBuf out;
+  DD_TRY(out.alloc(sizeof(unsigned)));
+  DD_CUDA(cudaMemsetAsync(out.ptr, 0, sizeof(unsigned), st));
+  k_su3_deviation<<<nblk(n, 256), 256, 0, st>>>(n, reinterpret_cast<const double2*>(g->links[0].ptr), g->lat->Vh,
+                                                reinterpret_cast<unsigned*>(out.ptr));
+  DD_CUDA(cudaGetLastError());
+  unsigned bits = 0;
+  DD_CUDA(cudaMemcpyAsync(&bits, out.ptr, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  DD_CUDA(cudaStreamSynchronize(st));
+  float f;
+  memcpy(&f, &bits, sizeof(f));
+  *dev = f;
+  return DD_OK;
+}
+
+int links_to_recon32(dd_gauge* g, cudaStream_t st) {
+  const int64_t n = g->lat->V * 4;
+  DD_TRY(g->links32r.alloc((size_t)g->lat->V * 24 * sizeof(float2)));
+  k_links_recon32<<<nblk(n, 128), 128, 0, st>>>(n, reinterpret_cast<const double2*>(g->links[0].ptr), g->lat->Vh,
+                                               reinterpret_cast<float2*>(g->links32r.ptr));
+  DD_CUDA(cudaGetLastError());
+  g->recon32 = 1;
   return DD_OK;
 }
 

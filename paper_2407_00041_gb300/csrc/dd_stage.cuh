@@ -148,7 +148,7 @@ __device__ __forceinline__ void stage_issue(const HopArgs& a, int64_t k, float4*
 // slot (six groups of `units` 16-byte units).
 template <int PG, int MU, int T, bool ADJ>
 __device__ __forceinline__ void stage_hop(cx<float> acc[12], const float4* slot, int64_t units, int64_t u,
-                                          const void* U, int64_t ls, int64_t Vh, float sign) {
+                                          const void* U, int64_t ls, int64_t Vh, float sign, bool recon) {
   cx<float> psi[12];
 #pragma unroll
   for (int gr = 0; gr < kStageGroups; ++gr) {
@@ -157,7 +157,7 @@ __device__ __forceinline__ void stage_hop(cx<float> acc[12], const float4* slot,
     psi[2 * gr + 1] = mk<float>(v.z, v.w);
   }
   cx<float> lk[9];
-  load_link<PG, float>(U, ls, Vh, MU, lk);
+  load_link<PG, float>(U, ls, Vh, MU, lk, recon);
   hop_regs<MU, T, ADJ, float>(acc, psi, lk, sign);
 }
 
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(MINB == 1 ? 512 : 256, MINB) k_hop_stage(const
       block_apply<PG, float>(a.M[p], s, Vh, y, acc);
     }
     cx<float> la[9], lb[9], lc[9];
-    if (active) load_link<PG, float>(a.U[p], s, Vh, 0, la);
+    if (active) load_link<PG, float>(a.U[p], s, Vh, 0, la, a.recon);
 
 // wait for local stage k, run BODY on its slot, release the slot
 #define DD_STAGE_STEP(...)                                                               \
@@ -267,19 +267,19 @@ __global__ void __launch_bounds__(MINB == 1 ? 512 : 256, MINB) k_hop_stage(const
   }
 
     do {
-      if (active) load_link<PG, float>(a.U[q], (int64_t)stage_row(a.g, c, 1) * hx + j, Vh, 0, lb);
+      if (active) load_link<PG, float>(a.U[q], (int64_t)stage_row(a.g, c, 1) * hx + j, Vh, 0, lb, a.recon);
       DD_STAGE_STEP(stage_hop_l<0, TF, false>(acc, sl, units, u, la, sgf);)
-      if (active) load_link<PG, float>(a.U[p], s, Vh, 1, la);
+      if (active) load_link<PG, float>(a.U[p], s, Vh, 1, la, a.recon);
       DD_STAGE_STEP(stage_hop_l<0, TB, true>(acc, sl, units, u, lb, sgb);)
-      if (active) load_link<PG, float>(a.U[q], (int64_t)stage_row(a.g, c, 3) * hx + j, Vh, 1, lb);
+      if (active) load_link<PG, float>(a.U[q], (int64_t)stage_row(a.g, c, 3) * hx + j, Vh, 1, lb, a.recon);
       DD_STAGE_STEP(stage_hop_l<1, TF, false>(acc, sl, units, u, la, beta);)
-      if (active) load_link<PG, float>(a.U[p], s, Vh, 2, la);
+      if (active) load_link<PG, float>(a.U[p], s, Vh, 2, la, a.recon);
       DD_STAGE_STEP(stage_hop_l<1, TB, true>(acc, sl, units, u, lb, beta);)
-      if (active) load_link<PG, float>(a.U[q], (int64_t)stage_row(a.g, c, 5) * hx + j, Vh, 2, lb);
+      if (active) load_link<PG, float>(a.U[q], (int64_t)stage_row(a.g, c, 5) * hx + j, Vh, 2, lb, a.recon);
       DD_STAGE_STEP(stage_hop_l<2, TF, false>(acc, sl, units, u, la, beta);)
       if (active) {
-        load_link<PG, float>(a.U[p], s, Vh, 3, la);
-        load_link<PG, float>(a.U[q], row * hx + jb, Vh, 3, lc);
+        load_link<PG, float>(a.U[p], s, Vh, 3, la, a.recon);
+        load_link<PG, float>(a.U[q], row * hx + jb, Vh, 3, lc, a.recon);
       }
       DD_STAGE_STEP(stage_hop_l<2, TB, true>(acc, sl, units, u, lb, beta);)
       DD_STAGE_STEP(stage_hop_l<3, TF, false>(acc, sl, units, (int64_t)jf * N + r, la, beta);

@@ -172,3 +172,24 @@ def test_host_layout_pipelined_equals_device(dims, prec):
         host = apply(op, which, prec, psi, layout=dd.DD_LAYOUT_CANONICAL_HOST)
         dev = apply(op, which, prec, psi)
         assert np.array_equal(host, dev)
+
+
+def test_two_row_fp32_links_and_non_su3_fallback():
+    """SU(3) links: single-RHS FP32 applies read a two-row copy and rebuild
+    the third row; links that are not SU(3) get no two-row copy.  Both match
+    the oracle, which uses the links as given."""
+    dims = (6, 4, 2, 8)
+    U = synthetic.gauge(dims)
+    _, lat, g, op = make(dims, U=U)
+    assert dd.lib.dd_gauge_stored_rows(g.h, dd.DD_PREC_F32) == 2
+    assert dd.lib.dd_gauge_stored_rows(g.h, dd.DD_PREC_F64) == 3
+    # a non-unitary perturbation of every link
+    W = U * (1.0 + 0.01 * synthetic.gaussian(U.size, seed=9).real.reshape(U.shape))
+    _, lat2, g2, op2 = make(dims, U=W)
+    assert dd.lib.dd_gauge_stored_rows(g2.h, dd.DD_PREC_F32) == 3
+    psi = synthetic.spinor(dims, nrhs=1)  # one RHS: the launches that read the two-row copy
+    for links, o in ((U, op), (W, op2)):
+        A = oracle.clover(links, dims, M0, CSW)
+        for which, ref_fn in ((dd.DD_OP_D, oracle.apply_D), (dd.DD_OP_DH, oracle.apply_DH)):
+            got = apply(o, which, dd.DD_PREC_F32, psi)
+            assert rel(got[0], ref_fn(links, A, psi[0].reshape(-1, 12), dims)) < TOL[dd.DD_PREC_F32]
