@@ -144,26 +144,8 @@ __device__ __forceinline__ void stage_issue(const HopArgs& a, int64_t k, float4*
   for (int gr = 0; gr < kStageGroups; ++gr) bulk_copy_g2s(slot + gr * units, src + gr * a.gstride, bytes, bar);
 }
 
-// One hop of the output (s, r) with the neighbour spinor at unit `u` of the
-// slot (six groups of `units` 16-byte units).
-template <int PG, int MU, int T, bool ADJ>
-__device__ __forceinline__ void stage_hop(cx<float> acc[12], const float4* slot, int64_t units, int64_t u,
-                                          const void* U, int64_t ls, int64_t Vh, float sign, bool recon) {
-  cx<float> psi[12];
-#pragma unroll
-  for (int gr = 0; gr < kStageGroups; ++gr) {
-    const float4 v = slot[gr * units + u];
-    psi[2 * gr] = mk<float>(v.x, v.y);
-    psi[2 * gr + 1] = mk<float>(v.z, v.w);
-  }
-  cx<float> lk[9];
-  load_link<PG, float>(U, ls, Vh, MU, lk, recon);
-  hop_regs<MU, T, ADJ, float>(acc, psi, lk, sign);
-}
-
-// MINB = 1: up to 512 threads, 128 registers; MINB = 3: up to 256 threads,
-// 80 registers (three resident CTAs per SM).
-// The same with the link already in registers.
+// One hop of the output with the neighbour spinor at unit `u` of the slot
+// (six groups of `units` 16-byte units) and the link already in registers.
 template <int MU, int T, bool ADJ>
 __device__ __forceinline__ void stage_hop_l(cx<float> acc[12], const float4* slot, int64_t units, int64_t u,
                                             const cx<float> lk[9], float sign) {
@@ -177,9 +159,11 @@ __device__ __forceinline__ void stage_hop_l(cx<float> acc[12], const float4* slo
   hop_regs<MU, T, ADJ, float>(acc, psi, lk, sign);
 }
 
+// MINB = 1: up to 512 threads, 128 registers; MINB = 3: up to 256 threads,
+// 80 registers (three resident CTAs per SM).
 template <int PG, bool DAG, int MINB>
-__global__ void __launch_bounds__(MINB == 1 ? 512 : 256, MINB) k_hop_stage(const HopArgs a, int nslots, int64_t ntiles, int* err,
-                                                                     long long budget, int poison) {
+__global__ void __launch_bounds__(MINB == 1 ? 512 : 256, MINB)
+    k_hop_stage(const HopArgs a, int nslots, int64_t ntiles, int* err, long long budget, int poison) {
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
   float4* slots = reinterpret_cast<float4*>(smem + kStageHeader);
@@ -333,7 +317,7 @@ bool launch_stage(const HopArgs& a, bool dagger, cudaStream_t st, cudaError_t* e
   while (nslots > 2 && kStageHeader + nslots * slot_bytes > max_smem) --nslots;
   const size_t smem = kStageHeader + nslots * slot_bytes;
   if (smem > max_smem) return false;
-  static const int narrow_ok = stage_env("DD_STAGE_NARROW", 1);
+  static const int narrow_ok = stage_env("DD_STAGE_NARROW", 0);  // spills; measured slower
   const int threads = (int)((units + 31) / 32 * 32);
   const bool narrow = narrow_ok && threads <= 256;
   auto kern = narrow ? (dagger ? k_hop_stage<PG, true, 3> : k_hop_stage<PG, false, 3>)
