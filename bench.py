@@ -612,7 +612,7 @@ def main():
                           peaks["hbm_gbs"], "gflops_nominal": gflops, "bound": bound,
                           "roof_frac": frac, "bytes_per_site": bytes_per_site(prec, N)}
         if prec == args.prec:
-            traffic = profile_traffic(prec) if N == 1 else None
+            traffic = profile_traffic(prec) if N == 1 and dims == DIMS else None
             head = {"value": gbs, "ms": ms, "kernel_s": kern,
                     "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": frac,
                                  "traffic": traffic,
