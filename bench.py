@@ -612,7 +612,8 @@ def main():
                           peaks["hbm_gbs"], "gflops_nominal": gflops, "bound": bound,
                           "roof_frac": frac, "bytes_per_site": bytes_per_site(prec, N)}
         if prec == args.prec:
-            traffic = profile_traffic(prec) if N == 1 and dims == DIMS else None
+            traffic = (profile_traffic(prec) if N == 1 and dims == DIMS and (prec != "f32" or LINK_ROWS_F32[0] == 2)
+                       else None)  # the captured launch: 48^3x96, one RHS, two-row FP32 links
             head = {"value": gbs, "ms": ms, "kernel_s": kern,
                     "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": frac,
                                  "traffic": traffic,
