@@ -3,10 +3,10 @@
 TEST INFRASTRUCTURE ONLY (part of the CPU oracle).
 
 Both follow the algorithms step by step in numpy, in FP64:
-  * restart loop: r = b - A x, beta = ||r||, v_1 = r / beta (lines 4-6);
-  * Arnoldi with modified Gram-Schmidt (lines 7-16), h_ij = <w, v_i> = v_i^H w;
-  * least squares y = argmin ||beta e_1 - H y|| (line 18) via numpy's lstsq;
-  * x <- x + Z y (FGMRES, line 19) or x <- x + M^{-1} V y (GMRES, line 19).
+  * restart loop: r = b - A x, beta = ||r||, v_1 = r / beta;
+  * Arnoldi with modified Gram-Schmidt, h_ij = <w, v_i> = v_i^H w;
+  * least squares y = argmin ||beta e_1 - H y|| via numpy's lstsq;
+  * x <- x + Z y (FGMRES) or x <- x + M^{-1} V y (GMRES).
 
 Readings where the thesis is silent:
   * termination: ||b - A x|| < tol * ||b - A x_0|| checked on the true
@@ -24,7 +24,7 @@ import numpy as np
 
 class Stats:
     def __init__(self):
-        self.applies = 0          # operator applications (lines 4 and 9)
+        self.applies = 0          # operator applications (residuals and Arnoldi steps)
         self.cycles = 0           # restart cycles run
         self.inner_steps = []     # Arnoldi steps per cycle
         self.true_residuals = []  # ||b - A x|| at the start of each cycle
@@ -45,9 +45,9 @@ def _krylov(A, b, m, tol, max_restarts, x0, precond, flexible, record):
     st = Stats()
     r0norm = None
     while True:
-        r = b - A(x)                                   # line 4
+        r = b - A(x)                                   # residual of the cycle
         st.applies += 1
-        beta = np.linalg.norm(r)                       # line 5
+        beta = np.linalg.norm(r)
         st.true_residuals.append(beta)
         if r0norm is None:
             r0norm = beta
@@ -57,32 +57,32 @@ def _krylov(A, b, m, tol, max_restarts, x0, precond, flexible, record):
         if st.cycles >= max_restarts:
             break
         st.cycles += 1
-        V = [r / beta]                                 # line 6
+        V = [r / beta]                                 # first basis vector
         Z = []
-        H = np.zeros((m + 1, m), dtype=np.complex128)  # line 2
+        H = np.zeros((m + 1, m), dtype=np.complex128)  # Hessenberg matrix
         k = 0
-        for j in range(m):                             # line 7
-            z = precond(j, V[j])                       # line 8
+        for j in range(m):                             # Arnoldi steps
+            z = precond(j, V[j])                       # z_j = M_j^{-1} v_j
             Z.append(z)
-            w = A(z)                                   # line 9
+            w = A(z)
             st.applies += 1
-            for i in range(j + 1):                     # lines 10-13 (MGS)
+            for i in range(j + 1):                     # modified Gram-Schmidt
                 H[i, j] = np.vdot(V[i], w)
                 w = w - H[i, j] * V[i]
-            H[j + 1, j] = np.linalg.norm(w)            # line 14
+            H[j + 1, j] = np.linalg.norm(w)
             k = j + 1
             _, res = _lsq(H, beta, k)
             if record is not None:
                 record.append((V[: j + 1], H[: j + 2, : j + 1].copy(), Z[:]))
             if res < tol * r0norm or abs(H[j + 1, j]) < tol / 10:
                 break
-            V.append(w / H[j + 1, j])                  # line 15
+            V.append(w / H[j + 1, j])                  # next basis vector
         st.inner_steps.append(k)
-        y, _ = _lsq(H, beta, k)                        # line 18
+        y, _ = _lsq(H, beta, k)                        # least squares
         if flexible:
-            x = x + np.stack(Z[:k], axis=1) @ y        # line 19 (Algorithm 2)
+            x = x + np.stack(Z[:k], axis=1) @ y        # Algorithm 2: x + Z_m y
         else:
-            x = x + precond(None, np.stack(V[:k], axis=1) @ y)  # line 19 (Algorithm 1)
+            x = x + precond(None, np.stack(V[:k], axis=1) @ y)  # Algorithm 1: x + M^{-1} V_m y
     return x, st
 
 

@@ -7,24 +7,24 @@
 //
 // Inner solve: FGMRES(m) with M_j = I (so z_j = v_j) on the even-odd Schur
 // operator Dhat (odd sites) or on D, in the inner precision.  Each Arnoldi
-// step applies the operator once (Algorithm 2, line 9) and orthogonalises
-// with classical Gram-Schmidt applied twice (an equivalent of the modified
-// Gram-Schmidt of lines 10-13 that reads every basis vector in one pass),
-// inner products accumulated in FP64.  The small least-squares problem of
-// line 18 is solved on the host with complex Givens rotations, whose
+// step applies the operator once (Algorithm 2) and orthogonalises with
+// classical Gram-Schmidt (one pass, or two with gs_passes = 2) in place of the
+// algorithm's modified Gram-Schmidt: it reads every basis vector once per
+// pass; inner products accumulated in FP64.  The small least-squares problem is
+// solved on the host with complex Givens rotations, whose
 // residual estimate is checked after every step; a cycle also ends when
 // |h_{j+1,j}| falls below tol / 10 of ||f|| (the breakdown rule after
 // Algorithm 1).  Right-hand sides that have converged are masked out (their
 // new basis vectors are scaled by zero).
 //
-// Preconditioners M_j (Algorithm 2, line 8):
+// Preconditioners M_j (Algorithm 2):
 //   none    z_j = v_j
 //   normal  the fixed right preconditioner M^{-1} = A^H: A M^{-1} = A A^H is
 //           Hermitian positive definite, so restarted FGMRES cannot stagnate
 //   cgnr    the flexible preconditioner z_j = k steps of the conjugate-gradient
 //           method on the normal equations A^H A z = A^H v_j (from z = 0), run
 //           on the device with step sizes kept in device memory; Z_m is stored
-//           and x += Z_m y (line 19).
+//           and x += Z_m y.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -120,7 +120,7 @@ struct Inner {
     if (eo) return op_Dhat(op, pg, pv, dagger, fv(i), fv(out), field_view(op->lat, pv, 2, tmp.ptr, N), st);
     return op_D(op, pg, pv, dagger, fv(i), fv(out), st);
   }
-  // w = A M^{-1} v (Algorithm 2, lines 8-9)
+  // w = A M^{-1} v (Algorithm 2)
   int apply(const void* v, void* out, cudaStream_t st) {
     if (!normal) return apply_op(v, out, false, st);
     DD_TRY(apply_op(v, zt.ptr, true, st));
@@ -208,7 +208,7 @@ struct Inner {
     bool done = false;
     for (int cyc = 0; cyc < max_restarts && !done; ++cyc) {
       ++cycles;
-      // residual of this cycle (Algorithm 2, line 4); x0 = 0 on the first
+      // residual of this cycle (Algorithm 2); x0 = 0 on the first
       if (cyc == 0) {
         DD_CUDA(cudaMemcpyAsync(rvec.ptr, f, vbytes, cudaMemcpyDeviceToDevice, st));
       } else {
@@ -220,7 +220,7 @@ struct Inner {
         DD_CUDA(cudaMemcpyAsync(dcoef, hc, N * sizeof(double2), cudaMemcpyHostToDevice, st));
         DD_TRY(axpys(vw, 1, dcoef, -1.0, rvec.ptr, st));
       }
-      DD_TRY(norms(rvec.ptr, beta, st));  // line 5
+      DD_TRY(norms(rvec.ptr, beta, st));  // beta = ||r||
       int nlive = 0;
       for (int r = 0; r < N; ++r) {
         live[r] = beta[r] > tol_rel[r] * fnorm[r] && fnorm[r] > 0.0;
@@ -233,20 +233,20 @@ struct Inner {
       if (!nlive) break;
       for (int r = 0; r < N; ++r) hc[r] = make_double2(live[r] ? 1.0 / beta[r] : 0.0, 0.0);
       DD_CUDA(cudaMemcpyAsync(dcoef, hc, N * sizeof(double2), cudaMemcpyHostToDevice, st));
-      DD_TRY(scale(dcoef, rvec.ptr, V(0), st));  // line 6
+      DD_TRY(scale(dcoef, rvec.ptr, V(0), st));  // v_1 = r / beta
       int jmax = 0;
       for (int j = 0; j < m; ++j) {
         ++steps;
         if (mode == DD_PRECOND_CGNR) {
-          DD_TRY(cgnr(V(j), Zb(j), st));             // line 8: z_j = M_j^{-1} v_j
-          DD_TRY(apply_op(Zb(j), w.ptr, false, st));  // line 9
+          DD_TRY(cgnr(V(j), Zb(j), st));             // z_j = M_j^{-1} v_j
+          DD_TRY(apply_op(Zb(j), w.ptr, false, st));  // w = A z_j
         } else {
-          DD_TRY(apply(V(j), w.ptr, st));  // line 9 (z_j = v_j, or A^H v_j for the fixed preconditioner)
+          DD_TRY(apply(V(j), w.ptr, st));  // w = A z_j (z_j = v_j, or A^H v_j for the fixed preconditioner)
         }
         VecList vs;
         for (int i = 0; i <= j; ++i) vs.p[i] = V(i);
-        // lines 10-13: classical Gram-Schmidt (one pass, or two when
-        // gs_passes = 2); the norm of line 14 is fused into the last update
+        // classical Gram-Schmidt (one pass, or two when
+        // gs_passes = 2); the norm h_{j+1,j} is fused into the last update
         DD_TRY(dots(vs, j + 1, w.ptr, dots1, 0, st));
         if (gs_passes > 1) {
           DD_TRY(axpys(vs, j + 1, dots1, -1.0, w.ptr, st));
@@ -312,10 +312,10 @@ struct Inner {
         jmax = j + 1;
         if (!still) break;
         DD_CUDA(cudaMemcpyAsync(dcoef, hc, N * sizeof(double2), cudaMemcpyHostToDevice, st));
-        DD_TRY(scale(dcoef, w.ptr, V(j + 1), st));  // line 15
+        DD_TRY(scale(dcoef, w.ptr, V(j + 1), st));  // v_{j+1} = w / h_{j+1,j}
       }
       DD_CUDA(cudaStreamSynchronize(st));  // the last coefficient upload has landed before hc is reused
-      // line 18: back substitution R y = g; line 19: e += V y
+      // back substitution R y = g, then e += Z_m y
       std::vector<cd> y((size_t)N * m);
       for (int r = 0; r < N; ++r) {
         for (int i = k[r] - 1; i >= 0; --i) {
@@ -333,9 +333,9 @@ struct Inner {
       VecList vs;
       for (int i = 0; i < jmax; ++i) vs.p[i] = mode == DD_PRECOND_CGNR ? Zb(i) : V(i);
       if (!normal) {
-        DD_TRY(axpys(vs, jmax, dcoef, 1.0, e, st));  // line 19: e += Z_m y (Z_m = V_m without preconditioner)
+        DD_TRY(axpys(vs, jmax, dcoef, 1.0, e, st));  // e += Z_m y (Z_m = V_m without preconditioner)
       } else {
-        // fixed preconditioner: e += M^{-1} (V y) (line 19 of Algorithm 1)
+        // fixed preconditioner: e += M^{-1} (V y) (Algorithm 1)
         DD_CUDA(cudaMemsetAsync(ut.ptr, 0, vbytes, st));
         DD_TRY(axpys(vs, jmax, dcoef, 1.0, ut.ptr, st));
         DD_TRY(apply_op(ut.ptr, zt.ptr, true, st));
