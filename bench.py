@@ -652,17 +652,21 @@ def main():
         # FGMRES(8) with the flexible preconditioner M_j = 64 CG steps on the
         # normal equations of Dhat: plain restarted FGMRES stalls near 2.5e-3
         # on this lattice at m0 = -0.4
-        legs = [("mixed", PREC[args.solve_inner], 8), ("fp64", PREC["f64"], 8)]
+        # (name, inner precision, FGMRES restart, CG steps per M_j, inner tolerance): the
+        # mixed and FP64 legs run the same algorithm; the FP16-storage leg uses the
+        # settings that suit its less accurate inner operator (measured: 2.0 s
+        # with 32 CG steps and inner tolerance 1e-3 against 2.8 s with the
+        # FP32 settings)
+        legs = [("mixed", PREC[args.solve_inner], 8, 64, 1e-6), ("fp64", PREC["f64"], 8, 64, 1e-6)]
         if args.solve_inner != "f16":
-            # FP16 links and clover with FP32 vectors inside, same FP64 refinement
-            legs.insert(1, ("mixed_f16", PREC["f16"], 8))
-        for name, inner, restart in legs:
+            legs.insert(1, ("mixed_f16", PREC["f16"], 8, 32, 1e-3))
+        for name, inner, restart, cg, tol_in in legs:
             x = torch.zeros_like(b)
             log(f"solve {name}")
             barrier(tdist)
             w0 = time.time()
             status, st = op.solve(b, x, 1, tol=1e-10, inner_prec=inner, restart=restart, max_restarts=100,
-                                  max_outer=10, precond=dd.DD_PRECOND_CGNR, precond_iters=64)
+                                  max_outer=20, precond=dd.DD_PRECOND_CGNR, precond_iters=cg, inner_tol=tol_in)
             w1 = time.time()
             clocks.window(w0, w1)
             sols[name] = x
@@ -672,7 +676,8 @@ def main():
                            "inner_steps": st["inner_iterations"], "applies_inner": st["applies_inner"],
                            "applies_fp64": st["applies_fp64"],
                            "inner_prec": {1: "f64", 2: "f32", 4: "f16 links/clover, f32 vectors"}[inner],
-                           "method": "even-odd FGMRES(8), M_j = 64 CG steps on Dhat^H Dhat, FP64 refinement"}
+                           "method": f"even-odd FGMRES({restart}), M_j = {cg} CG steps on Dhat^H Dhat, "
+                                     f"inner tolerance {tol_in:g}, FP64 refinement"}
         d = (sols["mixed"] - sols["fp64"]).norm().item() / sols["fp64"].norm().item()
         solve["mixed_vs_fp64_solution_rel_diff"] = d
         solve["speedup_mixed_over_fp64"] = solve["fp64"]["seconds"] / solve["mixed"]["seconds"]
