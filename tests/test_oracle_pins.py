@@ -5,6 +5,8 @@ algebra, an independent dense assembly of Eq. 1.13, the free-field closed-form
 spectrum, gamma5-hermiticity, gauge covariance, a closed form of the clover
 term for an abelian field, and brute-force linear algebra.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -46,6 +48,24 @@ def test_gamma_T_projector_couples_spins_0_2_and_1_3():
     """Listing 4.2: (1 - gamma_T) pairs spin 0 with spin 2 and spin 1 with spin 3."""
     P = np.eye(4) - oracle.gamma(0)
     assert np.allclose(P, [[1, 0, -1, 0], [0, 1, 0, -1], [-1, 0, 1, 0], [0, -1, 0, 1]])
+
+
+def test_T_projection_matches_listing_4_2_fixture():
+    """The oracle's (1 - gamma_T) acting on the 12 components of a site
+    reproduces the index pattern of the projection in Listing 4.2 (fixture
+    tests/golden/listing_4_2_T_projection.txt): output component c of the
+    upper two spins reads components c and c + 6 only, the second with a
+    coefficient of unit modulus."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "listing_4_2_T_projection.txt")
+    rows = [list(map(int, ln.split())) for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 6
+    P12 = np.kron(np.eye(4) - oracle.gamma(0), np.eye(3))  # component = 3 * spin + colour
+    for out, first, second, spin in rows:
+        nz = set(np.flatnonzero(np.abs(P12[out]) > 1e-12))
+        assert nz == {first, second}
+        assert np.isclose(P12[out, first], 1.0)
+        assert np.isclose(abs(P12[out, second]), 1.0)
+        assert second // 3 == spin + 2 and out // 3 == spin
 
 
 # ----------------------------------------------------------------- generator
@@ -424,3 +444,43 @@ def test_link_force_finite_differences(with_clover):
         fd = (_L(Up, phi, psi, dims, A_fixed) - _L(Um, phi, psi, dims, A_fixed)) / (2 * h)
         val = G[x, mu, a, b_].real if comp == 0 else G[x, mu, a, b_].imag
         assert abs(fd - val) < 1e-7 * max(1, abs(val))
+
+
+def _table_5_1():
+    path = os.path.join(os.path.dirname(__file__), "golden", "table_5_1_configurations.txt")
+    rows = {}
+    for ln in open(path):
+        if ln.strip() and not ln.startswith("#"):
+            f = ln.split()
+            rows[f[0]] = (tuple(int(v) for v in f[1:5]), float(f[5]), float(f[6]), float(f[7]))
+    return rows
+
+
+def test_oracle_solves_the_tiny_configuration_of_table_5_1():
+    """The thesis' tiny configuration (Table 5.1: 8^4, m0 = -0.1, c_sw = 1.0)
+    with its tolerance (Section 5.3: 1e-10), on a synthetic gauge field (the
+    thesis' configuration is not available): the oracle's FGMRES (Algorithm 2,
+    M = I, restart 30) reaches the tolerance on the true residual."""
+    dims, m0, csw, tol = _table_5_1()["tiny"]
+    assert (dims, m0, csw, tol) == ((8, 8, 8, 8), -0.1, 1.0, 1e-10)
+    U = synthetic.gauge(dims)
+    A = oracle.clover(U, dims, m0, csw)
+    b = synthetic.spinor(dims, nrhs=1)[0].reshape(-1)
+    x, st = oracle.fgmres(lambda v: oracle.apply_D(U, A, v.reshape(-1, 12), dims).reshape(-1), b, m=30, tol=tol,
+                   max_restarts=200)
+    r = b - oracle.apply_D(U, A, x.reshape(-1, 12), dims).reshape(-1)
+    assert np.linalg.norm(r) / np.linalg.norm(b) < tol
+
+
+def test_c_sw_and_tolerance_defaults_follow_table_5_1():
+    """c_sw = 1.0 in every configuration of Table 5.1 and the 1e-10 tolerance
+    of Section 5.3 are the defaults of the benchmark and of dd_solve."""
+    import ctypes
+    rows = _table_5_1()
+    assert {r[2] for r in rows.values()} == {1.0} and {r[3] for r in rows.values()} == {1e-10}
+    import bench
+    assert bench.CSW == 1.0
+    import paper_2407_00041_gb300 as dd
+    p = dd.binding.SolveParams()
+    dd.lib.dd_solve_params_default(ctypes.byref(p))
+    assert p.tol == 1e-10
