@@ -38,7 +38,7 @@ int stage_in(DevBuf& buf, const void* src, size_t bytes, int layout, const doubl
   return DD_OK;
 }
 
-// D or D^H of a full field in canonical host layout, pipelined over C <= 16
+// D or D^H of a full field in canonical host layout, pipelined over C <= 24
 // chunks of time slices: the host-to-device copy of chunk c + 1 (stream
 // s_in), the pack / stencil / unpack of chunk c (the caller's stream) and the
 // device-to-host copy of chunk c - 1 (stream s_out) overlap.  The stencil of
@@ -48,7 +48,12 @@ int apply_host_pipelined(dd_clover* op, int prec, bool dagger, const void* hin, 
                          cudaStream_t st) {
   const dd_lattice* lat = op->lat;
   const int nT = lat->dims[0];
-  const int C = nT < 16 ? nT : 16;
+  static const int max_chunks = [] {
+    const char* e = getenv("DD_HOST_CHUNKS");  // tuning override
+    const int v = e ? atoi(e) : 24;
+    return v < 2 ? 2 : v;
+  }();
+  const int C = nT < max_chunks ? nT : max_chunks;
   const int64_t slice = (int64_t)lat->dims[1] * lat->dims[2] * lat->dims[3];
   const size_t row = (size_t)lat->V * 12 * 16;  // one RHS of the canonical array
   const size_t cb = row * nrhs;
