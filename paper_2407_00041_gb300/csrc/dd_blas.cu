@@ -77,13 +77,26 @@ __global__ void __launch_bounds__(256) k_multidot(VecList vs, int J, const void*
 #pragma unroll
   for (int j = 0; j < MAXJ; ++j) are[j] = aim[j] = 0.0, fre[j] = fim[j] = R(0);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  int run = 0;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < L; e += stride) {
-    const T we = w[e];
+  // four elements per pass (independent loads in flight); a vector equal to w
+  // (a norm) is not read twice
+  bool self[MAXJ];
 #pragma unroll
-    for (int j = 0; j < MAXJ; ++j)
-      if (j < J) acc_dot(reinterpret_cast<const T*>(vs.p[j])[e], we, fre[j], fim[j]);
-    if (PV == P32 && ++run == 16) {
+  for (int j = 0; j < MAXJ; ++j) self[j] = j < J && vs.p[j] == wp;
+  int run = 0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < L; e += 4 * stride) {
+    T we[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (e + u * stride < L) we[u] = w[e + u * stride];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (e + u * stride >= L) break;
+#pragma unroll
+      for (int j = 0; j < MAXJ; ++j)
+        if (j < J) acc_dot(self[j] ? we[u] : reinterpret_cast<const T*>(vs.p[j])[e + u * stride], we[u], fre[j], fim[j]);
+    }
+    run += 4;
+    if (PV == P32 && run >= 16) {
       run = 0;
 #pragma unroll
       for (int j = 0; j < MAXJ; ++j) are[j] += (double)fre[j], aim[j] += (double)fim[j], fre[j] = fim[j] = R(0);
