@@ -65,7 +65,7 @@ constexpr int MAXJ = 8;
 constexpr int kMaxCoef = 1024;
 
 // partials[block][j][r] = sum over this block's groups of <V_j, w> for RHS r.
-template <int PV>
+template <int PV, int MAXJ>
 __global__ void __launch_bounds__(256) k_multidot(VecList vs, int J, const void* __restrict__ wp, int64_t L, int N,
                                                   double2* partials) {
   using T = typename G<PV>::group;
@@ -106,7 +106,10 @@ __global__ void __launch_bounds__(256) k_multidot(VecList vs, int J, const void*
   for (int j = 0; j < MAXJ; ++j) are[j] += (double)fre[j], aim[j] += (double)fim[j];
   const int t = threadIdx.x;
   const int per = blockDim.x / N;  // threads per RHS in this block
-  for (int j = 0; j < J; ++j) {
+  // unrolled over MAXJ so that are[] / aim[] stay in registers
+#pragma unroll
+  for (int j = 0; j < MAXJ; ++j) {
+    if (j >= J) break;
     sre[t] = are[j];
     sim[t] = aim[j];
     __syncthreads();
@@ -330,7 +333,10 @@ int blas_multidot(const VecList& vs, int J, const void* w, int64_t L, int N, dou
     const int Jc = J - j0 < MAXJ ? J - j0 : MAXJ;
     VecList sub;
     for (int j = 0; j < Jc; ++j) sub.p[j] = vs.p[j0 + j];
-    k_multidot<PV><<<grid, block, 0, st>>>(sub, Jc, w, L, N, partials);
+    if (Jc == 1)  // one vector (a norm or a single product): fewer registers
+      k_multidot<PV, 1><<<grid, block, 0, st>>>(sub, Jc, w, L, N, partials);
+    else
+      k_multidot<PV, MAXJ><<<grid, block, 0, st>>>(sub, Jc, w, L, N, partials);
     const int JN = Jc * N;
     k_reduce_partials<<<JN, 256, 0, st>>>(partials, grid, JN, dots_dev + (int64_t)j0 * N, add);
   }
