@@ -64,6 +64,23 @@ __device__ __forceinline__ void caxpy(float cr, float ci, float4 v, float4& w) {
 constexpr int MAXJ = 8;
 constexpr int kMaxCoef = 1024;
 
+// Sum of v over the threads of the block with the same t % N, delivered to
+// threads t < N; N divides 32 and the block is a multiple of 32 threads.  An
+// xor-shuffle tree inside each warp (lanes with equal lane % N), then the
+// warps' sums in a fixed order through `sm` (at least blockDim / 32 * N
+// doubles): deterministic.
+__device__ __forceinline__ double block_sum_by_rhs(double v, int N, double* sm) {
+  for (int off = 16; off >= N; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (lane < N) sm[warp * N + lane] = v;
+  __syncthreads();
+  double tot = 0.0;
+  if ((int)threadIdx.x < N)
+    for (int w = 0; w < nw; ++w) tot += sm[w * N + threadIdx.x];
+  __syncthreads();
+  return tot;
+}
+
 // partials[block][j][r] = sum over this block's groups of <V_j, w> for RHS r.
 template <int PV, int MAXJ>
 __global__ void __launch_bounds__(256) k_multidot(VecList vs, int J, const void* __restrict__ wp, int64_t L, int N,
@@ -110,15 +127,21 @@ __global__ void __launch_bounds__(256) k_multidot(VecList vs, int J, const void*
 #pragma unroll
   for (int j = 0; j < MAXJ; ++j) {
     if (j >= J) break;
-    sre[t] = are[j];
-    sim[t] = aim[j];
-    __syncthreads();
-    if (t < N) {
-      double re = 0.0, im = 0.0;
-      for (int k = 0; k < per; ++k) re += sre[t + k * N], im += sim[t + k * N];
-      partials[((int64_t)blockIdx.x * J + j) * N + t] = make_double2(re, im);
+    if (32 % N == 0) {  // warp shuffles
+      const double re = block_sum_by_rhs(are[j], N, sre);
+      const double im = block_sum_by_rhs(aim[j], N, sim);
+      if (t < N) partials[((int64_t)blockIdx.x * J + j) * N + t] = make_double2(re, im);
+    } else {
+      sre[t] = are[j];
+      sim[t] = aim[j];
+      __syncthreads();
+      if (t < N) {
+        double re = 0.0, im = 0.0;
+        for (int k = 0; k < per; ++k) re += sre[t + k * N], im += sim[t + k * N];
+        partials[((int64_t)blockIdx.x * J + j) * N + t] = make_double2(re, im);
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 
@@ -135,22 +158,14 @@ __global__ void __launch_bounds__(256) k_reduce_partials(const double2* __restri
     re += v.x;
     im += v.y;
   }
-  sre[threadIdx.x] = re;
-  sim[threadIdx.x] = im;
-  __syncthreads();
-  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-    if (threadIdx.x < h) {
-      sre[threadIdx.x] += sre[threadIdx.x + h];
-      sim[threadIdx.x] += sim[threadIdx.x + h];
-    }
-    __syncthreads();
-  }
+  re = block_sum_by_rhs(re, 1, sre);
+  im = block_sum_by_rhs(im, 1, sim);
   if (threadIdx.x == 0) {
     if (add) {
-      sre[0] += out[i].x;
-      sim[0] += out[i].y;
+      re += out[i].x;
+      im += out[i].y;
     }
-    out[i] = make_double2(sre[0], sim[0]);
+    out[i] = make_double2(re, im);
   }
 }
 
@@ -194,6 +209,11 @@ __global__ void __launch_bounds__(256) k_multiaxpy(VecList vs, int J, const doub
   }
   if (!partials) return;
   nrm += (double)fn;
+  if (32 % N == 0) {  // warp shuffles
+    const double acc = block_sum_by_rhs(nrm, N, sn);
+    if ((int)threadIdx.x < N) partials[(int64_t)blockIdx.x * N + threadIdx.x] = make_double2(acc, 0.0);
+    return;
+  }
   sn[threadIdx.x] = nrm;
   __syncthreads();
   if (threadIdx.x < N) {
