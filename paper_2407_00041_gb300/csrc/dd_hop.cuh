@@ -19,6 +19,7 @@
 
 #include <cstdlib>
 
+#include "dd_blas.h"
 #include "dd_ops.h"
 
 namespace dd {
@@ -260,9 +261,11 @@ __device__ __forceinline__ void block_apply(const void* M, int64_t s, int64_t Vh
   block_apply_g<PG, false, R>(M, s, Vh, x, out, true);
 }
 
-// The work of one thread: output slot `tid` in [0, npar * Vh * nrhs).
-template <int PG, int PIN, int POUT, bool DAG, int EPI>
-__device__ __forceinline__ void hop_thread(const HopArgs& a, int64_t tid) {
+// The work of one thread: output slot `tid` in [0, npar * Vh * nrhs).  With
+// NORM it returns |out|^2 of the stored FP32 result (summed in FP32 over the
+// 12 components), else 0.
+template <int PG, int PIN, int POUT, bool DAG, int EPI, bool NORM = false>
+__device__ __forceinline__ float hop_thread(const HopArgs& a, int64_t tid) {
   using R = typename Store<PG>::real;
   using E = typename Store<PG>::elem;
   int p, s, r;
@@ -354,6 +357,16 @@ __device__ __forceinline__ void hop_thread(const HopArgs& a, int64_t tid) {
     block_apply<PG, R>(M, s, Vh, y, res);
   }
   store_spinor<POUT, R, true>(a.out[p], a.gstride, i, res);
+  float n2 = 0.f;
+  if constexpr (NORM) {
+    static_assert(POUT == P32, "the fused norm reads the FP32 result");
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      n2 = __fmaf_rn((float)res[c].re, (float)res[c].re, n2);
+      n2 = __fmaf_rn((float)res[c].im, (float)res[c].im, n2);
+    }
+  }
+  return n2;
 }
 
 // RHS-blocked variant for several right-hand sides (three-row links only): one thread handles NB
@@ -473,6 +486,23 @@ __global__ void __launch_bounds__(128, HopMinBlocks<PG>::value) k_hop(const HopA
   hop_thread<PG, PIN, POUT, DAG, EPI>(a, tid);
 }
 
+// EPI_D stencil of one right-hand side that also reduces |out|^2 over the
+// block: warp shuffles, then the four warps' sums in order, one partial per
+// block (partials[blockIdx.x].x); threads past the end contribute zero.
+template <int PG, int PIN, int POUT, bool DAG>
+__global__ void __launch_bounds__(128, HopMinBlocks<PG>::value) k_hop_norm(const HopArgs a, double2* partials) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float n2 = 0.f;
+  if (tid < launch_sites(a.g, a.npar)) n2 = hop_thread<PG, PIN, POUT, DAG, EPI_D, true>(a, tid);
+  double v = (double)n2;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  __shared__ double sw[4];
+  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) partials[blockIdx.x] = make_double2(((sw[0] + sw[1]) + sw[2]) + sw[3], 0.0);
+}
+
 template <int PG, int PIN, int POUT>
 __global__ void __launch_bounds__(128) k_block(const BlockArgs a) {
   using R = typename Store<PG>::real;
@@ -586,6 +616,31 @@ cudaError_t launch_hop(const HopArgs& args, bool dagger, int epi, cudaStream_t s
   return cudaGetLastError();
 }
 
+// One right-hand side, EPI_D, out written in FP32: the stencil plus
+// norm_out[0] = (|out|^2, 0), reduced in a fixed order (deterministic).
+// `partials` holds at least hop_norm_blocks(launch sites) complex doubles.
+template <int PG, int PIN, int POUT>
+cudaError_t launch_hop_norm(const HopArgs& args, bool dagger, double2* partials, int64_t npartials,
+                            double2* norm_out, cudaStream_t st) {
+  if (args.nrhs != 1) return cudaErrorInvalidValue;
+  HopArgs a = args;
+  prepare_divs(a.g);
+  a.fblk = make_fastdiv(1u);
+  const int64_t n = launch_sites(a.g, a.npar);
+  if (n == 0 || n >= (int64_t)1 << 31) return cudaErrorInvalidValue;
+  const int threads = 128;
+  const int64_t blocks = hop_norm_blocks(n);
+  if (blocks > npartials || blocks > INT32_MAX) return cudaErrorInvalidValue;
+  if (dagger)
+    k_hop_norm<PG, PIN, POUT, true><<<(unsigned)blocks, threads, 0, st>>>(a, partials);
+  else
+    k_hop_norm<PG, PIN, POUT, false><<<(unsigned)blocks, threads, 0, st>>>(a, partials);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return blas_reduce_partials(partials, (int)blocks, 1, norm_out, 0, st) == 0 ? cudaSuccess
+                                                                                   : cudaErrorLaunchFailure;
+}
+
 template <int PG, int PIN, int POUT>
 cudaError_t launch_block(const BlockArgs& a, cudaStream_t st) {
   const int64_t n = a.Vh * a.nrhs * a.npar;
@@ -598,5 +653,7 @@ cudaError_t launch_block(const BlockArgs& a, cudaStream_t st) {
 #define DD_INSTANTIATE_HOP(PG, PIN, POUT)                                                                  \
   template cudaError_t launch_hop<PG, PIN, POUT>(const HopArgs&, bool, int, cudaStream_t);                \
   template cudaError_t launch_block<PG, PIN, POUT>(const BlockArgs&, cudaStream_t);
+#define DD_INSTANTIATE_HOP_NORM(PG, PIN, POUT) \
+  template cudaError_t launch_hop_norm<PG, PIN, POUT>(const HopArgs&, bool, double2*, int64_t, double2*, cudaStream_t);
 
 }  // namespace dd

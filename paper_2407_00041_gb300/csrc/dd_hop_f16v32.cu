@@ -2,4 +2,5 @@
 #include "dd_hop.cuh"
 namespace dd {
 DD_INSTANTIATE_HOP(P16, P32, P32)
+DD_INSTANTIATE_HOP_NORM(P16, P32, P32)
 }  // namespace dd

@@ -127,6 +127,13 @@ int op_SC(const dd_clover* op, int pg, int pv, const Field& in, const Field& out
 // out_o = Dhat in_o (odd half fields); tmp_e: even half-field workspace
 int op_Dhat(const dd_clover* op, int pg, int pv, bool dagger, const Field& in, const Field& out, const Field& tmp,
             cudaStream_t st);
+// Whether op_Dhat_norm supports (pg, pv, nrhs): one RHS, FP32 vectors,
+// FP32 or FP16 links and blocks.
+bool dhat_norm_fused(int pg, int pv, int nrhs);
+// op_Dhat that also writes norm_out[0] = (|out|^2, 0) from the second
+// stencil launch (partials: hop_norm_blocks(Vh) complex doubles of scratch).
+int op_Dhat_norm(const dd_clover* op, int pg, int pv, bool dagger, const Field& in, const Field& out, const Field& tmp,
+                 double2* norm_out, double2* partials, int64_t npartials, cudaStream_t st);
 // r = b - D x (full fields)
 int op_residual(const dd_clover* op, int pg, int pv, const Field& b, const Field& x, const Field& r,
                 cudaStream_t st);

@@ -245,26 +245,48 @@ int op_SC(const dd_clover* op, int pg, int pv, const Field& in, const Field& out
 
 // Dhat in_o = A_oo in_o - (1/4) H_oe A_ee^{-1} H_eo in_o (D_eo = -1/2 H_eo):
 //   tmp_e = A_ee^{-1} (1/2 H_eo in_o);  out_o = A_oo in_o - 1/2 H_oe tmp_e
-int op_Dhat(const dd_clover* op, int pg, int pv, bool dagger, const Field& in, const Field& out, const Field& tmp,
-            cudaStream_t st) {
-  DD_TRY(check_prec(op, pg));
-  const int pi = prec_index(pg);
-  HopArgs a = base_args(op, pg, in.nrhs);
+// The two launches of Dhat: a) tmp_e = A_ee^{-1} (1/2 H_eo in_o);
+// b) out_o = A_oo in_o - 1/2 H_oe tmp_e.
+static void dhat_args(const dd_clover* op, int pg, const Field& in, const Field& out, const Field& tmp, HopArgs& a,
+                      HopArgs& b) {
+  a = base_args(op, pg, in.nrhs);
   a.npar = 1;
   a.p0 = 0;
   a.in[1] = in.h[1];
   a.out[0] = tmp.h[0];
-  a.M[0] = op->Ainv(pi);
+  a.M[0] = op->Ainv(prec_index(pg));
   a.beta = 0.5;
-  DD_TRY(run_hop(pg, pv, a, dagger, EPI_AINV, st));
-  HopArgs b = base_args(op, pg, in.nrhs);
+  b = base_args(op, pg, in.nrhs);
   b.npar = 1;
   b.p0 = 1;
   b.in[0] = tmp.h[0];
   b.y[1] = in.h[1];
   b.out[1] = out.h[1];
   b.beta = -0.5;
+}
+
+int op_Dhat(const dd_clover* op, int pg, int pv, bool dagger, const Field& in, const Field& out, const Field& tmp,
+            cudaStream_t st) {
+  DD_TRY(check_prec(op, pg));
+  HopArgs a, b;
+  dhat_args(op, pg, in, out, tmp, a, b);
+  DD_TRY(run_hop(pg, pv, a, dagger, EPI_AINV, st));
   return run_hop(pg, pv, b, dagger, EPI_D, st);
+}
+
+bool dhat_norm_fused(int pg, int pv, int nrhs) { return nrhs == 1 && pv == P32 && (pg == P32 || pg == P16); }
+
+int op_Dhat_norm(const dd_clover* op, int pg, int pv, bool dagger, const Field& in, const Field& out, const Field& tmp,
+                 double2* norm_out, double2* partials, int64_t npartials, cudaStream_t st) {
+  if (!dhat_norm_fused(pg, pv, in.nrhs)) return fail(DD_ERR_UNSUPPORTED, "fused norm: one RHS, FP32 vectors");
+  DD_TRY(check_prec(op, pg));
+  HopArgs a, b;
+  dhat_args(op, pg, in, out, tmp, a, b);
+  DD_TRY(run_hop(pg, pv, a, dagger, EPI_AINV, st));
+  const cudaError_t e = pg == P32 ? launch_hop_norm<P32, P32, P32>(b, dagger, partials, npartials, norm_out, st)
+                                  : launch_hop_norm<P16, P32, P32>(b, dagger, partials, npartials, norm_out, st);
+  if (e != cudaSuccess) return cuda_fail(e, "stencil launch with norm");
+  return DD_OK;
 }
 
 int op_residual(const dd_clover* op, int pg, int pv, const Field& b, const Field& x, const Field& r,

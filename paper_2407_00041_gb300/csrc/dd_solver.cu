@@ -30,10 +30,12 @@
 #include <cmath>
 #include <complex>
 #include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 #include "dd_blas.h"
 #include "dd_internal.h"
+#include "dd_ops.h"
 
 namespace dd {
 
@@ -69,6 +71,11 @@ struct Inner {
   int verbose = 0;
   int gs_passes = 1;    // classical Gram-Schmidt passes per Arnoldi step
   DevBuf basis, w, rvec, tmp, red, partials, coef, zt, ut, zbasis, cr, cz, cp, cgs;
+  // CG norms formed by the second stencil launch of Dhat (one RHS, FP32
+  // vectors; DD_FUSED_NORM=0 turns it off): per-block partial sums
+  bool fuse_norm = false;
+  DevBuf npart;
+  int64_t npart_len = 0;
   Pinned hred, hcoef;
   // counters
   int applies = 0, steps = 0, cycles = 0;
@@ -98,6 +105,12 @@ struct Inner {
       DD_TRY(cz.ensure(vbytes));
       DD_TRY(cp.ensure(vbytes));
       DD_TRY(cgs.ensure((size_t)3 * N * sizeof(double2)));
+      const char* fe = getenv("DD_FUSED_NORM");
+      fuse_norm = eo && dhat_norm_fused(pg, pv, N) && !(fe && atoi(fe) == 0);
+      if (fuse_norm) {
+        npart_len = hop_norm_blocks(lat->Vh);
+        DD_TRY(npart.ensure((size_t)npart_len * sizeof(double2)));
+      }
     }
     if (eo) DD_TRY(tmp.ensure(field_bytes(lat, pv, 2, N)));
     const size_t nred = (size_t)(2 * (m + 1) + 1) * N;
@@ -120,6 +133,20 @@ struct Inner {
     if (eo) return op_Dhat(op, pg, pv, dagger, fv(i), fv(out), field_view(op->lat, pv, 2, tmp.ptr, N), st);
     return op_D(op, pg, pv, dagger, fv(i), fv(out), st);
   }
+  // out = A in and nrm[0] = (|out|^2, 0): fused into the stencil where
+  // supported, else a separate reduction
+  int apply_op_norm(const void* in, void* out, bool dagger, double2* nrm, cudaStream_t st) {
+    if (!fuse_norm) {
+      DD_TRY(apply_op(in, out, dagger, st));
+      VecList one;
+      one.p[0] = out;
+      return dots(one, 1, out, nrm, 0, st);
+    }
+    ++applies;
+    void* i = const_cast<void*>(in);
+    return op_Dhat_norm(op, pg, pv, dagger, fv(i), fv(out), field_view(op->lat, pv, 2, tmp.ptr, N), nrm,
+                        (double2*)npart.ptr, npart_len, st);
+  }
   // w = A M^{-1} v (Algorithm 2)
   int apply(const void* v, void* out, cudaStream_t st) {
     if (!normal) return apply_op(v, out, false, st);
@@ -133,25 +160,18 @@ struct Inner {
     double2* g1 = g0 + N;
     double2* nw = g0 + 2 * N;
     double2* g[2] = {g0, g1};
-    VecList one;
     DD_CUDA(cudaMemsetAsync(z, 0, vbytes, st));
     DD_CUDA(cudaMemcpyAsync(cr.ptr, v, vbytes, cudaMemcpyDeviceToDevice, st));
-    DD_TRY(apply_op(cr.ptr, cz.ptr, true, st));  // A^H r
+    DD_TRY(apply_op_norm(cr.ptr, cz.ptr, true, g[0], st));  // A^H r and its norm
     DD_CUDA(cudaMemcpyAsync(cp.ptr, cz.ptr, vbytes, cudaMemcpyDeviceToDevice, st));
-    one.p[0] = cz.ptr;
-    DD_TRY(dots(one, 1, cz.ptr, g[0], 0, st));
     for (int i = 0; i < cg_iters; ++i) {
-      DD_TRY(apply_op(cp.ptr, w.ptr, false, st));  // w = A p
-      one.p[0] = w.ptr;
-      DD_TRY(dots(one, 1, w.ptr, nw, 0, st));
+      DD_TRY(apply_op_norm(cp.ptr, w.ptr, false, nw, st));  // w = A p, |w|^2
       if (pv == P64)
         DD_TRY(blas_cg_xr<P64>(z, cr.ptr, cp.ptr, w.ptr, g[i & 1], nw, L, N, st));
       else
         DD_TRY(blas_cg_xr<P32>(z, cr.ptr, cp.ptr, w.ptr, g[i & 1], nw, L, N, st));
       if (i + 1 == cg_iters) break;  // the last direction update is not needed
-      DD_TRY(apply_op(cr.ptr, cz.ptr, true, st));  // z' = A^H r
-      one.p[0] = cz.ptr;
-      DD_TRY(dots(one, 1, cz.ptr, g[(i + 1) & 1], 0, st));
+      DD_TRY(apply_op_norm(cr.ptr, cz.ptr, true, g[(i + 1) & 1], st));  // z' = A^H r, |z'|^2
       if (pv == P64)
         DD_TRY(blas_cg_p<P64>(cp.ptr, cz.ptr, g[(i + 1) & 1], g[i & 1], L, N, st));
       else
