@@ -148,24 +148,26 @@ __global__ void __launch_bounds__(256) k_multidot(VecList vs, int J, const void*
 // out[j][r] (+)= sum over blocks of partials[block][j][r]: one CTA per
 // output, a strided pass over the blocks and a fixed-shape tree, so the
 // result does not depend on scheduling.
-// out[i] (+)= sum over the blocks' partials of entry i; one CTA per entry,
-// eight independent loads in flight per thread (up to ~10^5 partials when
-// the stencil forms a norm), fixed summation order.
+// out[y * JN + i] (+)= sum of entry i over the partials of chunk y (blocks
+// y * chunk .. (y + 1) * chunk - 1); grid (JN, chunks).  Eight independent
+// loads in flight per thread on long chunks; fixed summation order.
 __global__ void __launch_bounds__(1024) k_reduce_partials(const double2* __restrict__ partials, int nblocks, int JN,
-                                                          double2* out, int add) {
+                                                          double2* out, int add, int chunk) {
   __shared__ double sre[32], sim[32];
   const int i = blockIdx.x;
   const int nt = blockDim.x;
+  const int b0 = blockIdx.y * chunk;
+  const int b1 = min(nblocks, b0 + chunk);
   double re = 0.0, im = 0.0;
-  int b = threadIdx.x;
-  for (; b + 7 * nt < nblocks; b += 8 * nt) {
+  int b = b0 + threadIdx.x;
+  for (; b + 7 * nt < b1; b += 8 * nt) {
     double2 v[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) v[u] = partials[(int64_t)(b + u * nt) * JN + i];
 #pragma unroll
     for (int u = 0; u < 8; ++u) re += v[u].x, im += v[u].y;
   }
-  for (; b < nblocks; b += nt) {
+  for (; b < b1; b += nt) {
     const double2 v = partials[(int64_t)b * JN + i];
     re += v.x;
     im += v.y;
@@ -173,11 +175,12 @@ __global__ void __launch_bounds__(1024) k_reduce_partials(const double2* __restr
   re = block_sum_by_rhs(re, 1, sre);
   im = block_sum_by_rhs(im, 1, sim);
   if (threadIdx.x == 0) {
+    double2* o = out + (int64_t)blockIdx.y * JN + i;
     if (add) {
-      re += out[i].x;
-      im += out[i].y;
+      re += o->x;
+      im += o->y;
     }
-    out[i] = make_double2(re, im);
+    *o = make_double2(re, im);
   }
 }
 
@@ -342,9 +345,9 @@ __global__ void __launch_bounds__(256) k_cg_p(void* pp, const void* zp, const do
   }
 }
 
-// threads of the partial reduce: about eight partials per thread, 32..1024
+// threads of the partial reduce: about four partials per thread, 32..1024
 int reduce_threads(int nblocks) {
-  const int t = ((nblocks + 7) / 8 + 31) / 32 * 32;
+  const int t = ((nblocks + 3) / 4 + 31) / 32 * 32;
   return t < 32 ? 32 : t > 1024 ? 1024 : t;
 }
 
@@ -376,7 +379,8 @@ int blas_multidot(const VecList& vs, int J, const void* w, int64_t L, int N, dou
     else
       k_multidot<PV, MAXJ><<<grid, block, 0, st>>>(sub, Jc, w, L, N, partials);
     const int JN = Jc * N;
-    k_reduce_partials<<<JN, reduce_threads(grid), 0, st>>>(partials, grid, JN, dots_dev + (int64_t)j0 * N, add);
+    k_reduce_partials<<<JN, reduce_threads(grid), 0, st>>>(partials, grid, JN, dots_dev + (int64_t)j0 * N, add,
+                                                           grid);
   }
   DD_CUDA(cudaGetLastError());
   return DD_OK;
@@ -398,14 +402,22 @@ int blas_multiaxpy(const VecList& vs, int J, const double2* c_dev, double csign,
                                             last && norm_out ? partials : nullptr);
     if (J == 0) break;
   }
-  if (norm_out) k_reduce_partials<<<N, reduce_threads(grid), 0, st>>>(partials, grid, N, norm_out, 0);
+  if (norm_out) k_reduce_partials<<<N, reduce_threads(grid), 0, st>>>(partials, grid, N, norm_out, 0, grid);
   DD_CUDA(cudaGetLastError());
   return DD_OK;
 }
 
-int blas_reduce_partials(const double2* partials, int nblocks, int JN, double2* out, int add, cudaStream_t st) {
+int blas_reduce_partials(const double2* partials, int nblocks, int JN, double2* out, int add, cudaStream_t st,
+                         double2* scratch) {
   if (nblocks < 1 || JN < 1) return fail(DD_ERR_ARG, "empty reduction");
-  k_reduce_partials<<<JN, reduce_threads(nblocks), 0, st>>>(partials, nblocks, JN, out, add);
+  if (blas_reduce_scratch(nblocks, JN) > 0 && scratch) {
+    // FP64 adds are slow on one SM: spread the first stage over 64 CTAs
+    const int G = 64, chunk = (nblocks + G - 1) / G;
+    k_reduce_partials<<<dim3(JN, G), reduce_threads(chunk), 0, st>>>(partials, nblocks, JN, scratch, 0, chunk);
+    k_reduce_partials<<<JN, reduce_threads(G), 0, st>>>(scratch, G, JN, out, add, G);
+  } else {
+    k_reduce_partials<<<JN, reduce_threads(nblocks), 0, st>>>(partials, nblocks, JN, out, add, nblocks);
+  }
   DD_CUDA(cudaGetLastError());
   return DD_OK;
 }

@@ -32,8 +32,12 @@ int blas_cg_xr(void* x, void* r, const void* p, const void* w, const double2* g,
 template <int PV>
 int blas_cg_p(void* p, const void* z, const double2* gn, const double2* go, int64_t L, int N, cudaStream_t st);
 // out[i] (+)= sum over b < nblocks of partials[b * JN + i], i < JN, summed in
-// a fixed order (warp shuffles, then the warps in turn)
-int blas_reduce_partials(const double2* partials, int nblocks, int JN, double2* out, int add, cudaStream_t st);
+// a fixed order (warp shuffles, then the warps in turn).  From 4096 partials
+// on, the sum runs in two stages (64 CTAs over contiguous chunks, then one)
+// through `scratch`, blas_reduce_scratch(nblocks, JN) complex doubles.
+int blas_reduce_partials(const double2* partials, int nblocks, int JN, double2* out, int add, cudaStream_t st,
+                         double2* scratch = nullptr);
+inline int blas_reduce_scratch(int nblocks, int JN) { return nblocks >= 4096 ? 64 * JN : 0; }
 // FP64 native field -> FP32 native field (nhalf half fields, VN = Vh * N)
 int blas_demote(const void* in64, void* out32, int64_t nhalf, int64_t VN, cudaStream_t st);
 // FP64 native field += FP32 native field

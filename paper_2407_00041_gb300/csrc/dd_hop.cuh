@@ -487,20 +487,21 @@ __global__ void __launch_bounds__(128, HopMinBlocks<PG>::value) k_hop(const HopA
 }
 
 // EPI_D stencil of one right-hand side that also reduces |out|^2 over the
-// block: warp shuffles, then the four warps' sums in order, one partial per
-// block (partials[blockIdx.x].x); threads past the end contribute zero.
+// block: FP32 warp shuffles (32 sites, as the dot kernel sums short runs in
+// FP32), then the four warps' sums in FP64 in order, one partial per block
+// (partials[blockIdx.x].x); threads past the end contribute zero.
 template <int PG, int PIN, int POUT, bool DAG>
 __global__ void __launch_bounds__(128, HopMinBlocks<PG>::value) k_hop_norm(const HopArgs a, double2* partials) {
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  float n2 = 0.f;
-  if (tid < launch_sites(a.g, a.npar)) n2 = hop_thread<PG, PIN, POUT, DAG, EPI_D, true>(a, tid);
-  double v = (double)n2;
+  float v = 0.f;
+  if (tid < launch_sites(a.g, a.npar)) v = hop_thread<PG, PIN, POUT, DAG, EPI_D, true>(a, tid);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-  __shared__ double sw[4];
+  __shared__ float sw[4];
   if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = v;
   __syncthreads();
-  if (threadIdx.x == 0) partials[blockIdx.x] = make_double2(((sw[0] + sw[1]) + sw[2]) + sw[3], 0.0);
+  if (threadIdx.x == 0)
+    partials[blockIdx.x] = make_double2((((double)sw[0] + (double)sw[1]) + (double)sw[2]) + (double)sw[3], 0.0);
 }
 
 template <int PG, int PIN, int POUT>
@@ -618,7 +619,8 @@ cudaError_t launch_hop(const HopArgs& args, bool dagger, int epi, cudaStream_t s
 
 // One right-hand side, EPI_D, out written in FP32: the stencil plus
 // norm_out[0] = (|out|^2, 0), reduced in a fixed order (deterministic).
-// `partials` holds at least hop_norm_blocks(launch sites) complex doubles.
+// `partials` holds at least hop_norm_blocks(launch sites) complex doubles
+// plus the reduction's own scratch (blas_reduce_scratch(blocks, 1)).
 template <int PG, int PIN, int POUT>
 cudaError_t launch_hop_norm(const HopArgs& args, bool dagger, double2* partials, int64_t npartials,
                             double2* norm_out, cudaStream_t st) {
@@ -630,14 +632,14 @@ cudaError_t launch_hop_norm(const HopArgs& args, bool dagger, double2* partials,
   if (n == 0 || n >= (int64_t)1 << 31) return cudaErrorInvalidValue;
   const int threads = 128;
   const int64_t blocks = hop_norm_blocks(n);
-  if (blocks > npartials || blocks > INT32_MAX) return cudaErrorInvalidValue;
+  if (blocks > INT32_MAX || blocks + blas_reduce_scratch((int)blocks, 1) > npartials) return cudaErrorInvalidValue;
   if (dagger)
     k_hop_norm<PG, PIN, POUT, true><<<(unsigned)blocks, threads, 0, st>>>(a, partials);
   else
     k_hop_norm<PG, PIN, POUT, false><<<(unsigned)blocks, threads, 0, st>>>(a, partials);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return blas_reduce_partials(partials, (int)blocks, 1, norm_out, 0, st) == 0 ? cudaSuccess
+  return blas_reduce_partials(partials, (int)blocks, 1, norm_out, 0, st, partials + blocks) == 0 ? cudaSuccess
                                                                                    : cudaErrorLaunchFailure;
 }
 

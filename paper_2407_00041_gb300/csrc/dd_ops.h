@@ -54,7 +54,7 @@ int64_t stencil_bytes_per_site(int pg, int nrhs);
 template <int PG, int PIN, int POUT>
 cudaError_t launch_block(const BlockArgs& a, cudaStream_t st);
 // Blocks (of 128 threads) of the fused-norm stencil over `sites` sites: the
-// partial sums it needs.
+// partial sums it writes (its scratch: these plus blas_reduce_scratch).
 inline int64_t hop_norm_blocks(int64_t sites) { return (sites + 127) / 128; }
 // EPI_D stencil of one right-hand side with an FP32 output that also writes
 // norm_out[0] = (|out|^2, 0) (instantiated for (P32, P32, P32) and

@@ -108,7 +108,8 @@ struct Inner {
       const char* fe = getenv("DD_FUSED_NORM");
       fuse_norm = eo && dhat_norm_fused(pg, pv, N) && !(fe && atoi(fe) == 0);
       if (fuse_norm) {
-        npart_len = hop_norm_blocks(lat->Vh);
+        const int64_t nb = hop_norm_blocks(lat->Vh);
+        npart_len = nb + blas_reduce_scratch((int)std::min<int64_t>(nb, INT32_MAX), 1);
         DD_TRY(npart.ensure((size_t)npart_len * sizeof(double2)));
       }
     }
