@@ -378,7 +378,7 @@ def extra_measurements(dd, torch, stream, op48, psi48, V48, tdist, clocks, alu_p
         link, clov, spin = {"f32": (96 * LINK_ROWS_F32[0], 288, 96), "f16": (144, 144, 52)}[name]
         bytes_ = 2 * link * V48 + clov * V48 + 5 * spin * (V48 // 2)
         out[f"dhat_{name}"] = {"ms": t * 1e3, "gbs_formula": bytes_ / t / 1e9}
-    # lattices of config 3
+    # the batch of uneven lattices 8^4 x 1, 16^4 x 5, 24^4 x 17, 32^4 x 32 RHS
     shapes = [(8, 8, 8, 8), (16, 16, 16, 16), (24, 24, 24, 24), (32, 32, 32, 32)]
     nrhs = [1, 5, 17, 32]
     keep, ops, ins, outs = [], [], [], []
@@ -429,7 +429,7 @@ def extra_measurements(dd, torch, stream, op48, psi48, V48, tdist, clocks, alu_p
     t_sep = _time_fn(separate, 20)
     units = sum(int(np.prod(d)) * n for d, n in zip(shapes, nrhs))
     bytes_ = sum(int(np.prod(d)) * bytes_per_site("f32", n) for d, n in zip(shapes, nrhs))
-    out["batch_config3_f32"] = {"ms_one_graph_launch": t_batch * 1e3, "ms_four_launches": t_sep * 1e3,
+    out["batch_8c4_16c4_24c4_32c4_f32"] = {"ms_one_graph_launch": t_batch * 1e3, "ms_four_launches": t_sep * 1e3,
                                 "gbs": bytes_ / t_batch / 1e9, "site_rhs": units,
                                 "tuned_tile_threads": chosen[0], "tuned_ctas_per_sm": chosen[2]}
     dd.lib.dd_batch_destroy(b)
@@ -473,7 +473,7 @@ def run_solve_only(args):
     return 0 if status == dd.DD_OK else 1
 
 
-def run_config5(args):
+def run_solve_64c128_8rhs(args):
     """Mixed-precision multi-RHS even-odd FGMRES with FP64 refinement to 1e-10
     on the 64^3 x 128 lattice with 8 Gaussian RHS, fitted in one GPU: FP64
     and FP16 copies of links and self coupling only, b and x resident in host
@@ -486,9 +486,9 @@ def run_config5(args):
     import synthetic
     import paper_2407_00041_gb300 as dd
     dims = (128, 64, 64, 64)
-    N, batch, m = 8, args.c5_batch, args.c5_restart
+    N, batch, m = 8, args.rhs_batch, args.restart
     V = int(np.prod(dims))
-    log("config 5: generating links and 8 right-hand sides")
+    log("64^3x128 solve: generating links and 8 right-hand sides")
     U = synthetic.gauge(dims, eps=EPS)
     b = synthetic.spinor(dims, nrhs=N)
     x = np.zeros_like(b)
@@ -504,10 +504,10 @@ def run_config5(args):
     plan = (free0 - free1) + 6 * h64 + V * 12 * 16 * batch + (2 * m + 1 + 8) * h32
     t0 = time.time()
     status, st = op.solve(b, x, N, layout=dd.DD_LAYOUT_CANONICAL_HOST, tol=1e-10, inner_prec=dd.DD_PREC_F16,
-                          restart=m, rhs_batch=batch, precond=dd.DD_PRECOND_CGNR, precond_iters=args.c5_cg,
+                          restart=m, rhs_batch=batch, precond=dd.DD_PRECOND_CGNR, precond_iters=args.cg_steps,
                           max_restarts=200, max_outer=10, verbose=1)
     wall = time.time() - t0
-    log(f"config 5 solve: status {status} {st}")
+    log(f"64^3x128 solve: status {status} {st}")
     # oracle check of ||b - D x|| / ||b|| on two time slices per RHS
     per = dims[1] * dims[2] * dims[3]
     sites = np.arange(2 * per, dtype=np.int64)
@@ -525,7 +525,7 @@ def run_config5(args):
             "vs_baseline": None, "dtype": "f32 (fp16 links/clover inner, fp64 refinement)", "data": "synthetic",
             "config": {"workload": "64^3x128 Wilson-clover, eps=0.3 links, m0=-0.4, c_sw=1.0, 8 Gaussian RHS",
                        "rhs_batch": batch, "restart": m,
-                       "method": f"even-odd FGMRES({m}), M_j = {args.c5_cg} CG steps on Dhat^H Dhat, FP64 refinement"},
+                       "method": f"even-odd FGMRES({m}), M_j = {args.cg_steps} CG steps on Dhat^H Dhat, FP64 refinement"},
             "status": status, "stats": st, "wall_s": wall,
             "device_memory": {"total_gb": total / 1e9, "handles_gb": (free0 - free1) / 1e9,
                               "planned_peak_gb": plan / 1e9},
@@ -548,16 +548,16 @@ def main():
     ap.add_argument("--solve-inner", default="f32", choices=["f32", "f16"])
     ap.add_argument("--dims", default="96x48x48x48", help="nT x nZ x nY x nX (a smaller lattice for profiling)")
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides of the timed D psi (profiling)")
-    ap.add_argument("--config5", action="store_true", help="run the 64^3x128, 8-RHS memory-fitted solve instead")
+    ap.add_argument("--solve-64x128-8rhs", action="store_true", help="run the 64^3x128, 8-RHS memory-fitted solve instead")
     ap.add_argument("--solve-only", action="store_true", help="run only the mixed 48^3x96 solve (for profiling)")
-    ap.add_argument("--c5-batch", type=int, default=2)
-    ap.add_argument("--c5-restart", type=int, default=8)
-    ap.add_argument("--c5-cg", type=int, default=64)
+    ap.add_argument("--rhs-batch", type=int, default=2, help="64^3x128 solve: right-hand sides per batch")
+    ap.add_argument("--restart", type=int, default=8, help="64^3x128 solve: FGMRES restart length")
+    ap.add_argument("--cg-steps", type=int, default=64, help="64^3x128 solve: CG steps per preconditioner application")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
-    if args.config5:
-        return run_config5(args)
+    if args.solve_64x128_8rhs:
+        return run_solve_64c128_8rhs(args)
     if args.solve_only:
         return run_solve_only(args)
 
