@@ -337,7 +337,7 @@ def test_fgmres_converges_true_residual_4x4():
     assert rel(x, np.linalg.solve(D, b)) < 1e-8
     for c, k in enumerate(st.inner_steps[:-1]):
         assert k == 30  # full cycles
-    # 1 application for the true residual + one per Arnoldi step (L297)
+    # one application for each true residual + one per Arnoldi step (Algorithm 2)
     assert st.applies == len(st.true_residuals) + sum(st.inner_steps)
 
 
