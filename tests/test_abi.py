@@ -52,3 +52,36 @@ def test_no_cpu_fallback_in_package():
             if f.endswith(".py"):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle", txt, flags=re.M), f
+
+
+def _ctype_of(decl):
+    """Kind of ctypes type the binding must use for one C parameter
+    declaration ("type name", "type* name", "type name[4]")."""
+    decl = decl.strip()
+    if "*" in decl or "[" in decl:
+        return "char_p" if re.match(r"const\s+char\s*\*", decl) else "pointer"
+    words = decl.replace("const", " ").split()
+    base = " ".join(words[:-1])  # the last word is the parameter name
+    return {"int": "int", "double": "double", "int64_t": "int64", "unsigned": "uint", "size_t": "size_t",
+            "void": None}[base]
+
+
+def test_binding_argument_and_return_types_match_the_header():
+    """Every ctypes signature in the binding has the parameter count, the
+    parameter kinds and the return type of its C declaration."""
+    from paper_2407_00041_gb300 import binding
+    kinds = {ctypes.c_void_p: "pointer", ctypes.c_int: "int", ctypes.c_double: "double", ctypes.c_int64: "int64",
+             ctypes.c_uint: "uint", ctypes.c_size_t: "size_t", ctypes.c_char_p: "char_p", None: None}
+    src = open(os.path.join(ROOT, "include", "dd_wilson.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    decls = re.findall(r"^([A-Za-z_][\w \*]*?)\b(dd_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", src, flags=re.S | re.M)
+    assert len(decls) == len(binding.SIGNATURES)
+    for ret, name, params in decls:
+        res, args = binding.SIGNATURES[name]
+        params = params.strip()
+        plist = [] if params in ("", "void") else [p for p in params.split(",")]
+        assert len(plist) == len(args), name
+        assert kinds[res] == _ctype_of(ret.strip() + " x"), (name, ret)
+        for i, (p, a) in enumerate(zip(plist, args)):
+            assert kinds[a] == _ctype_of(p), (name, i, p)
