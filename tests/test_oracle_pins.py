@@ -113,6 +113,28 @@ def test_dense_brute_force(dims):
         assert np.max(np.abs(cols - D)) < 1e-14
 
 
+@pytest.mark.parametrize("t_bc", [-1, 1])
+def test_site_sampled_apply_and_clover_match_the_dense_assembly(t_bc):
+    """clover_sites and apply_D_sites (the oracle of the full-size GPU tests)
+    against the rows of the independent dense assembly of Eq. 1.13: an
+    asymmetric lattice, an unsorted site list with a repeat, both time
+    boundaries included."""
+    dims = (4, 2, 4, 6)
+    per = dims[1] * dims[2] * dims[3]
+    V = int(np.prod(dims))
+    U = synthetic.gauge(dims)
+    psi = synthetic.spinor(dims, nrhs=1)[0].reshape(-1, 12)
+    rng = np.random.default_rng(7)
+    sites = np.concatenate([[V - 1, 0, per - 1, V - per], rng.integers(0, V, 20), [5, 5]]).astype(np.int64)
+    Ad = _dense.clover_field(U, dims, M0, CSW)
+    As = oracle.clover_sites(U, dims, M0, CSW, sites)
+    assert rel(As, Ad[sites]) < 1e-14
+    D = _dense.dense_D(U, dims, M0, CSW, t_bc=t_bc, A=Ad)
+    ref = (D @ psi.reshape(-1)).reshape(-1, 12)[sites]
+    got = oracle.apply_D_sites(U, As, psi, dims, sites, t_bc=t_bc)
+    assert rel(got, ref) < 1e-14
+
+
 def test_periodic_time_bc():
     dims = (2, 2, 2, 4)
     U = synthetic.gauge(dims)
