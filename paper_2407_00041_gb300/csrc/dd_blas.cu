@@ -304,43 +304,60 @@ __global__ void k_add64(const double2* __restrict__ in, double2* out, int64_t n)
 
 // Conjugate-gradient updates with per-RHS step sizes read from device
 // scalars (no host round trip):
-//   k_cg_xr:  alpha = g / n (0 if n == 0);  x += alpha p;  r -= alpha w
-//   k_cg_p:   beta = gn / go (0 if go == 0); p = z + beta p
-// g, n, gn, go: complex double [N] holding squared norms in .x.
+// g, n, gn: complex double [N] holding squared norms in .x (a zero
+// denominator gives a zero step).
+//   k_cg_r:   alpha = g / n;  r -= alpha w
+//   k_cg_x:   alpha = g / n;  x += alpha p
+//   k_cg_xp:  alpha = g / n, beta = gn / g;  x += alpha p;  p = z + beta p
+// (the CG step with the x update deferred into the direction update: the
+// same arithmetic in one pass over p)
 template <int PV>
-__global__ void __launch_bounds__(256) k_cg_xr(void* xp, void* rp, const void* pp, const void* wp,
-                                               const double2* __restrict__ g, const double2* __restrict__ n,
-                                               int64_t L, int N) {
+__global__ void __launch_bounds__(256) k_cg_r(void* rp, const void* wp, const double2* __restrict__ g,
+                                              const double2* __restrict__ n, int64_t L, int N) {
+  using T = typename G<PV>::group;
+  using R = typename G<PV>::real;
+  const int r = threadIdx.x % N;
+  const double nn = n[r].x;
+  const R alpha = nn > 0.0 ? (R)(g[r].x / nn) : R(0);
+  T* res = reinterpret_cast<T*>(rp);
+  const T* w = reinterpret_cast<const T*>(wp);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < L; e += stride) caxpy(-alpha, R(0), w[e], res[e]);
+}
+
+template <int PV>
+__global__ void __launch_bounds__(256) k_cg_x(void* xp, const void* pp, const double2* __restrict__ g,
+                                              const double2* __restrict__ n, int64_t L, int N) {
   using T = typename G<PV>::group;
   using R = typename G<PV>::real;
   const int r = threadIdx.x % N;
   const double nn = n[r].x;
   const R alpha = nn > 0.0 ? (R)(g[r].x / nn) : R(0);
   T* x = reinterpret_cast<T*>(xp);
-  T* res = reinterpret_cast<T*>(rp);
   const T* p = reinterpret_cast<const T*>(pp);
-  const T* w = reinterpret_cast<const T*>(wp);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < L; e += stride) {
-    caxpy(alpha, R(0), p[e], x[e]);
-    caxpy(-alpha, R(0), w[e], res[e]);
-  }
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < L; e += stride) caxpy(alpha, R(0), p[e], x[e]);
 }
 
 template <int PV>
-__global__ void __launch_bounds__(256) k_cg_p(void* pp, const void* zp, const double2* __restrict__ gn,
-                                              const double2* __restrict__ go, int64_t L, int N) {
+__global__ void __launch_bounds__(256) k_cg_xp(void* xp, void* pp, const void* zp, const double2* __restrict__ g,
+                                               const double2* __restrict__ n, const double2* __restrict__ gn,
+                                               int64_t L, int N) {
   using T = typename G<PV>::group;
   using R = typename G<PV>::real;
   const int r = threadIdx.x % N;
-  const double d = go[r].x;
-  const R beta = d > 0.0 ? (R)(gn[r].x / d) : R(0);
+  const double nn = n[r].x, go = g[r].x;
+  const R alpha = nn > 0.0 ? (R)(go / nn) : R(0);
+  const R beta = go > 0.0 ? (R)(gn[r].x / go) : R(0);
+  T* x = reinterpret_cast<T*>(xp);
   T* p = reinterpret_cast<T*>(pp);
   const T* z = reinterpret_cast<const T*>(zp);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < L; e += stride) {
+    const T pe = p[e];
+    caxpy(alpha, R(0), pe, x[e]);
     T v = z[e];
-    caxpy(beta, R(0), p[e], v);
+    caxpy(beta, R(0), pe, v);
     p[e] = v;
   }
 }
@@ -455,30 +472,41 @@ int blas_add64(const void* in, void* out, int64_t n, cudaStream_t st) {
 }
 
 template <int PV>
-int blas_cg_xr(void* x, void* r, const void* p, const void* w, const double2* g, const double2* n, int64_t L, int N,
-               cudaStream_t st) {
+int blas_cg_r(void* r, const void* w, const double2* g, const double2* n, int64_t L, int N, cudaStream_t st) {
   const int block = block_for(N);
   if (block <= 0) return fail(DD_ERR_ARG, "too many right-hand sides for the vector kernels");
-  k_cg_xr<PV><<<blas_grid(L, block), block, 0, st>>>(x, r, p, w, g, n, L, N);
+  k_cg_r<PV><<<blas_grid(L, block), block, 0, st>>>(r, w, g, n, L, N);
   DD_CUDA(cudaGetLastError());
   return DD_OK;
 }
 
 template <int PV>
-int blas_cg_p(void* p, const void* z, const double2* gn, const double2* go, int64_t L, int N, cudaStream_t st) {
+int blas_cg_x(void* x, const void* p, const double2* g, const double2* n, int64_t L, int N, cudaStream_t st) {
   const int block = block_for(N);
   if (block <= 0) return fail(DD_ERR_ARG, "too many right-hand sides for the vector kernels");
-  k_cg_p<PV><<<blas_grid(L, block), block, 0, st>>>(p, z, gn, go, L, N);
+  k_cg_x<PV><<<blas_grid(L, block), block, 0, st>>>(x, p, g, n, L, N);
   DD_CUDA(cudaGetLastError());
   return DD_OK;
 }
 
-template int blas_cg_xr<P64>(void*, void*, const void*, const void*, const double2*, const double2*, int64_t, int,
+template <int PV>
+int blas_cg_xp(void* x, void* p, const void* z, const double2* g, const double2* n, const double2* gn, int64_t L,
+               int N, cudaStream_t st) {
+  const int block = block_for(N);
+  if (block <= 0) return fail(DD_ERR_ARG, "too many right-hand sides for the vector kernels");
+  k_cg_xp<PV><<<blas_grid(L, block), block, 0, st>>>(x, p, z, g, n, gn, L, N);
+  DD_CUDA(cudaGetLastError());
+  return DD_OK;
+}
+
+template int blas_cg_r<P64>(void*, const void*, const double2*, const double2*, int64_t, int, cudaStream_t);
+template int blas_cg_r<P32>(void*, const void*, const double2*, const double2*, int64_t, int, cudaStream_t);
+template int blas_cg_x<P64>(void*, const void*, const double2*, const double2*, int64_t, int, cudaStream_t);
+template int blas_cg_x<P32>(void*, const void*, const double2*, const double2*, int64_t, int, cudaStream_t);
+template int blas_cg_xp<P64>(void*, void*, const void*, const double2*, const double2*, const double2*, int64_t, int,
                              cudaStream_t);
-template int blas_cg_xr<P32>(void*, void*, const void*, const void*, const double2*, const double2*, int64_t, int,
+template int blas_cg_xp<P32>(void*, void*, const void*, const double2*, const double2*, const double2*, int64_t, int,
                              cudaStream_t);
-template int blas_cg_p<P64>(void*, const void*, const double2*, const double2*, int64_t, int, cudaStream_t);
-template int blas_cg_p<P32>(void*, const void*, const double2*, const double2*, int64_t, int, cudaStream_t);
 template int blas_multidot<P64>(const VecList&, int, const void*, int64_t, int, double2*, int, double2*, cudaStream_t);
 template int blas_multidot<P32>(const VecList&, int, const void*, int64_t, int, double2*, int, double2*, cudaStream_t);
 template int blas_multiaxpy<P64>(const VecList&, int, const double2*, double, void*, int64_t, int, cudaStream_t,

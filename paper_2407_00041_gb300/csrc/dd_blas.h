@@ -24,13 +24,16 @@ int blas_multiaxpy(const VecList& vs, int J, const double2* c_dev, double csign,
 // out = c[r] * in
 template <int PV>
 int blas_scale(const double2* c_dev, const void* in, void* out, int64_t L, int N, cudaStream_t st);
-// CG updates with step sizes from device scalars (squared norms in .x):
-// x += (g/n) p, r -= (g/n) w;   p = z + (gn/go) p
+// CG updates with step sizes from device scalars (squared norms in .x), the
+// x update deferred into the direction update: r -= (g/n) w;  x += (g/n) p;
+// x += (g/n) p and p = z + (gn/g) p in one pass over p.
 template <int PV>
-int blas_cg_xr(void* x, void* r, const void* p, const void* w, const double2* g, const double2* n, int64_t L, int N,
-               cudaStream_t st);
+int blas_cg_r(void* r, const void* w, const double2* g, const double2* n, int64_t L, int N, cudaStream_t st);
 template <int PV>
-int blas_cg_p(void* p, const void* z, const double2* gn, const double2* go, int64_t L, int N, cudaStream_t st);
+int blas_cg_x(void* x, const void* p, const double2* g, const double2* n, int64_t L, int N, cudaStream_t st);
+template <int PV>
+int blas_cg_xp(void* x, void* p, const void* z, const double2* g, const double2* n, const double2* gn, int64_t L,
+               int N, cudaStream_t st);
 // out[i] (+)= sum over b < nblocks of partials[b * JN + i], i < JN, summed in
 // a fixed order (warp shuffles, then the warps in turn).  From 4096 partials
 // on, the sum runs in two stages (64 CTAs over contiguous chunks, then one)

@@ -165,18 +165,28 @@ struct Inner {
     DD_CUDA(cudaMemcpyAsync(cr.ptr, v, vbytes, cudaMemcpyDeviceToDevice, st));
     DD_TRY(apply_op_norm(cr.ptr, cz.ptr, true, g[0], st));  // A^H r and its norm
     DD_CUDA(cudaMemcpyAsync(cp.ptr, cz.ptr, vbytes, cudaMemcpyDeviceToDevice, st));
+    // step i: alpha = g_i / |A p|^2, x += alpha p, r -= alpha A p,
+    // z' = A^H r, beta = g_{i+1} / g_i, p = z' + beta p; the x update is
+    // deferred into the direction update (one pass over p), and the last
+    // step updates x only (r is not needed after it)
     for (int i = 0; i < cg_iters; ++i) {
       DD_TRY(apply_op_norm(cp.ptr, w.ptr, false, nw, st));  // w = A p, |w|^2
+      if (i + 1 == cg_iters) {
+        if (pv == P64)
+          DD_TRY(blas_cg_x<P64>(z, cp.ptr, g[i & 1], nw, L, N, st));
+        else
+          DD_TRY(blas_cg_x<P32>(z, cp.ptr, g[i & 1], nw, L, N, st));
+        break;
+      }
       if (pv == P64)
-        DD_TRY(blas_cg_xr<P64>(z, cr.ptr, cp.ptr, w.ptr, g[i & 1], nw, L, N, st));
+        DD_TRY(blas_cg_r<P64>(cr.ptr, w.ptr, g[i & 1], nw, L, N, st));
       else
-        DD_TRY(blas_cg_xr<P32>(z, cr.ptr, cp.ptr, w.ptr, g[i & 1], nw, L, N, st));
-      if (i + 1 == cg_iters) break;  // the last direction update is not needed
+        DD_TRY(blas_cg_r<P32>(cr.ptr, w.ptr, g[i & 1], nw, L, N, st));
       DD_TRY(apply_op_norm(cr.ptr, cz.ptr, true, g[(i + 1) & 1], st));  // z' = A^H r, |z'|^2
       if (pv == P64)
-        DD_TRY(blas_cg_p<P64>(cp.ptr, cz.ptr, g[(i + 1) & 1], g[i & 1], L, N, st));
+        DD_TRY(blas_cg_xp<P64>(z, cp.ptr, cz.ptr, g[i & 1], nw, g[(i + 1) & 1], L, N, st));
       else
-        DD_TRY(blas_cg_p<P32>(cp.ptr, cz.ptr, g[(i + 1) & 1], g[i & 1], L, N, st));
+        DD_TRY(blas_cg_xp<P32>(z, cp.ptr, cz.ptr, g[i & 1], nw, g[(i + 1) & 1], L, N, st));
     }
     return DD_OK;
   }
