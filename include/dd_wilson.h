@@ -57,6 +57,24 @@
  * Errors: every call returns a status (DD_OK = 0, negative on error); it never
  * aborts.  dd_last_error_detail() describes the last error of the calling
  * thread.
+ *
+ * Environment (each read once per process, at first use; all optional):
+ *   DD_RECON=0          no two-row FP32 link copy at dd_gauge_create (the
+ *                       single-RHS kernels then read three rows).
+ *   DD_RHS_BLOCK=n      largest RHS block of the multi-RHS stencil (1, 2 or
+ *                       4; default 4; 1 gives one thread per site and RHS).
+ *   DD_ZBLOCK=d         Z-slab depth of the traversal (a divisor of nZ; 0 =
+ *                       nZ); default: the deepest slab within 30 MB.
+ *   DD_HOST_CHUNKS=c    time-slice chunks of the pipelined host-buffer
+ *                       apply (default 24).
+ *   DD_FUSED_NORM=0     the CG preconditioner of dd_solve takes its norms
+ *                       from separate reductions instead of the stencil
+ *                       launch (read at each dd_solve).
+ *   DD_STAGE=1          opt-in row-staged stencil for full-lattice FP32
+ *                       applies (slower; DD_STAGE_SLOTS sets its ring depth,
+ *                       DD_STAGE_NARROW=1 allows its narrow-row variant,
+ *                       DD_STAGE_WAIT_TEST=1 makes one of its waits expire
+ *                       so that tests can check dd_device_status).
  */
 #ifndef DD_WILSON_H
 #define DD_WILSON_H
