@@ -155,6 +155,27 @@ int dd_gauge_stored_rows(const dd_gauge* g, int prec);
  * the gauge handle.
  */
 int dd_gauge_create(const dd_lattice* lat, const double* U, int location, unsigned prec_mask, dd_gauge** out);
+/*
+ * Synthetic gauge field generated on the device (the thesis' gauge
+ * configurations are not public; this generator stands in for them and is not
+ * part of the thesis).  Link U_mu(x) = exp(i eps H) with H = (A + A^H)/2 -
+ * (tr A_re / 3) I traceless Hermitian, A a 3x3 matrix of complex Gaussians
+ * (Re, Im i.i.d. N(0, 1)); U is special unitary, the SU(3) element of
+ * Section 1.1.  The Gaussians come from a counter-based stream, so every link
+ * is drawn independently of launch shape and thread count:
+ *   key = mix64(seed), word k = mix64(key + (k + 1) * 0x9E3779B97F4A7C15)
+ *   (SplitMix64, Steele, Lea and Flood 2014); Gaussian pair number
+ *   n = (4 x + mu) * 9 + (3 a + b) for entry (a, b) of A at link (x, mu), from
+ *   u1 = ((word(2n) >> 11) + 1) 2^-53, u2 = (word(2n + 1) >> 11) 2^-53 by
+ *   Box-Muller: sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2).
+ * The exponential is a 14-term Taylor series with scaling and squaring.
+ * Layouts and precision copies as for dd_gauge_create (FP64 always kept);
+ * the result equals dd_gauge_create of the same field generated on the host
+ * to rounding (about 1e-15).  eps must be finite and >= 0 (DD_ERR_ARG
+ * otherwise); the benchmark configurations use eps = 0.3, seed 20240700.
+ * Synchronises the device.  The lattice must outlive the gauge handle.
+ */
+int dd_gauge_generate(const dd_lattice* lat, uint64_t seed, double eps, unsigned prec_mask, dd_gauge** out);
 int dd_gauge_destroy(dd_gauge* g);
 /* Copy the FP64 links back out as complex double [V][4][3][3] to host (location 0) or device (1). */
 int dd_gauge_download(const dd_gauge* g, double* U, int location);

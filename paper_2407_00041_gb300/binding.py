@@ -58,6 +58,7 @@ SIGNATURES = {
     "dd_lattice_destroy": (_I, [_P]),
     "dd_lattice_volume": (_L, [_P]),
     "dd_gauge_create": (_I, [_P, _P, _I, _U, _P]),
+    "dd_gauge_generate": (_I, [_P, ctypes.c_uint64, _D, _U, _P]),
     "dd_gauge_destroy": (_I, [_P]),
     "dd_gauge_download": (_I, [_P, _P, _I]),
     "dd_clover_create": (_I, [_P, _D, _D, _U, _P]),
@@ -153,6 +154,28 @@ class Gauge:
         h = ctypes.c_void_p()
         check(lib.dd_gauge_create(lattice.h, _ptr(U), loc, precisions, ctypes.byref(h)), "dd_gauge_create")
         self.h = h
+
+    @classmethod
+    def generate(cls, lattice, seed=20240700, eps=0.3, precisions=DD_PREC_F64 | DD_PREC_F32 | DD_PREC_F16):
+        """Links exp(i eps H) drawn on the device by ``dd_gauge_generate``."""
+        lib = load()
+        self = cls.__new__(cls)
+        self.lattice = lattice
+        h = ctypes.c_void_p()
+        check(lib.dd_gauge_generate(lattice.h, int(seed), float(eps), precisions, ctypes.byref(h)),
+              "dd_gauge_generate")
+        self.h = h
+        return self
+
+    def download(self, out=None):
+        """The FP64 links as complex128 [V, 4, 3, 3] (numpy, or into a torch tensor on the device)."""
+        import numpy as np
+        if out is None:
+            out = np.empty((self.lattice.V, 4, 3, 3), dtype=np.complex128)
+            check(_lib.dd_gauge_download(self.h, out.ctypes.data, 0), "dd_gauge_download")
+        else:
+            check(_lib.dd_gauge_download(self.h, _ptr(out), 1 if out.is_cuda else 0), "dd_gauge_download")
+        return out
 
     def __del__(self):
         if getattr(self, "h", None) and _lib is not None:

@@ -185,36 +185,75 @@ int dd_lattice_destroy(dd_lattice* lat) {
 
 int64_t dd_lattice_volume(const dd_lattice* lat) { return lat ? lat->V : 0; }
 
-int dd_gauge_create(const dd_lattice* lat, const double* U, int location, unsigned prec_mask, dd_gauge** out) {
-  if (!lat || !U || !out) return fail(DD_ERR_ARG, "null argument");
-  if (location != 0 && location != 1) return fail(DD_ERR_ARG, "location must be 0 (host) or 1 (device)");
-  if (prec_mask & ~7u) return fail(DD_ERR_ARG, "bad precision mask");
+namespace {
+
+// A gauge handle with the native link buffers of prec_mask (FP64 always).
+int gauge_alloc(const dd_lattice* lat, unsigned prec_mask, dd_gauge** out) {
   dd_gauge* g = new (std::nothrow) dd_gauge;
   if (!g) return fail(DD_ERR_OOM, "host allocation failed");
   g->lat = lat;
   g->prec_mask = prec_mask | DD_PREC_F64;
-  const size_t bytes = (size_t)lat->V * 4 * 9 * 16;
   const int64_t nel = lat->V * 4 * 9;
   int s = g->links[0].alloc(nel * 16);
   if (s == DD_OK && (g->prec_mask & DD_PREC_F32)) s = g->links[1].alloc(nel * 8);
   if (s == DD_OK && (g->prec_mask & DD_PREC_F16)) s = g->links[2].alloc(nel * 4);
+  if (s != DD_OK) {
+    delete g;
+    return s;
+  }
+  *out = g;
+  return DD_OK;
+}
+
+// After the links are in place: SU(3) check, the two-row FP32 copy when
+// every link is SU(3) to FP32 accuracy (DD_RECON=0 keeps all three rows),
+// and a device synchronisation.
+int gauge_finish(dd_gauge* g) {
+  int s = links_su3_deviation(g, &g->su3_deviation, 0);
+  if (s == DD_OK && (g->prec_mask & DD_PREC_F32) && g->su3_deviation < 1e-6) {
+    const char* e = getenv("DD_RECON");
+    if (!e || atoi(e) != 0) s = links_to_recon32(g, 0);
+  }
+  if (s == DD_OK && cudaDeviceSynchronize() != cudaSuccess) s = cuda_fail(cudaGetLastError(), "link conversion");
+  return s;
+}
+
+}  // namespace
+
+int dd_gauge_create(const dd_lattice* lat, const double* U, int location, unsigned prec_mask, dd_gauge** out) {
+  if (!lat || !U || !out) return fail(DD_ERR_ARG, "null argument");
+  if (location != 0 && location != 1) return fail(DD_ERR_ARG, "location must be 0 (host) or 1 (device)");
+  if (prec_mask & ~7u) return fail(DD_ERR_ARG, "bad precision mask");
+  dd_gauge* g = nullptr;
+  DD_TRY(gauge_alloc(lat, prec_mask, &g));
+  const size_t bytes = (size_t)lat->V * 4 * 9 * 16;
+  int s = DD_OK;
   DevBuf staging;
   const double* Ud = U;
-  if (s == DD_OK && location == 0) {
+  if (location == 0) {
     s = staging.alloc(bytes);
     if (s == DD_OK && cudaMemcpy(staging.ptr, U, bytes, cudaMemcpyHostToDevice) != cudaSuccess)
       s = cuda_fail(cudaGetLastError(), "cudaMemcpy of the links");
     Ud = reinterpret_cast<const double*>(staging.ptr);
   }
   if (s == DD_OK) s = links_to_native(lat, Ud, g, 0);
-  if (s == DD_OK) s = links_su3_deviation(g, &g->su3_deviation, 0);
-  // two-row FP32 links when every link is SU(3) to FP32 accuracy (DD_RECON=0
-  // keeps all three rows)
-  if (s == DD_OK && (g->prec_mask & DD_PREC_F32) && g->su3_deviation < 1e-6) {
-    const char* e = getenv("DD_RECON");
-    if (!e || atoi(e) != 0) s = links_to_recon32(g, 0);
+  if (s == DD_OK) s = gauge_finish(g);
+  if (s != DD_OK) {
+    delete g;
+    return s;
   }
-  if (s == DD_OK && cudaDeviceSynchronize() != cudaSuccess) s = cuda_fail(cudaGetLastError(), "link conversion");
+  *out = g;
+  return DD_OK;
+}
+
+int dd_gauge_generate(const dd_lattice* lat, uint64_t seed, double eps, unsigned prec_mask, dd_gauge** out) {
+  if (!lat || !out) return fail(DD_ERR_ARG, "null argument");
+  if (prec_mask & ~7u) return fail(DD_ERR_ARG, "bad precision mask");
+  if (!(eps >= 0.0 && eps <= 1e6)) return fail(DD_ERR_ARG, "eps must be finite and >= 0");
+  dd_gauge* g = nullptr;
+  DD_TRY(gauge_alloc(lat, prec_mask, &g));
+  int s = links_generate(lat, seed, eps, g, 0);
+  if (s == DD_OK) s = gauge_finish(g);
   if (s != DD_OK) {
     delete g;
     return s;

@@ -148,6 +148,9 @@ int op_dhat_residual(const dd_clover* op, int pg, int pv, const Field& bhat, con
 
 // ---- setup kernels (dd_setup.cu) ----
 int links_to_native(const dd_lattice* lat, const double* U_canon_dev, dd_gauge* g, cudaStream_t st);
+// synthetic links exp(i eps H) from the counter-based generator, written to
+// every native copy of g (dd_gauge_generate)
+int links_generate(const dd_lattice* lat, uint64_t seed, double eps, dd_gauge* g, cudaStream_t st);
 // max over links of max(|U U^H - 1|, |det U - 1|) from the FP64 copy (synchronises)
 int links_su3_deviation(const dd_gauge* g, double* dev, cudaStream_t st);
 // build the two-row FP32 copy: [parity][12 groups][Vh] float4

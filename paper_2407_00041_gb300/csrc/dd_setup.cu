@@ -40,12 +40,10 @@ __device__ __forceinline__ int coords_to_lex(const LexGeom& g, const int c[4]) {
 }
 
 // ---------------------------------------------------------------- links
-__global__ void k_links_to_native(LexGeom g, const double2* __restrict__ Uc, double2* U64, float2* U32,
-                                  __half2* U16) {
-  const int64_t V = 2 * g.Vh;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= V * 4) return;
-  const int lex = (int)(t >> 2), mu = (int)(t & 3);
+// Store link (lex, mu), nine complex elements row-major, in every native
+// copy that exists (U32 / U16 may be null).
+__device__ __forceinline__ void put_link_native(const LexGeom& g, int lex, int mu, const double2 v[9], double2* U64,
+                                                float2* U32, __half2* U16) {
   int c[4];
   lex_to_coords(g, lex, c);
   const int p = (c[0] + c[1] + c[2] + c[3]) & 1;
@@ -55,12 +53,118 @@ __global__ void k_links_to_native(LexGeom g, const double2* __restrict__ Uc, dou
   const int64_t pbase = (int64_t)p * 36 * g.Vh;
 #pragma unroll
   for (int e = 0; e < 9; ++e) {
-    double2 v = Uc[t * 9 + e];
-    U64[base + e * g.Vh] = v;
+    U64[base + e * g.Vh] = v[e];
     const int E = 9 * mu + e;
-    if (U32) U32[pbase + ((int64_t)(E >> 1) * g.Vh + s) * 2 + (E & 1)] = make_float2((float)v.x, (float)v.y);
-    if (U16) U16[pbase + ((int64_t)(E >> 2) * g.Vh + s) * 4 + (E & 3)] = __floats2half2_rn((float)v.x, (float)v.y);
+    if (U32) U32[pbase + ((int64_t)(E >> 1) * g.Vh + s) * 2 + (E & 1)] = make_float2((float)v[e].x, (float)v[e].y);
+    if (U16)
+      U16[pbase + ((int64_t)(E >> 2) * g.Vh + s) * 4 + (E & 3)] = __floats2half2_rn((float)v[e].x, (float)v[e].y);
   }
+}
+
+__global__ void k_links_to_native(LexGeom g, const double2* __restrict__ Uc, double2* U64, float2* U32,
+                                  __half2* U16) {
+  const int64_t V = 2 * g.Vh;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= V * 4) return;
+  double2 v[9];
+#pragma unroll
+  for (int e = 0; e < 9; ++e) v[e] = Uc[t * 9 + e];
+  put_link_native(g, (int)(t >> 2), (int)(t & 3), v, U64, U32, U16);
+}
+
+// ---------------------------------------------------------------- link generator
+// Counter-based synthetic links (not part of the thesis; it stands in for its
+// gauge configurations).  SplitMix64 (Steele, Lea and Flood, "Fast splittable
+// pseudorandom number generators", 2014) keyed by the seed gives word k of
+// the stream as mix64(mix64(seed) + (k + 1) * golden gamma); pair k of
+// uniforms u1 = ((word(2k) >> 11) + 1) 2^-53 in (0, 1], u2 = (word(2k+1) >> 11)
+// 2^-53 turns into one complex Gaussian by Box-Muller,
+// sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2).  Link (x, mu) uses pairs
+// (4 x + mu) 9 + j, j = 0..8, as the entries of a 3x3 matrix A; with
+// H = (A + A^H) / 2 - tr / 3 (traceless Hermitian) the link is U = exp(i eps H),
+// special unitary.  The exponential is scaling and squaring of a 14-term
+// Taylor series in Horner form (Higham 2005), exact to rounding here.
+__device__ __forceinline__ uint64_t gen_mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ double2 gen_normal_pair(uint64_t key, uint64_t pair) {
+  const uint64_t w1 = gen_mix64(key + (2 * pair + 1ULL) * 0x9E3779B97F4A7C15ULL);
+  const uint64_t w2 = gen_mix64(key + (2 * pair + 2ULL) * 0x9E3779B97F4A7C15ULL);
+  const double two53 = 1.0 / 9007199254740992.0;
+  const double u1 = (double)((w1 >> 11) + 1ULL) * two53;
+  const double u2 = (double)(w2 >> 11) * two53;
+  const double r = sqrt(-2.0 * log(u1));
+  double sn, cs;
+  sincos(6.283185307179586476925286766559 * u2, &sn, &cs);
+  return make_double2(r * cs, r * sn);
+}
+
+// C = A B for 3x3 complex matrices (row-major); C may alias neither operand
+__device__ __forceinline__ void gen_m3_mul(const double2* A, const double2* B, double2* C) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      double re = 0.0, im = 0.0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const double2 x = A[3 * a + k], y = B[3 * k + b];
+        re += x.x * y.x - x.y * y.y;
+        im += x.x * y.y + x.y * y.x;
+      }
+      C[3 * a + b] = make_double2(re, im);
+    }
+}
+
+__global__ void k_links_generate(LexGeom g, uint64_t key, double eps, double2* U64, float2* U32, __half2* U16) {
+  const int64_t V = 2 * g.Vh;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= V * 4) return;
+  double2 A[9], X[9];
+#pragma unroll
+  for (int j = 0; j < 9; ++j) A[j] = gen_normal_pair(key, (uint64_t)t * 9ULL + (uint64_t)j);
+  // X = i eps H, H = (A + A^H) / 2 - (tr / 3) I
+  double tr = 0.0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) tr += A[4 * a].x;
+  tr /= 3.0;
+  double nrm = 0.0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      double hre = 0.5 * (A[3 * a + b].x + A[3 * b + a].x);
+      const double him = 0.5 * (A[3 * a + b].y - A[3 * b + a].y);
+      if (a == b) hre -= tr;
+      X[3 * a + b] = make_double2(-eps * him, eps * hre);
+      nrm += X[3 * a + b].x * X[3 * a + b].x + X[3 * a + b].y * X[3 * a + b].y;
+    }
+  nrm = sqrt(nrm);
+  int k = 0;
+  double scale = 1.0;
+  while (nrm * scale > 0.25) {
+    scale *= 0.5;
+    ++k;
+  }
+#pragma unroll
+  for (int i = 0; i < 9; ++i) X[i] = make_double2(X[i].x * scale, X[i].y * scale);
+  double2 E[9], T[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) E[i] = make_double2(i % 4 == 0 ? 1.0 : 0.0, 0.0);
+  for (int n = 14; n >= 1; --n) {
+    gen_m3_mul(X, E, T);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) E[i] = make_double2(T[i].x / (double)n + (i % 4 == 0 ? 1.0 : 0.0), T[i].y / (double)n);
+  }
+  for (int s = 0; s < k; ++s) {
+    gen_m3_mul(E, E, T);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) E[i] = T[i];
+  }
+  put_link_native(g, (int)(t >> 2), (int)(t & 3), E, U64, U32, U16);
 }
 
 // max(|U U^H - 1|, |det U - 1|) of every link, reduced with an atomic max on
@@ -493,6 +597,20 @@ int links_to_native(const dd_lattice* lat, const double* Uc, dd_gauge* g, cudaSt
   const int64_t n = lat->V * 4;
   k_links_to_native<<<nblk(n, 128), 128, 0, st>>>(
       lex_geom(lat), reinterpret_cast<const double2*>(Uc), reinterpret_cast<double2*>(g->links[0].ptr),
+      reinterpret_cast<float2*>(g->links[1].ptr), reinterpret_cast<__half2*>(g->links[2].ptr));
+  DD_CUDA(cudaGetLastError());
+  return DD_OK;
+}
+
+int links_generate(const dd_lattice* lat, uint64_t seed, double eps, dd_gauge* g, cudaStream_t st) {
+  const int64_t n = lat->V * 4;
+  // the stream key is mix64(seed), as in the host-side generator
+  uint64_t z = seed;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  const uint64_t key = z ^ (z >> 31);
+  k_links_generate<<<nblk(n, 128), 128, 0, st>>>(
+      lex_geom(lat), key, eps, reinterpret_cast<double2*>(g->links[0].ptr),
       reinterpret_cast<float2*>(g->links[1].ptr), reinterpret_cast<__half2*>(g->links[2].ptr));
   DD_CUDA(cudaGetLastError());
   return DD_OK;

@@ -62,8 +62,8 @@ def _ctype_of(decl):
         return "char_p" if re.match(r"const\s+char\s*\*", decl) else "pointer"
     words = decl.replace("const", " ").split()
     base = " ".join(words[:-1])  # the last word is the parameter name
-    return {"int": "int", "double": "double", "int64_t": "int64", "unsigned": "uint", "size_t": "size_t",
-            "void": None}[base]
+    return {"int": "int", "double": "double", "int64_t": "int64", "uint64_t": "size_t", "unsigned": "uint",
+            "size_t": "size_t", "void": None}[base]
 
 
 def test_binding_argument_and_return_types_match_the_header():
