@@ -70,6 +70,7 @@ def log(msg):
 
 
 LINK_ROWS_F32 = [3]  # rows per FP32 link read by single-RHS applies (set once the gauge exists)
+HBM_PEAK = [6800.0]  # GB/s, replaced by the measured copy bandwidth at start
 
 
 def bytes_per_site(prec, nrhs=1):
@@ -294,10 +295,45 @@ def cpu_baseline(U, psi, dims, budget_s=20.0, reps=3):
     slices = int(max(1, min(dims[0] - 2, (budget_s - s1 - t1) / max(s1 + reps * t1, 1e-6))))
     sites, out, dt, ts = oracle_sample_rate(U, psi, dims, slices, reps)
     gbs = bytes_per_site("f64") * sites.size / dt / 1e9
-    return {"value": gbs, "unit": "GB/s", "cores": oracle.threads(), "kind": "oracle",
+    cores = oracle.threads()
+    # the same oracle on one core (one time slice, `reps` repetitions)
+    oracle.set_threads(1)
+    try:
+        s1, _, dt1, _ = oracle_sample_rate(U, psi, dims, 1, reps)
+    finally:
+        oracle.set_threads(cores)
+    gbs1 = bytes_per_site("f64") * s1.size / dt1 / 1e9
+    return {"value": gbs, "unit": "GB/s", "cores": cores, "kind": "oracle",
             "sample": f"FP64 CPU oracle D psi (Eq. 1.13) on the {sites.size} sites of time slices 0..{slices - 1} "
                       f"of the 48^3x96 lattice, {reps} repetitions, {dt:.3f} s per apply (self-coupling setup "
-                      f"{ts:.1f} s not timed); GB/s counts the FP64 algorithmic 1536 B/site"}, (sites, out)
+                      f"{ts:.1f} s not timed); GB/s counts the FP64 algorithmic 1536 B/site",
+            "single_thread": {"value": gbs1, "unit": "GB/s", "cores": 1,
+                              "sample": f"the {s1.size} sites of time slice 0, {reps} repetitions, "
+                                        f"{dt1:.3f} s per apply",
+                              "full_lattice_apply_s_est": dt1 * int(np.prod(dims)) / s1.size},
+            "full_lattice_apply_s_est": dt * int(np.prod(dims)) / sites.size,
+            "host_cpu": host_cpu_model()}, (sites, out)
+
+
+def host_cpu_model():
+    """CPU model and logical CPU count of this host (from /proc/cpuinfo and os)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                k = ln.split(":", 1)[0].strip().lower()
+                if k in ("model name", "cpu part", "hardware") and model is None:
+                    model = ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        impl = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        m = re.search(r"Model name:\s*(.+)", impl)
+        if m:
+            model = m.group(1).strip()
+    except Exception:
+        pass
+    return {"model": model, "nproc": os.cpu_count()}
 
 
 def run_reference(args):
@@ -408,7 +444,7 @@ def extra_measurements(dd, torch, stream, op48, psi48, V48, tdist, clocks, alu_p
                                                       dd.DD_LAYOUT_NATIVE, st), "D 12 RHS"), 20)
         out[f"mrhs_32x4_12rhs_{name}"] = {"ms": t * 1e3, "gbs": bytes_per_site(name, 12) * V32 / t / 1e9,
                                           "site_rhs_per_s": V32 * 12 / t,
-                                          "hbm_frac": bytes_per_site(name, 12) * V32 / t / 1e9 / 6791.0}
+                                          "hbm_frac": bytes_per_site(name, 12) * V32 / t / 1e9 / HBM_PEAK[0]}
     del x12
     # batched uneven lattices, FP32
     arr = lambda v, t=ctypes.c_void_p: (t * len(v))(*v)
@@ -570,6 +606,7 @@ def main():
     tdist = init_dist(world, local)
     stream = torch.cuda.current_stream()
     peaks, peak_kind = measured_peaks()
+    HBM_PEAK[0] = peaks["hbm_gbs"]
     try:
         uuid = str(torch.cuda.get_device_properties(local).uuid)
         gpu_id = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
@@ -595,6 +632,7 @@ def main():
 
     gpu_launches = 0
     variants = {}
+    rooflines = {}
     f64_peak = f32_peak = None
     fl = np.zeros(1, dtype=np.float64)
     dd.check(dd.lib.dd_probe_flops(dd.DD_PREC_F64, fl.ctypes.data, stream.cuda_stream), "probe")
@@ -636,6 +674,13 @@ def main():
         variants[prec] = {"gbs": gbs, "ms_per_apply": ms, "hbm_frac": bytes_per_site(prec, N) * V / kern / 1e9 /
                           peaks["hbm_gbs"], "gflops_nominal": gflops, "bound": bound,
                           "roof_frac": frac, "bytes_per_site": bytes_per_site(prec, N)}
+        rooflines[prec] = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": frac,
+                           "traffic": (profile_traffic(prec) if N == 1 and dims == DIMS and
+                                       (prec != "f32" or LINK_ROWS_F32[0] == 2) else None),
+                           "ms_per_apply": kern * 1e3,
+                           "peak_source": f"{peak_kind} MEASURED_PEAKS.json hbm_gbs" if bound == "hbm"
+                           else "FMA-chain probe dd_probe_flops on this GPU (FP64 pipe)" if prec == "f64"
+                           else "FMA-chain probe dd_probe_flops on this GPU (FP32 pipe)"}
         if prec == args.prec:
             traffic = (profile_traffic(prec) if N == 1 and dims == DIMS and (prec != "f32" or LINK_ROWS_F32[0] == 2)
                        else None)  # the captured launch: 48^3x96, one RHS, two-row FP32 links
@@ -744,7 +789,8 @@ def main():
                    "precision": args.prec, "nrhs": N, "sites": V, "f32_link_rows_single_rhs": rows32,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "inputs (>8 GB) larger than L2; no flush"},
-        "roofline": head["roofline"], "variants": variants, "e2e": e2e, "solve": solve,
+        "roofline": head["roofline"], "roofline_by_precision": rooflines, "variants": variants, "e2e": e2e,
+        "solve": solve,
         "cpu_baseline": cpu, "parity_sample": parity, "extra": extra, "gpu_launches": gpu_launches, "clocks": clk,
         "probe_tflops": {"f64": f64_peak / 1e12, "f32": f32_peak / 1e12},
     }

@@ -60,6 +60,7 @@ def _load():
             "oracle_clover_field": [P, P, D, D, P],
             "oracle_clover_sites": [P, P, D, D, P, L, P],
             "oracle_threads": [],
+            "oracle_set_threads": [I],
             "oracle_apply_D": [P, I, P, P, P, P],
             "oracle_apply_D_sites": [P, I, P, P, P, P, L, P],
             "oracle_apply_DH": [P, I, P, P, P, P],
@@ -131,6 +132,11 @@ def clover_sites(U, dims, m0: float, csw: float, sites) -> np.ndarray:
 def threads() -> int:
     """OpenMP threads the oracle's site loops use."""
     return int(_load().oracle_threads())
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's later site loops (timing only; same results)."""
+    _load().oracle_set_threads(int(n))
 
 
 def apply_D(U, A, psi, dims, t_bc: int = -1) -> np.ndarray:

@@ -204,6 +204,16 @@ int oracle_threads(void) {
 #endif
 }
 
+/* Set the threads of later OpenMP loops (n >= 1), for timing the oracle on one
+ * core beside all cores; no effect on the arithmetic. */
+void oracle_set_threads(int n) {
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 void oracle_clover_field(const int d[4], const cplx* U, double m0, double csw, cplx* A) {
   const int64_t V = volume(d);
 #pragma omp parallel for schedule(static)
