@@ -414,6 +414,24 @@ def extra_measurements(dd, torch, stream, op48, psi48, V48, tdist, clocks, alu_p
         link, clov, spin = {"f32": (96 * LINK_ROWS_F32[0], 288, 96), "f16": (144, 144, 52)}[name]
         bytes_ = 2 * link * V48 + clov * V48 + 5 * spin * (V48 // 2)
         out[f"dhat_{name}"] = {"ms": t * 1e3, "gbs_formula": bytes_ / t / 1e9}
+    # domain-decomposed D psi (Algorithm 3 on virtual ranks of this GPU): the
+    # 48^3 x 96 lattice split in T, in T and X, and in all four directions
+    xi = torch.empty(op48.field_bytes(2, 0, 1), dtype=torch.uint8, device="cuda")
+    op48.pack(2, 0, psi48[:1].contiguous(), xi, 1)
+    xo = torch.empty_like(xi)
+    t_single = _time_fn(lambda: dd.check(dd.lib.dd_apply(op48.h, dd.DD_OP_D, 2, xi.data_ptr(), xo.data_ptr(), 1,
+                                                         dd.DD_LAYOUT_NATIVE, st), "D"), 20)
+    dec_res = {"ms_single_domain": t_single * 1e3}
+    for grid in ((2, 1, 1, 1), (2, 1, 1, 2), (2, 2, 2, 2)):
+        dec = dd.Decomposition(op48, grid)
+        dec.scatter(2, 0, xi, 1)
+        t = _time_fn(lambda: dec.apply(dd.DD_OP_D, 2, 1, stream), 20)
+        dec_res["x".join(map(str, grid))] = {"ms": t * 1e3, "overhead": t / t_single - 1.0,
+                                             "boundary_sites_rank0": dec.info(0)["boundary_sites"]}
+        del dec
+    out["decomposed_D_48c96_f32"] = dec_res
+    del xi, xo
+    torch.cuda.empty_cache()
     # the batch of uneven lattices 8^4 x 1, 16^4 x 5, 24^4 x 17, 32^4 x 32 RHS
     shapes = [(8, 8, 8, 8), (16, 16, 16, 16), (24, 24, 24, 24), (32, 32, 32, 32)]
     nrhs = [1, 5, 17, 32]

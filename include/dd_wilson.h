@@ -312,6 +312,52 @@ int dd_batch_tune(dd_batch* b, const void* const* ins, void* const* outs, void* 
  * afterwards (same pointers required; DD_ERR_ARG otherwise). */
 int dd_apply_batched_graph(dd_batch* b, const void* const* ins, void* const* outs, void* stream);
 
+/* ---- domain decomposition (Sections 2.1, 2.2, Algorithm 3) ----
+ * The lattice of an operator handle split into grid[0] x grid[1] x grid[2] x
+ * grid[3] hyper-rectangular local lattices P_i, one per virtual rank on this
+ * GPU; rank i has lexicographic grid coordinates (T, Z, Y, X; X fastest) and
+ * local site (t, z, y, x) is global site (t + off_T, ..., x + off_X) with
+ * off = coordinate * local extent.  Every global extent must divide into
+ * grid[mu] even local extents.  Each rank holds its own copy of the links,
+ * the self-coupling blocks and A_ee^{-1} of every precision of `op`, native
+ * input, output and work fields (the full-field native layout of its local
+ * lattice) and face buffers.  An apply evaluates the neighbour coupling as
+ * Algorithm 3 does, for every split direction mu: each rank projects the spin
+ * components of its lowest mu slice, (I -/+ gamma_mu) psi (lambda), and of its
+ * highest slice times U_mu(x)^H (chi), 6 complex per site and RHS, sends
+ * lambda to the rank at -mu and chi to the rank at +mu (device-to-device
+ * copies into the receiver's own buffer, on a stream of the handle), computes
+ * its interior sites meanwhile, and finishes the sites next to a seam once
+ * the messages have arrived.  Directions with grid[mu] = 1 wrap inside the
+ * rank.  The results equal the single-domain dd_apply bit for bit where that
+ * runs the one-thread-per-(site, RHS) stencil (one RHS, an odd RHS count, or
+ * FP64), and to rounding otherwise.  `op` must outlive the handle.
+ */
+typedef struct dd_decomp dd_decomp;
+int dd_decomp_create(const dd_clover* op, const int grid[4], dd_decomp** out);
+int dd_decomp_destroy(dd_decomp* d);
+/* Number of ranks (> 0), or a negative status; fills the rank's grid
+ * coordinates, global offset, local extents and number of sites next to a
+ * split seam (each pointer may be NULL). */
+int dd_decomp_info(const dd_decomp* d, int rank, int* coord4, int* offset4, int* local4, int64_t* boundary_sites);
+/* Copy a global native field of precision `prec` (subset 0: full lattice;
+ * 1: odd sites, the Dhat layout) into every rank's input field (scatter), or
+ * every rank's output field back into a global native field (gather, with the
+ * precision and RHS count of the last scatter).  Enqueued on `stream`. */
+int dd_decomp_scatter(dd_decomp* d, int prec, int subset, const void* global_native, int nrhs, void* stream);
+int dd_decomp_gather(dd_decomp* d, int prec, int subset, void* global_native, int nrhs, void* stream);
+/* output = OP input on every rank: DD_OP_D, DD_OP_DH (full fields) or
+ * DD_OP_DHAT, DD_OP_DHAT_H (odd halves; two exchange rounds, one per stencil
+ * launch).  Precision and RHS count of the last scatter.  Enqueued on
+ * `stream`. */
+int dd_decomp_apply(dd_decomp* d, int which, int prec, int nrhs, void* stream);
+/* dots[r] = sum over all ranks of sum_x output_r(x)^H input_r(x) (subset 0
+ * full fields, 1 odd halves): each rank's partial sum over its own sites, then
+ * the sum over ranks in rank order (the allreduce of the Gram-Schmidt inner
+ * products in a decomposed Algorithm 2).  FP64 or FP32 fields; written to
+ * host memory [nrhs][2] after synchronising `stream`. */
+int dd_decomp_dot(dd_decomp* d, int prec, int subset, int nrhs, double* dots_host, void* stream);
+
 /* ---- vector operations on canonical device fields (FP64) ----
  * dots[r] = <a_r, b_r> = sum a_r^H b_r over `nsites` sites, for r < nrhs;
  * written to host memory after synchronising the stream. */

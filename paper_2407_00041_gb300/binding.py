@@ -81,6 +81,13 @@ SIGNATURES = {
     "dd_device_status": (_I, [_P]),
     "dd_gauge_stored_rows": (_I, [_P, _I]),
     "dd_dot_noalloc": (_I, [_P, _P, _L, _I, _P, _P]),
+    "dd_decomp_create": (_I, [_P, _P, _P]),
+    "dd_decomp_destroy": (_I, [_P]),
+    "dd_decomp_info": (_I, [_P, _I, _P, _P, _P, _P]),
+    "dd_decomp_scatter": (_I, [_P, _I, _I, _P, _I, _P]),
+    "dd_decomp_gather": (_I, [_P, _I, _I, _P, _I, _P]),
+    "dd_decomp_apply": (_I, [_P, _I, _I, _I, _P]),
+    "dd_decomp_dot": (_I, [_P, _I, _I, _I, _P, _P]),
 }
 
 _lib = None
@@ -236,3 +243,44 @@ class Operator:
         A = np.empty((self.lattice.V, 12, 12), dtype=np.complex128)
         check(_lib.dd_clover_download(self.h, A.ctypes.data), "dd_clover_download")
         return A
+
+
+class Decomposition:
+    """Virtual-rank domain decomposition of an operator's lattice (dd_decomp)."""
+
+    def __init__(self, op, grid):
+        lib = load()
+        self.op = op
+        self.grid = tuple(int(g) for g in grid)
+        h = ctypes.c_void_p()
+        check(lib.dd_decomp_create(op.h, (ctypes.c_int * 4)(*self.grid), ctypes.byref(h)), "dd_decomp_create")
+        self.h = h
+        self.nranks = self.info(0)["nranks"]
+
+    def info(self, rank):
+        c, o, n = (ctypes.c_int * 4)(), (ctypes.c_int * 4)(), (ctypes.c_int * 4)()
+        nb = ctypes.c_int64()
+        k = _lib.dd_decomp_info(self.h, rank, c, o, n, ctypes.byref(nb))
+        if k < 0:
+            check(k, "dd_decomp_info")
+        return {"nranks": k, "coord": tuple(c), "offset": tuple(o), "local": tuple(n), "boundary_sites": nb.value}
+
+    def scatter(self, prec, subset, native, nrhs, stream=None):
+        check(_lib.dd_decomp_scatter(self.h, prec, subset, _ptr(native), nrhs, _stream(stream)), "dd_decomp_scatter")
+
+    def gather(self, prec, subset, native, nrhs, stream=None):
+        check(_lib.dd_decomp_gather(self.h, prec, subset, _ptr(native), nrhs, _stream(stream)), "dd_decomp_gather")
+
+    def apply(self, which, prec, nrhs, stream=None):
+        check(_lib.dd_decomp_apply(self.h, which, prec, nrhs, _stream(stream)), "dd_decomp_apply")
+
+    def dot(self, prec, subset, nrhs, stream=None):
+        import numpy as np
+        out = np.empty((nrhs, 2), dtype=np.float64)
+        check(_lib.dd_decomp_dot(self.h, prec, subset, nrhs, out.ctypes.data, _stream(stream)), "dd_decomp_dot")
+        return out[:, 0] + 1j * out[:, 1]
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.dd_decomp_destroy(self.h)
+            self.h = None

@@ -63,12 +63,15 @@ __device__ __forceinline__ void bh_times(cx<R> g0, cx<R> g1, cx<R>& b0, cx<R>& b
   }
 }
 
-// acc += (I + T gamma_mu) (x) W psi, W = U (ADJ = false) or U^H (ADJ = true),
-// scaled by `sign` (the time-boundary sign, times any overall factor); the
-// nine elements of U are given in registers.
-template <int MU, int T, bool ADJ, typename R>
-__device__ __forceinline__ void hop_regs(cx<R> acc[12], const cx<R> psi[12], const cx<R> u[9], R sign) {
-  cx<R> h0[3], h1[3];
+// The three stages of one hop, acc += (I + T gamma_mu) (x) W psi with
+// W = U (ADJ = false) or U^H (ADJ = true), scaled by `sign` (the time-boundary
+// sign, times any overall factor).  Split so that a domain-decomposed apply
+// can run the first stage (projection, and for the backward hop the link
+// product) on the rank that owns psi and the rest on the rank that owns the
+// output site, with the same arithmetic as the fused hop.
+// Stage 1: the two independent spin components h = u + T B_mu l.
+template <int MU, int T, typename R>
+__device__ __forceinline__ void hop_project(const cx<R> psi[12], cx<R> h0[3], cx<R> h1[3]) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     cx<R> b0, b1;
@@ -81,7 +84,13 @@ __device__ __forceinline__ void hop_regs(cx<R> acc[12], const cx<R> psi[12], con
       h1[c] = psi[3 + c] - b1;
     }
   }
-  cx<R> g0[3], g1[3];
+}
+
+// Stage 2: g = W h for both spin components (the nine elements of U in
+// registers).
+template <bool ADJ, typename R>
+__device__ __forceinline__ void hop_mul(const cx<R> u[9], const cx<R> h0[3], const cx<R> h1[3], cx<R> g0[3],
+                                        cx<R> g1[3]) {
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     g0[a] = zero<R>();
@@ -97,6 +106,11 @@ __device__ __forceinline__ void hop_regs(cx<R> acc[12], const cx<R> psi[12], con
       }
     }
   }
+}
+
+// Stage 3: reconstruct the lower spin pair as T B_mu^H g and accumulate.
+template <int MU, int T, typename R>
+__device__ __forceinline__ void hop_reconstruct(cx<R> acc[12], const cx<R> g0[3], const cx<R> g1[3], R sign) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     acc[c] = caxpy(sign, g0[c], acc[c]);
@@ -107,6 +121,15 @@ __device__ __forceinline__ void hop_regs(cx<R> acc[12], const cx<R> psi[12], con
     acc[6 + c] = caxpy(sb, b0, acc[6 + c]);
     acc[9 + c] = caxpy(sb, b1, acc[9 + c]);
   }
+}
+
+// All three stages: acc += (I + T gamma_mu) (x) W psi.
+template <int MU, int T, bool ADJ, typename R>
+__device__ __forceinline__ void hop_regs(cx<R> acc[12], const cx<R> psi[12], const cx<R> u[9], R sign) {
+  cx<R> h0[3], h1[3], g0[3], g1[3];
+  hop_project<MU, T, R>(psi, h0, h1);
+  hop_mul<ADJ, R>(u, h0, h1, g0, g1);
+  hop_reconstruct<MU, T, R>(acc, g0, g1, sign);
 }
 
 // Link storage: the 36 elements of a site's four links (direction-major,
@@ -261,58 +284,13 @@ __device__ __forceinline__ void block_apply(const void* M, int64_t s, int64_t Vh
   block_apply_g<PG, false, R>(M, s, Vh, x, out, true);
 }
 
-// The work of one thread: output slot `tid` in [0, npar * Vh * nrhs).  With
-// NORM it returns |out|^2 of the stored FP32 result (summed in FP32 over the
-// 12 components), else 0.
-template <int PG, int PIN, int POUT, bool DAG, int EPI, bool NORM = false>
-__device__ __forceinline__ float hop_thread(const HopArgs& a, int64_t tid) {
-  using R = typename Store<PG>::real;
-  using E = typename Store<PG>::elem;
-  int p, s, r;
-  SiteCoord sc;
-  if (a.npar == 2) {
-    // both parities: threads follow the lexicographic site order, so the two
-    // uses of every link (forward hop at x, backward hop at x + mu) and the
-    // reads of a neighbour spinor fall within about one time slice of traffic
-    const int lex = fdiv((int)tid, a.fblk);
-    r = (int)tid - lex * a.nrhs;
-    sc = traversal_coords(a.g, lex);
-    p = (sc.c[0] + sc.c[1] + sc.c[2] + sc.c[3]) & 1;
-    s = sc.lex >> 1;
-  } else {
-    p = a.p0;
-    s = fdiv((int)tid, a.fblk);
-    r = (int)tid - s * a.nrhs;
-    sc = site_coords(a.g, s, p);
-  }
-  const int q = p ^ 1;
+// Epilogue of the one-thread-per-(site, RHS) stencil: combine the hopping
+// sum acc of output site s (parity p), right-hand side r, with the self
+// coupling as EPI says and store.  With NORM it returns |out|^2 of the stored
+// FP32 result (summed in FP32 over the 12 components), else 0.
+template <int PG, int PIN, int POUT, int EPI, bool NORM, typename R>
+__device__ __forceinline__ float hop_epilogue(const HopArgs& a, int p, int s, int r, cx<R> acc[12]) {
   const int64_t Vh = a.g.Vh;
-  // forward hop: (I - gamma) for D, (I + gamma) for D^H; backward the opposite
-  constexpr int TF = DAG ? +1 : -1;
-  constexpr int TB = -TF;
-
-  cx<R> acc[12];
-#pragma unroll
-  for (int c = 0; c < 12; ++c) acc[c] = zero<R>();
-
-#define DD_HOP_DIR(MU)                                                                     \
-  {                                                                                        \
-    cx<R> psi[12];                                                                         \
-    int nl = nb_fwd(a.g, sc, MU);                                                          \
-    R sg = (MU == 0 && sc.c[0] == a.g.n[0] - 1) ? (R)a.g.t_bc : (R)1;                      \
-    sg *= load_spinor_unscaled<PIN, R>(a.in[q], a.gstride, (int64_t)(nl >> 1) * a.nrhs + r, psi); \
-    hop<PG, MU, TF, false, R>(acc, psi, a.U[p], s, Vh, sg, a.recon);                       \
-    nl = nb_bwd(a.g, sc, MU);                                                              \
-    sg = (MU == 0 && sc.c[0] == 0) ? (R)a.g.t_bc : (R)1;                                   \
-    sg *= load_spinor_unscaled<PIN, R>(a.in[q], a.gstride, (int64_t)(nl >> 1) * a.nrhs + r, psi); \
-    hop<PG, MU, TB, true, R>(acc, psi, a.U[q], nl >> 1, Vh, sg, a.recon);                  \
-  }
-  DD_HOP_DIR(0)
-  DD_HOP_DIR(1)
-  DD_HOP_DIR(2)
-  DD_HOP_DIR(3)
-#undef DD_HOP_DIR
-
   const R beta = (R)a.beta;
   const int64_t i = (int64_t)s * a.nrhs + r;
   const void* M = a.M[p];
@@ -367,6 +345,61 @@ __device__ __forceinline__ float hop_thread(const HopArgs& a, int64_t tid) {
     }
   }
   return n2;
+}
+
+// The work of one thread: output slot `tid` in [0, npar * Vh * nrhs).  With
+// NORM it returns |out|^2 of the stored FP32 result (summed in FP32 over the
+// 12 components), else 0.
+template <int PG, int PIN, int POUT, bool DAG, int EPI, bool NORM = false>
+__device__ __forceinline__ float hop_thread(const HopArgs& a, int64_t tid) {
+  using R = typename Store<PG>::real;
+  using E = typename Store<PG>::elem;
+  int p, s, r;
+  SiteCoord sc;
+  if (a.npar == 2) {
+    // both parities: threads follow the lexicographic site order, so the two
+    // uses of every link (forward hop at x, backward hop at x + mu) and the
+    // reads of a neighbour spinor fall within about one time slice of traffic
+    const int lex = fdiv((int)tid, a.fblk);
+    r = (int)tid - lex * a.nrhs;
+    sc = traversal_coords(a.g, lex);
+    p = (sc.c[0] + sc.c[1] + sc.c[2] + sc.c[3]) & 1;
+    s = sc.lex >> 1;
+  } else {
+    p = a.p0;
+    s = fdiv((int)tid, a.fblk);
+    r = (int)tid - s * a.nrhs;
+    sc = site_coords(a.g, s, p);
+  }
+  const int q = p ^ 1;
+  const int64_t Vh = a.g.Vh;
+  // forward hop: (I - gamma) for D, (I + gamma) for D^H; backward the opposite
+  constexpr int TF = DAG ? +1 : -1;
+  constexpr int TB = -TF;
+
+  cx<R> acc[12];
+#pragma unroll
+  for (int c = 0; c < 12; ++c) acc[c] = zero<R>();
+
+#define DD_HOP_DIR(MU)                                                                     \
+  {                                                                                        \
+    cx<R> psi[12];                                                                         \
+    int nl = nb_fwd(a.g, sc, MU);                                                          \
+    R sg = (MU == 0 && sc.c[0] == a.g.n[0] - 1) ? (R)a.g.t_bc : (R)1;                      \
+    sg *= load_spinor_unscaled<PIN, R>(a.in[q], a.gstride, (int64_t)(nl >> 1) * a.nrhs + r, psi); \
+    hop<PG, MU, TF, false, R>(acc, psi, a.U[p], s, Vh, sg, a.recon);                       \
+    nl = nb_bwd(a.g, sc, MU);                                                              \
+    sg = (MU == 0 && sc.c[0] == 0) ? (R)a.g.t_bc : (R)1;                                   \
+    sg *= load_spinor_unscaled<PIN, R>(a.in[q], a.gstride, (int64_t)(nl >> 1) * a.nrhs + r, psi); \
+    hop<PG, MU, TB, true, R>(acc, psi, a.U[q], nl >> 1, Vh, sg, a.recon);                  \
+  }
+  DD_HOP_DIR(0)
+  DD_HOP_DIR(1)
+  DD_HOP_DIR(2)
+  DD_HOP_DIR(3)
+#undef DD_HOP_DIR
+
+  return hop_epilogue<PG, PIN, POUT, EPI, NORM, R>(a, p, s, r, acc);
 }
 
 // RHS-blocked variant for several right-hand sides (three-row links only): one thread handles NB
