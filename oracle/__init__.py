@@ -14,6 +14,9 @@ Contents and the passage each part follows:
     from the block form of D), the su(3) force projection wrapper.
   * ``fgmres.py``: Algorithm 2 (FGMRES) and Algorithm 1 (right-preconditioned
     GMRES), Section 1.2.
+  * ``sap.py``: the Schwarz alternating procedure named in Section 1.3 (red-black
+    multiplicative Schwarz with minimal-residual block solves), the smoother
+    and flexible preconditioner M_j.
 
 Array conventions (same as ``synthetic``):
   dims = (nT, nZ, nY, nX); psi [V, 4, 3] (or [V, 12]); U [V, 4, 3, 3];
