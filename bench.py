@@ -449,7 +449,8 @@ def extra_measurements(dd, torch, stream, op48, psi48, V48, tdist, clocks, alu_p
         ins.append(xi)
         outs.append(torch.empty_like(xi))
         del x
-    # multi-RHS at 32^4 x 12 (the first 12 of the 32 RHS) in FP32 and FP16
+    # multi-RHS at 32^4 x 12 (the first 12 of the 32 RHS) in FP32 and FP16:
+    # the paired-RHS layout (packed FP32x2 stencil) and the native layout
     lat32, g32, o32 = keep[3]
     V32 = lat32.V
     x12 = torch.from_numpy(synthetic.spinor(shapes[3], nrhs=12)).cuda()
@@ -458,12 +459,34 @@ def extra_measurements(dd, torch, stream, op48, psi48, V48, tdist, clocks, alu_p
         xi = torch.empty(nb, dtype=torch.uint8, device="cuda")
         xo = torch.empty_like(xi)
         o32.pack(p, 0, x12, xi, 12)
+        t_nat = _time_fn(lambda: dd.check(dd.lib.dd_apply(o32.h, dd.DD_OP_D, p, xi.data_ptr(), xo.data_ptr(), 12,
+                                                          dd.DD_LAYOUT_NATIVE, st), "D 12 RHS"), 20)
+        o32.pack_paired(p, 0, x12, xi, 12)
         t = _time_fn(lambda: dd.check(dd.lib.dd_apply(o32.h, dd.DD_OP_D, p, xi.data_ptr(), xo.data_ptr(), 12,
-                                                      dd.DD_LAYOUT_NATIVE, st), "D 12 RHS"), 20)
+                                                      dd.DD_LAYOUT_NATIVE_PAIRED, st), "D 12 RHS paired"), 20)
         out[f"mrhs_32x4_12rhs_{name}"] = {"ms": t * 1e3, "gbs": bytes_per_site(name, 12) * V32 / t / 1e9,
                                           "site_rhs_per_s": V32 * 12 / t,
-                                          "hbm_frac": bytes_per_site(name, 12) * V32 / t / 1e9 / HBM_PEAK[0]}
+                                          "hbm_frac": bytes_per_site(name, 12) * V32 / t / 1e9 / HBM_PEAK[0],
+                                          "layout": "paired-RHS (packed FP32x2 stencil)",
+                                          "ms_native_layout": t_nat * 1e3}
+        del xi, xo
     del x12
+    # two right-hand sides on the 48^3 x 96 lattice, paired layout
+    x2 = torch.from_numpy(synthetic.spinor(DIMS, nrhs=2)).cuda()
+    for name, p in (("f32", 2), ("f16", 4)):
+        nb = op48.field_bytes(p, 0, 2)
+        xi = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        xo = torch.empty_like(xi)
+        op48.pack_paired(p, 0, x2, xi, 2)
+        t = _time_fn(lambda: dd.check(dd.lib.dd_apply(op48.h, dd.DD_OP_D, p, xi.data_ptr(), xo.data_ptr(), 2,
+                                                      dd.DD_LAYOUT_NATIVE_PAIRED, st), "D 2 RHS paired"), 20)
+        out[f"mrhs_48c96_2rhs_{name}"] = {"ms": t * 1e3, "gbs": bytes_per_site(name, 2) * V48 / t / 1e9,
+                                          "site_rhs_per_s": V48 * 2 / t,
+                                          "hbm_frac": bytes_per_site(name, 2) * V48 / t / 1e9 / HBM_PEAK[0],
+                                          "layout": "paired-RHS (packed FP32x2 stencil)"}
+        del xi, xo
+    del x2
+    torch.cuda.empty_cache()
     # batched uneven lattices, FP32
     arr = lambda v, t=ctypes.c_void_p: (t * len(v))(*v)
     b = ctypes.c_void_p()

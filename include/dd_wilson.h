@@ -34,6 +34,10 @@
  *                             returns after the result has reached the host.
  *   DD_LAYOUT_NATIVE          device memory in the library's native layout for
  *                             the precision (see dd_field_bytes).
+ *   DD_LAYOUT_NATIVE_PAIRED   device memory in the paired-RHS layout (FP32 and
+ *                             FP16 only, nrhs even; same bytes as native):
+ *                             the same component of RHS 2j and 2j + 1 side by
+ *                             side, for the packed FP32x2 stencil.
  *   For the full-lattice operators (DD_OP_D, DD_OP_DH) nsites = V.  For the
  *   even-odd operators (DD_OP_DHAT, DD_OP_DHAT_H) fields live on odd sites
  *   only: nsites = V/2, in increasing lexicographic order.
@@ -48,6 +52,16 @@
  *                    components 4c .. 4c + 3, divided by the site scale),
  *                    then [Vh][N] float scales (max |re|, |im| over the 24 reals).
  *   A full field is the even half field followed by the odd half field.
+ * Paired-RHS layout (nrhs = N even, NP = N / 2; pair j holds RHS 2j and 2j + 1):
+ *   FP32 half field: [12 components][Vh][NP] of float4
+ *                    (re RHS 2j, re RHS 2j + 1, im RHS 2j, im RHS 2j + 1).
+ *   FP16 half field: [6 component pairs][Vh][NP] of 4 half2 (re and im of
+ *                    component 2c, then of 2c + 1; each half2 holds RHS 2j and
+ *                    2j + 1, divided by their own site scales), then [Vh][N]
+ *                    float scales as in the native FP16 layout.
+ *   Full fields as for the native layout.  Canonical applies of D, D^H, Dhat
+ *   and Dhat^H with an even nrhs in FP32 or FP16 run on this layout
+ *   internally; the result is bit-identical to the native-layout apply.
  *
  * Ownership: handles own the device memory they allocate.  Field pointers
  * passed to calls belong to the caller and are never freed or retained.
@@ -62,7 +76,9 @@
  *   DD_RECON=0          no two-row FP32 link copy at dd_gauge_create (the
  *                       single-RHS kernels then read three rows).
  *   DD_RHS_BLOCK=n      largest RHS block of the multi-RHS stencil (1, 2 or
- *                       4; default 4; 1 gives one thread per site and RHS).
+ *                       4; default 4; 1 gives one thread per site and RHS,
+ *                       also for canonical applies, which otherwise take the
+ *                       paired-RHS stencil for an even nrhs).
  *   DD_ZBLOCK=d         Z-slab depth of the traversal (a divisor of nZ; 0 =
  *                       nZ); default: the deepest slab within 30 MB.
  *   DD_HOST_CHUNKS=c    time-slice chunks of the pipelined host-buffer
@@ -71,7 +87,8 @@
  *                       from separate reductions instead of the stencil
  *                       launch (read at each dd_solve).
  *   DD_STAGE=1          opt-in row-staged stencil for full-lattice FP32
- *                       applies (slower; DD_STAGE_SLOTS sets its ring depth,
+ *                       applies (canonical applies then keep the native
+ *                       layout; slower; DD_STAGE_SLOTS sets its ring depth,
  *                       DD_STAGE_NARROW=1 allows its narrow-row variant,
  *                       DD_STAGE_WAIT_TEST=1 makes one of its waits expire
  *                       so that tests can check dd_device_status).
@@ -112,6 +129,7 @@ extern "C" {
 #define DD_LAYOUT_CANONICAL 0
 #define DD_LAYOUT_CANONICAL_HOST 1
 #define DD_LAYOUT_NATIVE 2
+#define DD_LAYOUT_NATIVE_PAIRED 3
 
 typedef struct dd_lattice dd_lattice;
 typedef struct dd_gauge dd_gauge;
@@ -209,6 +227,13 @@ size_t dd_field_bytes(const dd_clover* op, int prec, int subset, int nrhs);
  */
 int dd_pack(const dd_clover* op, int prec, int subset, const double* canon, void* native, int nrhs, void* stream);
 int dd_unpack(const dd_clover* op, int prec, int subset, const void* native, double* canon, int nrhs, void* stream);
+/* The same for the paired-RHS layout (prec DD_PREC_F32 or DD_PREC_F16, nrhs
+ * even and >= 2; DD_ERR_ARG otherwise).  The layout itself is not in the
+ * thesis: it serves the packed FP32x2 stencil of dd_apply. */
+int dd_pack_paired(const dd_clover* op, int prec, int subset, const double* canon, void* paired, int nrhs,
+                   void* stream);
+int dd_unpack_paired(const dd_clover* op, int prec, int subset, const void* paired, double* canon, int nrhs,
+                     void* stream);
 
 /*
  * out = OP in for `nrhs` right-hand sides at precision `prec` (the precision
@@ -217,6 +242,12 @@ int dd_unpack(const dd_clover* op, int prec, int subset, const void* native, dou
  * (odd sites).  in and out must not overlap.  Canonical layouts are converted
  * to and from the native layout inside the call, using workspace owned by the
  * operator handle (allocated on first use and kept).
+ * DD_LAYOUT_NATIVE_PAIRED (DD_OP_D, DD_OP_DH, DD_OP_DHAT, DD_OP_DHAT_H with
+ * prec DD_PREC_F32 or DD_PREC_F16 and an even nrhs) runs the packed FP32x2
+ * stencil: one thread per output site and pair of right-hand sides, each
+ * arithmetic step the FP32 operation of the native-layout kernel (results are
+ * bit-identical); DD_ERR_ARG for an odd nrhs or another precision,
+ * DD_ERR_UNSUPPORTED for DD_OP_SC.
  * Enqueued on `stream`; DD_LAYOUT_CANONICAL_HOST synchronises it.
  */
 int dd_apply(dd_clover* op, int which, int prec, const void* in, void* out, int nrhs, int layout, void* stream);

@@ -16,7 +16,7 @@ DD_ERR_ARG, DD_ERR_OOM, DD_ERR_CUDA, DD_ERR_SINGULAR = -1, -2, -3, -4
 DD_ERR_NOT_CONVERGED, DD_ERR_TIMEOUT, DD_ERR_UNSUPPORTED = -5, -6, -7
 DD_PREC_F64, DD_PREC_F32, DD_PREC_F16 = 1, 2, 4
 DD_OP_D, DD_OP_DH, DD_OP_DHAT, DD_OP_DHAT_H, DD_OP_SC = 0, 1, 2, 3, 4
-DD_LAYOUT_CANONICAL, DD_LAYOUT_CANONICAL_HOST, DD_LAYOUT_NATIVE = 0, 1, 2
+DD_LAYOUT_CANONICAL, DD_LAYOUT_CANONICAL_HOST, DD_LAYOUT_NATIVE, DD_LAYOUT_NATIVE_PAIRED = 0, 1, 2, 3
 
 DD_PRECOND_NONE, DD_PRECOND_NORMAL, DD_PRECOND_CGNR = 0, 1, 2
 PREC = {"f64": DD_PREC_F64, "f32": DD_PREC_F32, "f16": DD_PREC_F16}
@@ -67,6 +67,8 @@ SIGNATURES = {
     "dd_field_bytes": (_S, [_P, _I, _I, _I]),
     "dd_pack": (_I, [_P, _I, _I, _P, _P, _I, _P]),
     "dd_unpack": (_I, [_P, _I, _I, _P, _P, _I, _P]),
+    "dd_pack_paired": (_I, [_P, _I, _I, _P, _P, _I, _P]),
+    "dd_unpack_paired": (_I, [_P, _I, _I, _P, _P, _I, _P]),
     "dd_apply": (_I, [_P, _I, _I, _P, _P, _I, _I, _P]),
     "dd_solve_params_default": (None, [_P]),
     "dd_solve": (_I, [_P, _P, _P, _P, _I, _I, _P, _P]),
@@ -215,6 +217,14 @@ class Operator:
 
     def unpack(self, prec, subset, native, canon, nrhs, stream=None):
         check(_lib.dd_unpack(self.h, prec, subset, _ptr(native), _ptr(canon), nrhs, _stream(stream)), "dd_unpack")
+
+    def pack_paired(self, prec, subset, canon, paired, nrhs, stream=None):
+        check(_lib.dd_pack_paired(self.h, prec, subset, _ptr(canon), _ptr(paired), nrhs, _stream(stream)),
+              "dd_pack_paired")
+
+    def unpack_paired(self, prec, subset, paired, canon, nrhs, stream=None):
+        check(_lib.dd_unpack_paired(self.h, prec, subset, _ptr(paired), _ptr(canon), nrhs, _stream(stream)),
+              "dd_unpack_paired")
 
     # -- operators
     def apply(self, which, prec, inp, out, nrhs, layout=DD_LAYOUT_CANONICAL, stream=None):

@@ -343,11 +343,36 @@ int dd_unpack(const dd_clover* op, int prec, int subset, const void* native, dou
   return unpack(op->lat, prec, subset, f, canon, as_stream(stream));
 }
 
+int dd_pack_paired(const dd_clover* op, int prec, int subset, const double* canon, void* paired, int nrhs,
+                   void* stream) {
+  if (!op || !canon || !paired || nrhs < 2 || nrhs % 2 != 0)
+    return fail(DD_ERR_ARG, "null argument or nrhs not even and >= 2");
+  if ((prec != DD_PREC_F32 && prec != DD_PREC_F16) || subset < 0 || subset > 2)
+    return fail(DD_ERR_ARG, "paired layout: precision F32 or F16, subset 0..2");
+  Field f = field_view(op->lat, prec, subset, paired, nrhs, 1);
+  return pack(op->lat, prec, subset, canon, f, as_stream(stream));
+}
+
+int dd_unpack_paired(const dd_clover* op, int prec, int subset, const void* paired, double* canon, int nrhs,
+                     void* stream) {
+  if (!op || !canon || !paired || nrhs < 2 || nrhs % 2 != 0)
+    return fail(DD_ERR_ARG, "null argument or nrhs not even and >= 2");
+  if ((prec != DD_PREC_F32 && prec != DD_PREC_F16) || subset < 0 || subset > 2)
+    return fail(DD_ERR_ARG, "paired layout: precision F32 or F16, subset 0..2");
+  Field f = field_view(op->lat, prec, subset, const_cast<void*>(paired), nrhs, 1);
+  return unpack(op->lat, prec, subset, f, canon, as_stream(stream));
+}
+
 int dd_apply(dd_clover* op, int which, int prec, const void* in, void* out, int nrhs, int layout, void* stream) {
   if (!op || !in || !out || nrhs < 1) return fail(DD_ERR_ARG, "null argument or nrhs < 1");
   if (!valid_prec(prec)) return fail(DD_ERR_ARG, "bad precision");
   if (which < DD_OP_D || which > DD_OP_SC) return fail(DD_ERR_ARG, "bad operator");
-  if (layout < DD_LAYOUT_CANONICAL || layout > DD_LAYOUT_NATIVE) return fail(DD_ERR_ARG, "bad layout");
+  if (layout < DD_LAYOUT_CANONICAL || layout > DD_LAYOUT_NATIVE_PAIRED) return fail(DD_ERR_ARG, "bad layout");
+  if (layout == DD_LAYOUT_NATIVE_PAIRED) {
+    if (nrhs % 2 != 0 || (prec != DD_PREC_F32 && prec != DD_PREC_F16))
+      return fail(DD_ERR_ARG, "paired layout: precision F32 or F16 and an even nrhs");
+    if (which == DD_OP_SC) return fail(DD_ERR_UNSUPPORTED, "paired layout: D, D^H, Dhat and Dhat^H only");
+  }
   const int pi = prec_index(prec);
   if (!op->gauge->links[pi].ptr || !op->clov[pi].ptr)
     return fail(DD_ERR_UNSUPPORTED, "precision not created in the gauge/operator handles");
@@ -361,15 +386,21 @@ int dd_apply(dd_clover* op, int which, int prec, const void* in, void* out, int 
     return apply_host_pipelined(op, prec, which == DD_OP_DH, in, out, nrhs, st);
   Field fin, fout;
   const double* cin = nullptr;
-  if (layout == DD_LAYOUT_NATIVE) {
-    fin = field_view(lat, prec, subset, const_cast<void*>(in), nrhs);
-    fout = field_view(lat, prec, subset, out, nrhs);
+  // canonical fields with an even RHS count go through the paired-RHS stencil
+  // (bit-identical to the RHS-blocked one; DD_RHS_BLOCK=1 keeps one thread
+  // per site and RHS, DD_STAGE=1 the row-staged stencil)
+  const int paired = layout == DD_LAYOUT_NATIVE_PAIRED ||
+                     (layout != DD_LAYOUT_NATIVE && nrhs % 2 == 0 && which != DD_OP_SC &&
+                      (prec == DD_PREC_F32 || prec == DD_PREC_F16) && rhs_block_limit() >= 2 && !stage_opted_in());
+  if (layout == DD_LAYOUT_NATIVE || layout == DD_LAYOUT_NATIVE_PAIRED) {
+    fin = field_view(lat, prec, subset, const_cast<void*>(in), nrhs, paired);
+    fout = field_view(lat, prec, subset, out, nrhs, paired);
   } else {
     DD_TRY(stage_in(op->ws_canon_in, in, cb, layout, &cin, st));
     DD_TRY(op->ws_in.ensure(nb));
     DD_TRY(op->ws_out.ensure(nb));
-    fin = field_view(lat, prec, subset, op->ws_in.ptr, nrhs);
-    fout = field_view(lat, prec, subset, op->ws_out.ptr, nrhs);
+    fin = field_view(lat, prec, subset, op->ws_in.ptr, nrhs, paired);
+    fout = field_view(lat, prec, subset, op->ws_out.ptr, nrhs, paired);
     DD_TRY(pack(lat, prec, subset, cin, fin, st));
   }
   switch (which) {
@@ -382,11 +413,11 @@ int dd_apply(dd_clover* op, int which, int prec, const void* in, void* out, int 
       break;
     default: {
       DD_TRY(op->ws_tmp.ensure(field_bytes(lat, prec, 2, nrhs)));
-      Field tmp = field_view(lat, prec, 2, op->ws_tmp.ptr, nrhs);
+      Field tmp = field_view(lat, prec, 2, op->ws_tmp.ptr, nrhs, paired);
       DD_TRY(op_Dhat(op, prec, prec, which == DD_OP_DHAT_H, fin, fout, tmp, st));
     }
   }
-  if (layout != DD_LAYOUT_NATIVE) {
+  if (layout != DD_LAYOUT_NATIVE && layout != DD_LAYOUT_NATIVE_PAIRED) {
     double* cout = reinterpret_cast<double*>(out);
     if (layout == DD_LAYOUT_CANONICAL_HOST) {
       DD_TRY(op->ws_canon_out.ensure(cb));

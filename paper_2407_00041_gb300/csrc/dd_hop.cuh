@@ -556,18 +556,6 @@ __global__ void __launch_bounds__(128) k_block(const BlockArgs a) {
   store_spinor<POUT, R>(a.out[p], a.gstride, tid, res);
 }
 
-// Largest RHS block of the RHS-blocked stencil (DD_RHS_BLOCK overrides: 1
-// disables it).
-inline int rhs_block_limit() {
-  static int v = 0;
-  if (v == 0) {
-    const char* e = getenv("DD_RHS_BLOCK");
-    v = e ? atoi(e) : 4;
-    if (v < 1) v = 1;
-  }
-  return v;
-}
-
 }  // namespace dd
 
 #include "dd_stage.cuh"

@@ -109,11 +109,13 @@ struct Field {
   HalfField h[2];
   int prec = 0;
   int nrhs = 1;
+  int paired = 0;  // paired-RHS layout (dd_pair.cuh): FP32 / FP16, nrhs even
 };
 
 // Build a Field view of a native buffer.  subset: 0 full (even then odd),
 // 1 odd sites only, 2 even sites only.
-Field field_view(const dd_lattice* lat, int prec, int subset, void* base, int nrhs);
+// paired = 1: the paired-RHS layout, which takes the same bytes.
+Field field_view(const dd_lattice* lat, int prec, int subset, void* base, int nrhs, int paired = 0);
 size_t field_bytes(const dd_lattice* lat, int prec, int subset, int nrhs);
 
 // ---- operator layer (all enqueue on `st`) ----

@@ -68,10 +68,11 @@ static HalfField half_view(const dd_lattice* lat, int prec, char* base, int nrhs
   return h;
 }
 
-Field field_view(const dd_lattice* lat, int prec, int subset, void* base, int nrhs) {
+Field field_view(const dd_lattice* lat, int prec, int subset, void* base, int nrhs, int paired) {
   Field f;
   f.prec = prec;
   f.nrhs = nrhs;
+  f.paired = paired;
   char* b = reinterpret_cast<char*>(base);
   const size_t hb = field_bytes(lat, prec, 1, nrhs);
   f.h[0] = HalfField{nullptr, nullptr};
@@ -131,6 +132,20 @@ namespace {
 
 int run_hop(int pg, int pv, const HopArgs& a, bool dag, int epi, cudaStream_t st) {
   cudaError_t e;
+  if (a.paired) {
+    if (a.nrhs % 2 != 0 || (epi != EPI_D && epi != EPI_AINV))
+      return fail(DD_ERR_UNSUPPORTED, "paired layout: an even RHS count and the D / Dhat stencils only");
+    if (pg == P32 && pv == P32)
+      e = launch_hop_pair<P32, P32>(a, dag, epi, st);
+    else if (pg == P16 && pv == P16)
+      e = launch_hop_pair<P16, P16>(a, dag, epi, st);
+    else if (pg == P16 && pv == P32)
+      e = launch_hop_pair<P16, P32>(a, dag, epi, st);
+    else
+      return fail(DD_ERR_UNSUPPORTED, "paired layout: FP32 or FP16 only");
+    if (e != cudaSuccess) return cuda_fail(e, "paired stencil launch");
+    return DD_OK;
+  }
   if (pg == P64 && pv == P64)
     e = launch_hop<P64, P64, P64>(a, dag, epi, st);
   else if (pg == P32 && pv == P32)
@@ -171,6 +186,7 @@ HopArgs base_args(const dd_clover* op, int pg, int nrhs) {
   }
   a.beta = -0.5;
   a.rhs_block = 1;
+  a.paired = 0;
   // single right-hand side: the two-row FP32 links (fewer bytes; the
   // RHS-blocked kernels of several RHS are faster with three rows)
   a.recon = pg == P32 && nrhs == 1 && op->gauge->recon32;
@@ -186,7 +202,9 @@ HopArgs base_args(const dd_clover* op, int pg, int nrhs) {
 // D (or D^H) on the full lattice: out_p = A_pp in_p - 1/2 H_{p,1-p} in_{1-p}
 int op_D(const dd_clover* op, int pg, int pv, bool dagger, const Field& in, const Field& out, cudaStream_t st) {
   DD_TRY(check_prec(op, pg));
+  if (in.paired != out.paired) return fail(DD_ERR_ARG, "input and output layouts differ");
   HopArgs a = base_args(op, pg, in.nrhs);
+  a.paired = in.paired;
   for (int p = 0; p < 2; ++p) {
     a.in[p] = in.h[p];
     a.y[p] = in.h[p];
@@ -263,11 +281,13 @@ static void dhat_args(const dd_clover* op, int pg, const Field& in, const Field&
   b.y[1] = in.h[1];
   b.out[1] = out.h[1];
   b.beta = -0.5;
+  a.paired = b.paired = in.paired;
 }
 
 int op_Dhat(const dd_clover* op, int pg, int pv, bool dagger, const Field& in, const Field& out, const Field& tmp,
             cudaStream_t st) {
   DD_TRY(check_prec(op, pg));
+  if (in.paired != out.paired || in.paired != tmp.paired) return fail(DD_ERR_ARG, "field layouts differ");
   HopArgs a, b;
   dhat_args(op, pg, in, out, tmp, a, b);
   DD_TRY(run_hop(pg, pv, a, dagger, EPI_AINV, st));

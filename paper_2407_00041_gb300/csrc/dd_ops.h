@@ -3,6 +3,8 @@
 // once per precision triple in dd_hop_*.cu).
 #pragma once
 
+#include <cstdlib>
+
 #include "dd_device.cuh"
 
 namespace dd {
@@ -31,6 +33,7 @@ struct HopArgs {
   int rhs_block;  // batched launch: right-hand sides per thread (1 or 2)
   FastDiv fblk;   // division of the thread index by the RHS slots per site (set by the launcher)
   int recon;      // FP32 links stored as rows 0 and 1 (the third row is rebuilt)
+  int paired;     // fields in the paired-RHS layout (dd_pair.cuh; nrhs even, FP32 / FP16)
 };
 
 // Self-coupling apply without hopping: out = M y on npar parities.
@@ -43,8 +46,32 @@ struct BlockArgs {
   const void* M[2];
 };
 
+// Largest RHS block of the RHS-blocked stencils (DD_RHS_BLOCK overrides: 1
+// disables them, including the paired-RHS stencil of canonical applies).
+inline int rhs_block_limit() {
+  static int v = 0;
+  if (v == 0) {
+    const char* e = getenv("DD_RHS_BLOCK");
+    v = e ? atoi(e) : 4;
+    if (v < 1) v = 1;
+  }
+  return v;
+}
+
+// DD_STAGE=1 opts in to the row-staged stencil of native-layout FP32 applies
+// (dd_stage.cuh); canonical applies then keep the native layout.
+inline bool stage_opted_in() {
+  static const int v = getenv("DD_STAGE") ? atoi(getenv("DD_STAGE")) : 0;
+  return v != 0;
+}
+
 template <int PG, int PIN, int POUT>
 cudaError_t launch_hop(const HopArgs& a, bool dagger, int epi, cudaStream_t st);
+// The paired-RHS stencil (dd_hop_pair.cuh): EPI_D or EPI_AINV on paired fields
+// with nrhs even; PV is the vector precision (P32 or P16), PG that of links
+// and blocks (instantiated for (P32, P32), (P16, P16) and (P16, P32)).
+template <int PG, int PV>
+cudaError_t launch_hop_pair(const HopArgs& a, bool dagger, int epi, cudaStream_t st);
 // traversal slab depth for a lattice and the bytes per site of the stencil (dd_ops.cu)
 int zblock_for(const int dims[4], int64_t bytes_per_site);
 // Device flag that kernels with bounded waits set when a wait expires (one

@@ -3,6 +3,7 @@
 // conversion.
 #include <cstring>
 
+#include "dd_pair.cuh"
 #include "dd_internal.h"
 
 namespace dd {
@@ -574,6 +575,59 @@ __global__ void k_unpack(PackArgs a, double2* canon) {
   for (int c = 0; c < 12; ++c) dst[c] = make_double2((double)v[c].re, (double)v[c].im);
 }
 
+// The paired-RHS layouts (dd_pair.cuh): one thread per (site, RHS pair j),
+// which holds RHS 2j and 2j + 1; a.gstride = Vh * nrhs / 2.
+template <int P>
+__global__ void k_pack_pair(PackArgs a, const double2* __restrict__ canon) {
+  const int NP = a.nrhs >> 1;
+  const int64_t nper = a.ns * NP;
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nper * a.npar) return;
+  int p = a.p0;
+  if (t >= nper) {
+    t -= nper;
+    p ^= 1;
+  }
+  t += a.s0 * NP;
+  const int64_t s = t / NP;
+  const int j = (int)(t - s * NP);
+  const double2* sa = canon + canon_offset(a, p, s, 2 * j);
+  const double2* sb = canon + canon_offset(a, p, s, 2 * j + 1);
+  cx2 v[12];
+#pragma unroll
+  for (int c = 0; c < 12; ++c) {
+    const double2 da = sa[c], db = sb[c];
+    v[c].re = make_float2((float)da.x, (float)db.x);
+    v[c].im = make_float2((float)da.y, (float)db.y);
+  }
+  store_pair<P, false>(a.h[p], a.gstride, t, v);
+}
+
+template <int P>
+__global__ void k_unpack_pair(PackArgs a, double2* canon) {
+  const int NP = a.nrhs >> 1;
+  const int64_t nper = a.ns * NP;
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nper * a.npar) return;
+  int p = a.p0;
+  if (t >= nper) {
+    t -= nper;
+    p ^= 1;
+  }
+  t += a.s0 * NP;
+  const int64_t s = t / NP;
+  const int j = (int)(t - s * NP);
+  cx2 v[12];
+  const float2 sc = load_pair<P>(a.h[p], a.gstride, t, v);
+  double2* da = canon + canon_offset(a, p, s, 2 * j);
+  double2* db = canon + canon_offset(a, p, s, 2 * j + 1);
+#pragma unroll
+  for (int c = 0; c < 12; ++c) {
+    da[c] = make_double2((double)(v[c].re.x * sc.x), (double)(v[c].im.x * sc.x));
+    db[c] = make_double2((double)(v[c].re.y * sc.y), (double)(v[c].im.y * sc.y));
+  }
+}
+
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 PackArgs pack_args(const dd_lattice* lat, int subset, const Field& f) {
@@ -704,8 +758,19 @@ int pack(const dd_lattice* lat, int prec, int subset, const double* canon, const
     a.s0 = t0 * slice / 2;
     a.ns = nt * slice / 2;
   }
-  const int64_t n = a.ns * f.nrhs * a.npar;
   const double2* c = reinterpret_cast<const double2*>(canon);
+  if (f.paired) {
+    if (f.nrhs % 2 != 0 || (prec != P32 && prec != P16)) return fail(DD_ERR_ARG, "paired layout: FP32 / FP16, even nrhs");
+    a.gstride = lat->Vh * (f.nrhs / 2);
+    const int64_t np = a.ns * (f.nrhs / 2) * a.npar;
+    if (prec == P32)
+      k_pack_pair<P32><<<nblk(np, 128), 128, 0, st>>>(a, c);
+    else
+      k_pack_pair<P16><<<nblk(np, 128), 128, 0, st>>>(a, c);
+    DD_CUDA(cudaGetLastError());
+    return DD_OK;
+  }
+  const int64_t n = a.ns * f.nrhs * a.npar;
   if (prec == P64)
     k_pack<P64><<<nblk(n, 128), 128, 0, st>>>(a, c);
   else if (prec == P32)
@@ -724,8 +789,19 @@ int unpack(const dd_lattice* lat, int prec, int subset, const Field& f, double* 
     a.s0 = t0 * slice / 2;
     a.ns = nt * slice / 2;
   }
-  const int64_t n = a.ns * f.nrhs * a.npar;
   double2* c = reinterpret_cast<double2*>(canon);
+  if (f.paired) {
+    if (f.nrhs % 2 != 0 || (prec != P32 && prec != P16)) return fail(DD_ERR_ARG, "paired layout: FP32 / FP16, even nrhs");
+    a.gstride = lat->Vh * (f.nrhs / 2);
+    const int64_t np = a.ns * (f.nrhs / 2) * a.npar;
+    if (prec == P32)
+      k_unpack_pair<P32><<<nblk(np, 128), 128, 0, st>>>(a, c);
+    else
+      k_unpack_pair<P16><<<nblk(np, 128), 128, 0, st>>>(a, c);
+    DD_CUDA(cudaGetLastError());
+    return DD_OK;
+  }
+  const int64_t n = a.ns * f.nrhs * a.npar;
   if (prec == P64)
     k_unpack<P64><<<nblk(n, 128), 128, 0, st>>>(a, c);
   else if (prec == P32)

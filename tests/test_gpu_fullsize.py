@@ -95,6 +95,36 @@ def test_32c4_twelve_rhs_sampled():
             del out
 
 
+def test_32c4_twelve_rhs_paired_layout_sampled():
+    """The bench's multi-RHS launch: the paired-RHS layout at 32^4 x 12 (FP32,
+    FP16 storage), D and D^H, sampled against the oracle, and bit-identical to
+    the native-layout apply on every site."""
+    dims = (32, 32, 32, 32)
+    n = 12
+    U = synthetic.gauge(dims, eps=EPS)
+    psi = synthetic.spinor(dims, nrhs=n)
+    lat = dd.Lattice(dims, -1)
+    g = dd.Gauge(lat, U)
+    op = dd.Operator(g, M0, CSW)
+    psi_dev = torch.from_numpy(psi).cuda()
+    sites = _sample(dims, 5000, 3)
+    nb = op.field_bytes(dd.DD_PREC_F32, 0, n)
+    xi = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    xo = torch.empty_like(xi)
+    for prec in (dd.DD_PREC_F32, dd.DD_PREC_F16):
+        for which in (dd.DD_OP_D, dd.DD_OP_DH):
+            out = torch.empty_like(psi_dev)
+            op.pack_paired(prec, 0, psi_dev, xi, n)
+            op.apply(which, prec, xi, xo, n, dd.DD_LAYOUT_NATIVE_PAIRED)
+            op.unpack_paired(prec, 0, xo, out, n)
+            ref = _native_apply(op, prec, psi_dev, n, which)
+            assert torch.equal(out, ref)
+            del ref
+            if which == dd.DD_OP_D:
+                _check_sites(U, dims, psi, out, sites, (0, 5, n - 1), TOL[prec])
+            del out
+
+
 def test_batch_of_uneven_lattices_full_size():
     shapes = [(8, 8, 8, 8), (16, 16, 16, 16), (24, 24, 24, 24), (32, 32, 32, 32)]
     nrhs = [1, 5, 17, 32]
