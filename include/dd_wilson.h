@@ -264,17 +264,23 @@ typedef struct {
   int verbose;         /* 1: print progress lines to stderr */
   int precond;         /* preconditioner M_j of Algorithm 2: DD_PRECOND_NONE (M = I),
                           DD_PRECOND_NORMAL (M^{-1} = A^H, so A M^{-1} = A A^H is Hermitian
-                          positive definite and restarted FGMRES cannot stagnate) or
-                          DD_PRECOND_CGNR (flexible: CG steps on the normal equations) */
+                          positive definite and restarted FGMRES cannot stagnate),
+                          DD_PRECOND_CGNR (flexible: CG steps on the normal equations) or
+                          DD_PRECOND_SAP (flexible: Schwarz cycles, see dd_sap) */
   int gs_passes;       /* classical Gram-Schmidt passes per Arnoldi step: 1, or 2 (re-orthogonalised) */
   int rhs_batch;       /* even-odd solves: right-hand sides solved together (0 = all); smaller
                           batches need proportionally less device memory */
   int precond_iters;   /* DD_PRECOND_CGNR: conjugate-gradient steps per preconditioner application */
+  int sap_block[4];    /* DD_PRECOND_SAP: block extents (T, Z, Y, X), as for dd_sap */
+  int sap_cycles;      /* DD_PRECOND_SAP: red-black cycles per preconditioner application */
+  int sap_mr_steps;    /* DD_PRECOND_SAP: minimal-residual steps per block solve */
 } dd_solve_params;
 
 #define DD_PRECOND_NONE 0
 #define DD_PRECOND_NORMAL 1
 #define DD_PRECOND_CGNR 2  /* flexible M_j: precond_iters CG steps on A^H A z = A^H v_j */
+#define DD_PRECOND_SAP 3   /* flexible M_j: sap_cycles Schwarz cycles on D (even-odd: the odd half of
+                              the cycles applied to (0, v_j), D^{-1}'s odd-odd block being Dhat^{-1}) */
 
 typedef struct {
   int converged;             /* 1 if every right-hand side met tol */
@@ -289,7 +295,7 @@ typedef struct {
 
 /* Fill `p` with defaults: tol 1e-10, restart 30, max_restarts 100,
  * max_outer 30, inner_prec F32, inner_tol 1e-6, even_odd 1, precond NONE, gs_passes 1,
- * rhs_batch 0, precond_iters 32. */
+ * rhs_batch 0, precond_iters 32, sap_block {4, 4, 4, 4}, sap_cycles 1, sap_mr_steps 4. */
 void dd_solve_params_default(dd_solve_params* p);
 
 /*
@@ -307,6 +313,29 @@ void dd_solve_params_default(dd_solve_params* p);
  */
 int dd_solve(dd_clover* op, const dd_solve_params* params, const void* b, void* x, int nrhs, int layout,
              void* stream, dd_stats* stats);
+
+/* ---- Schwarz alternating procedure (SAP) ----
+ * z = M^{-1} v for the block smoother that the thesis names for DDalphaAMG
+ * (Section 1.3), read as red-black multiplicative Schwarz with
+ * non-overlapping blocks:
+ *   the lattice is cut into blocks of block[0..3] = (b_T, b_Z, b_Y, b_X)
+ *   sites aligned with the origin; every extent must hold an even number of
+ *   blocks and a block at most 256 sites (DD_ERR_ARG otherwise); the colour
+ *   of a block is the parity of the sum of its block coordinates;
+ *   D_B is D restricted to block B with the hops that leave it dropped;
+ *   from z = 0, r = v, each of `cycles` cycles treats the blocks of colour 0
+ *   and then of colour 1: e_B = `mr_steps` minimal-residual steps on
+ *   D_B e = r_B from e = 0 (q = D_B rho, alpha = q^H rho / q^H q,
+ *   e += alpha rho, rho -= alpha q) on every block of the colour,
+ *   z += e, r = v - D z.
+ * v, z: full fields of `nrhs` right-hand sides in `layout` (canonical device
+ * or host, or native); prec DD_PREC_F64 or DD_PREC_F32 (arithmetic and
+ * native vectors), or DD_PREC_F16 (FP16 links and blocks, FP32 vectors;
+ * canonical layouts only).  Workspace is owned by the operator handle.
+ * Enqueued on `stream` (host layout synchronises).
+ */
+int dd_sap(dd_clover* op, int prec, const int block[4], int cycles, int mr_steps, const void* v, void* z, int nrhs,
+           int layout, void* stream);
 
 /* ---- link derivative (not in the thesis) ----
  * For L = Re <phi, D psi> = Re sum_x phi(x)^H (D psi)(x), writes per link

@@ -18,7 +18,7 @@ DD_PREC_F64, DD_PREC_F32, DD_PREC_F16 = 1, 2, 4
 DD_OP_D, DD_OP_DH, DD_OP_DHAT, DD_OP_DHAT_H, DD_OP_SC = 0, 1, 2, 3, 4
 DD_LAYOUT_CANONICAL, DD_LAYOUT_CANONICAL_HOST, DD_LAYOUT_NATIVE, DD_LAYOUT_NATIVE_PAIRED = 0, 1, 2, 3
 
-DD_PRECOND_NONE, DD_PRECOND_NORMAL, DD_PRECOND_CGNR = 0, 1, 2
+DD_PRECOND_NONE, DD_PRECOND_NORMAL, DD_PRECOND_CGNR, DD_PRECOND_SAP = 0, 1, 2, 3
 PREC = {"f64": DD_PREC_F64, "f32": DD_PREC_F32, "f16": DD_PREC_F16}
 OPS = {"D": DD_OP_D, "DH": DD_OP_DH, "DHAT": DD_OP_DHAT, "DHAT_H": DD_OP_DHAT_H, "SC": DD_OP_SC}
 
@@ -34,7 +34,8 @@ class SolveParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("max_restarts", ctypes.c_int),
                 ("max_outer", ctypes.c_int), ("inner_prec", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("even_odd", ctypes.c_int), ("verbose", ctypes.c_int), ("precond", ctypes.c_int),
-                ("gs_passes", ctypes.c_int), ("rhs_batch", ctypes.c_int), ("precond_iters", ctypes.c_int)]
+                ("gs_passes", ctypes.c_int), ("rhs_batch", ctypes.c_int), ("precond_iters", ctypes.c_int),
+                ("sap_block", ctypes.c_int * 4), ("sap_cycles", ctypes.c_int), ("sap_mr_steps", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -73,6 +74,7 @@ SIGNATURES = {
     "dd_solve_params_default": (None, [_P]),
     "dd_solve": (_I, [_P, _P, _P, _P, _I, _I, _P, _P]),
     "dd_force": (_I, [_P, _I, _P, _P, _I, _I, _P, _P, _P]),
+    "dd_sap": (_I, [_P, _I, _P, _I, _I, _P, _P, _I, _I, _P]),
     "dd_batch_create": (_I, [_P, _I, _I, _P, _P]),
     "dd_batch_destroy": (_I, [_P]),
     "dd_apply_batched": (_I, [_P, _P, _P, _P]),
@@ -235,6 +237,8 @@ class Operator:
         p = SolveParams()
         _lib.dd_solve_params_default(ctypes.byref(p))
         for k, v in kw.items():
+            if k == "sap_block":
+                v = (ctypes.c_int * 4)(*v)
             setattr(p, k, v)
         st = Stats()
         s = 0 if layout == DD_LAYOUT_CANONICAL_HOST and stream is None else _stream(stream)
@@ -242,6 +246,11 @@ class Operator:
         if status not in (DD_OK, DD_ERR_NOT_CONVERGED):
             check(status, "dd_solve")
         return status, st.as_dict()
+
+    def sap(self, prec, block, cycles, mr_steps, v, z, nrhs, layout=DD_LAYOUT_CANONICAL, stream=None):
+        blk = (ctypes.c_int * 4)(*block)
+        s = 0 if layout == DD_LAYOUT_CANONICAL_HOST and stream is None else _stream(stream)
+        check(_lib.dd_sap(self.h, prec, blk, cycles, mr_steps, _ptr(v), _ptr(z), nrhs, layout, s), "dd_sap")
 
     def force(self, prec, phi, psi, nrhs, with_clover, G=None, F=None, stream=None):
         check(_lib.dd_force(self.h, prec, _ptr(phi), _ptr(psi), nrhs, int(with_clover),

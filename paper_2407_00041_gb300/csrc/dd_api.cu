@@ -7,6 +7,7 @@
 #include "dd_blas.h"
 #include "dd_internal.h"
 #include "dd_ops.h"
+#include "dd_sap.h"
 
 namespace dd {
 const char* last_error();
@@ -447,6 +448,9 @@ void dd_solve_params_default(dd_solve_params* p) {
   p->gs_passes = 1;
   p->rhs_batch = 0;
   p->precond_iters = 32;
+  for (int mu = 0; mu < 4; ++mu) p->sap_block[mu] = 4;
+  p->sap_cycles = 1;
+  p->sap_mr_steps = 4;
 }
 
 int dd_solve(dd_clover* op, const dd_solve_params* params, const void* b, void* x, int nrhs, int layout,
@@ -454,8 +458,12 @@ int dd_solve(dd_clover* op, const dd_solve_params* params, const void* b, void* 
   if (!op || !params || !b || !x || nrhs < 1) return fail(DD_ERR_ARG, "null argument or nrhs < 1");
   if (layout != DD_LAYOUT_CANONICAL && layout != DD_LAYOUT_CANONICAL_HOST)
     return fail(DD_ERR_ARG, "dd_solve takes canonical fields");
-  if (params->precond < DD_PRECOND_NONE || params->precond > DD_PRECOND_CGNR)
+  if (params->precond < DD_PRECOND_NONE || params->precond > DD_PRECOND_SAP)
     return fail(DD_ERR_ARG, "unknown preconditioner");
+  if (params->precond == DD_PRECOND_SAP) {
+    DD_TRY(sap_check_blocks(op->lat, params->sap_block, params->inner_prec == DD_PREC_F64 ? P64 : P32));
+    if (params->sap_cycles < 1 || params->sap_mr_steps < 1) return fail(DD_ERR_ARG, "SAP cycles and MR steps >= 1");
+  }
   if (params->precond == DD_PRECOND_CGNR && params->precond_iters < 1)
     return fail(DD_ERR_ARG, "precond_iters must be >= 1");
   if (!(params->tol > 0) || params->max_restarts < 1 || params->max_outer < 0)
@@ -477,6 +485,49 @@ int dd_solve(dd_clover* op, const dd_solve_params* params, const void* b, void* 
     DD_CUDA(cudaStreamSynchronize(st));
   }
   return s;
+}
+
+int dd_sap(dd_clover* op, int prec, const int block[4], int cycles, int mr_steps, const void* v, void* z, int nrhs,
+           int layout, void* stream) {
+  if (!op || !block || !v || !z || nrhs < 1) return fail(DD_ERR_ARG, "null argument or nrhs < 1");
+  if (!valid_prec(prec)) return fail(DD_ERR_ARG, "bad precision");
+  if (layout < DD_LAYOUT_CANONICAL || layout > DD_LAYOUT_NATIVE) return fail(DD_ERR_ARG, "bad layout");
+  if (layout == DD_LAYOUT_NATIVE && prec == DD_PREC_F16)
+    return fail(DD_ERR_ARG, "SAP: DD_PREC_F16 (FP32 vectors) takes canonical layouts");
+  if (cycles < 1 || mr_steps < 1) return fail(DD_ERR_ARG, "SAP: cycles and MR steps must be >= 1");
+  const int pg = prec, pv = prec == DD_PREC_F64 ? P64 : P32;
+  const dd_lattice* lat = op->lat;
+  DD_TRY(sap_check_blocks(lat, block, pv));
+  const int pi = prec_index(pg);
+  if (!op->gauge->links[pi].ptr || !op->clov[pi].ptr)
+    return fail(DD_ERR_UNSUPPORTED, "precision not created in the gauge/operator handles");
+  cudaStream_t st = as_stream(stream);
+  const size_t nb = field_bytes(lat, pv, 0, nrhs);
+  const size_t cb = (size_t)lat->V * 12 * 16 * nrhs;
+  DD_TRY(op->ws_sap.ensure(nb));
+  Field R = field_view(lat, pv, 0, op->ws_sap.ptr, nrhs);
+  if (layout == DD_LAYOUT_NATIVE) {
+    Field Vf = field_view(lat, pv, 0, const_cast<void*>(v), nrhs), Zf = field_view(lat, pv, 0, z, nrhs);
+    return sap_apply(op, pg, pv, block, cycles, mr_steps, Vf, Zf, R, st);
+  }
+  const double* cin = nullptr;
+  DD_TRY(stage_in(op->ws_canon_in, v, cb, layout, &cin, st));
+  DD_TRY(op->ws_in.ensure(nb));
+  DD_TRY(op->ws_out.ensure(nb));
+  Field Vf = field_view(lat, pv, 0, op->ws_in.ptr, nrhs), Zf = field_view(lat, pv, 0, op->ws_out.ptr, nrhs);
+  DD_TRY(pack(lat, pv, 0, cin, Vf, st));
+  DD_TRY(sap_apply(op, pg, pv, block, cycles, mr_steps, Vf, Zf, R, st));
+  double* cout = reinterpret_cast<double*>(z);
+  if (layout == DD_LAYOUT_CANONICAL_HOST) {
+    DD_TRY(op->ws_canon_out.ensure(cb));
+    cout = reinterpret_cast<double*>(op->ws_canon_out.ptr);
+  }
+  DD_TRY(unpack(lat, pv, 0, Zf, cout, st));
+  if (layout == DD_LAYOUT_CANONICAL_HOST) {
+    DD_CUDA(cudaMemcpyAsync(z, cout, cb, cudaMemcpyDeviceToHost, st));
+    DD_CUDA(cudaStreamSynchronize(st));
+  }
+  return DD_OK;
 }
 
 int dd_force(dd_clover* op, int prec, const double* phi, const double* psi, int nrhs, int with_clover, double* G,

@@ -94,6 +94,8 @@ struct dd_clover {
   dd::DevBuf ainv[3];
   // workspace for canonical-layout calls and operator intermediates
   dd::DevBuf ws_in, ws_out, ws_tmp, ws_canon_in, ws_canon_out;
+  // residual workspace of dd_sap
+  dd::DevBuf ws_sap;
   // FP32 link-derivative accumulator of dd_force: [V][4][20] floats
   dd::DevBuf ws_force;
   dd::HostPipe pipe;

@@ -25,6 +25,10 @@
 //           method on the normal equations A^H A z = A^H v_j (from z = 0), run
 //           on the device with step sizes kept in device memory; Z_m is stored
 //           and x += Z_m y.
+//   sap     the flexible preconditioner z_j = n red-black Schwarz cycles on
+//           D z = v_j (dd_sap.cu); for the even-odd system (A = Dhat, whose
+//           inverse is the odd-odd block of D^{-1}) z_j is the odd half of the
+//           cycles applied to the full field (0 on even sites, v_j on odd).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -36,6 +40,7 @@
 #include "dd_blas.h"
 #include "dd_internal.h"
 #include "dd_ops.h"
+#include "dd_sap.h"
 
 namespace dd {
 
@@ -65,12 +70,16 @@ struct Inner {
   int N, m;
   int64_t L;     // 16-byte groups per vector
   size_t vbytes;
-  int mode = 0;         // DD_PRECOND_NONE / _NORMAL / _CGNR
+  int mode = 0;         // DD_PRECOND_NONE / _NORMAL / _CGNR / _SAP
   int cg_iters = 32;    // CG steps per application of the cgnr preconditioner
   bool normal = false;  // mode == DD_PRECOND_NORMAL
   int verbose = 0;
   int gs_passes = 1;    // classical Gram-Schmidt passes per Arnoldi step
   DevBuf basis, w, rvec, tmp, red, partials, coef, zt, ut, zbasis, cr, cz, cp, cgs;
+  // sap: block extents, cycles and MR steps per block solve; full fields v, z, r
+  int sap_block[4] = {4, 4, 4, 4};
+  int sap_cycles = 1, sap_mr = 4;
+  DevBuf sv, sz, sr;
   // CG norms formed by the second stencil launch of Dhat (one RHS, FP32
   // vectors; DD_FUSED_NORM=0 turns it off): per-block partial sums
   bool fuse_norm = false;
@@ -99,6 +108,13 @@ struct Inner {
       DD_TRY(zt.ensure(vbytes));
       DD_TRY(ut.ensure(vbytes));
     }
+    if (mode == DD_PRECOND_SAP) {
+      DD_TRY(zbasis.ensure(vbytes * m));
+      const size_t fb = field_bytes(lat, pv, 0, N);
+      DD_TRY(sv.ensure(fb));
+      DD_TRY(sz.ensure(fb));
+      DD_TRY(sr.ensure(fb));
+    }
     if (mode == DD_PRECOND_CGNR) {
       DD_TRY(zbasis.ensure(vbytes * m));
       DD_TRY(cr.ensure(vbytes));
@@ -121,6 +137,12 @@ struct Inner {
     if (!hred.p) DD_TRY(hred.alloc(nred * sizeof(double2)));
     if (!hcoef.p) DD_TRY(hcoef.alloc((size_t)(m + 1) * N * sizeof(double2)));
     return DD_OK;
+  }
+
+  void set_sap(const dd_solve_params* prm) {
+    for (int mu = 0; mu < 4; ++mu) sap_block[mu] = prm->sap_block[mu];
+    sap_cycles = prm->sap_cycles;
+    sap_mr = prm->sap_mr_steps;
   }
 
   void* V(int j) { return reinterpret_cast<char*>(basis.ptr) + vbytes * j; }
@@ -153,6 +175,24 @@ struct Inner {
     if (!normal) return apply_op(v, out, false, st);
     DD_TRY(apply_op(v, zt.ptr, true, st));
     return apply_op(zt.ptr, out, false, st);
+  }
+
+  // z = SAP cycles on D z = v (full lattice), or for the even-odd system the
+  // odd half of the cycles applied to (0, v)
+  int sap(const void* v, void* z, cudaStream_t st) {
+    const dd_lattice* lat = op->lat;
+    Field V = field_view(lat, pv, 0, sv.ptr, N), Z = field_view(lat, pv, 0, sz.ptr, N),
+          R = field_view(lat, pv, 0, sr.ptr, N);
+    if (!eo) {
+      Field Vin = field_view(lat, pv, 0, const_cast<void*>(v), N), Zout = field_view(lat, pv, 0, z, N);
+      return sap_apply(op, pg, pv, sap_block, sap_cycles, sap_mr, Vin, Zout, R, st);
+    }
+    const size_t hb = field_bytes(lat, pv, 1, N);
+    DD_CUDA(cudaMemsetAsync(V.h[0].base, 0, hb, st));
+    DD_CUDA(cudaMemcpyAsync(V.h[1].base, v, hb, cudaMemcpyDeviceToDevice, st));
+    DD_TRY(sap_apply(op, pg, pv, sap_block, sap_cycles, sap_mr, V, Z, R, st));
+    DD_CUDA(cudaMemcpyAsync(z, Z.h[1].base, hb, cudaMemcpyDeviceToDevice, st));
+    return DD_OK;
   }
 
   // z = k steps of CG on A^H A z = A^H v from z = 0 (the cgnr preconditioner)
@@ -268,8 +308,11 @@ struct Inner {
       int jmax = 0;
       for (int j = 0; j < m; ++j) {
         ++steps;
-        if (mode == DD_PRECOND_CGNR) {
-          DD_TRY(cgnr(V(j), Zb(j), st));             // z_j = M_j^{-1} v_j
+        if (mode == DD_PRECOND_CGNR || mode == DD_PRECOND_SAP) {
+          if (mode == DD_PRECOND_CGNR)
+            DD_TRY(cgnr(V(j), Zb(j), st));  // z_j = M_j^{-1} v_j
+          else
+            DD_TRY(sap(V(j), Zb(j), st));
           DD_TRY(apply_op(Zb(j), w.ptr, false, st));  // w = A z_j
         } else {
           DD_TRY(apply(V(j), w.ptr, st));  // w = A z_j (z_j = v_j, or A^H v_j for the fixed preconditioner)
@@ -362,7 +405,7 @@ struct Inner {
         }
       DD_CUDA(cudaMemcpyAsync(dcoef, hc, (size_t)jmax * N * sizeof(double2), cudaMemcpyHostToDevice, st));
       VecList vs;
-      for (int i = 0; i < jmax; ++i) vs.p[i] = mode == DD_PRECOND_CGNR ? Zb(i) : V(i);
+      for (int i = 0; i < jmax; ++i) vs.p[i] = (mode == DD_PRECOND_CGNR || mode == DD_PRECOND_SAP) ? Zb(i) : V(i);
       if (!normal) {
         DD_TRY(axpys(vs, jmax, dcoef, 1.0, e, st));  // e += Z_m y (Z_m = V_m without preconditioner)
       } else {
@@ -580,6 +623,7 @@ int solve_schur(dd_clover* op, const dd_solve_params* prm, const double* b, doub
     const int nb = std::min(nbmax, N - r0);
     DD_TRY(inner.init(op, pin, pv, true, nb, prm->restart, prm->precond));
     inner.cg_iters = prm->precond_iters;
+    inner.set_sap(prm);
     inner.verbose = prm->verbose;
     inner.gs_passes = prm->gs_passes;
     const size_t off = (size_t)r0 * lat->V * 24;  // doubles per RHS: V sites x 12 complex
@@ -640,6 +684,7 @@ int solve(dd_clover* op, const dd_solve_params* prm, const double* b_canon, doub
   Inner inner;
   DD_TRY(inner.init(op, pg, pv, eo, N, prm->restart, prm->precond));
   inner.cg_iters = prm->precond_iters;
+  inner.set_sap(prm);
   inner.verbose = prm->verbose;
   inner.gs_passes = prm->gs_passes;
   dd_stats s{};
