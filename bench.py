@@ -689,6 +689,8 @@ def main():
     ap.add_argument("--solve-inner", default="f32", choices=["f32", "f16"])
     ap.add_argument("--dims", default="96x48x48x48", help="nT x nZ x nY x nX (a smaller lattice for profiling)")
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides of the timed D psi (profiling)")
+    ap.add_argument("--layout", default="native", choices=["native", "paired"],
+                    help="field layout of the timed FP32 / FP16 D psi (paired: even --nrhs; profiling)")
     ap.add_argument("--solve-64x128-8rhs", action="store_true", help="run the 64^3x128, 8-RHS memory-fitted solve instead")
     ap.add_argument("--solve-only", action="store_true", help="run only the mixed 48^3x96 solve (for profiling)")
     ap.add_argument("--rhs-batch", type=int, default=2, help="64^3x128 solve: right-hand sides per batch")
@@ -755,11 +757,16 @@ def main():
         nbytes = op.field_bytes(p, 0, N)
         xin = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
         xout = torch.empty_like(xin)
-        op.pack(p, 0, psi_dev, xin, N)
+        paired = args.layout == "paired" and prec != "f64" and N % 2 == 0
+        if paired:
+            op.pack_paired(p, 0, psi_dev, xin, N)
+        else:
+            op.pack(p, 0, psi_dev, xin, N)
+        layout = dd.DD_LAYOUT_NATIVE_PAIRED if paired else dd.DD_LAYOUT_NATIVE
 
         def step():
             dd.check(dd.lib.dd_apply(op.h, dd.DD_OP_D, p, xin.data_ptr(), xout.data_ptr(), N,
-                                     dd.DD_LAYOUT_NATIVE, stream.cuda_stream), "dd_apply")
+                                     layout, stream.cuda_stream), "dd_apply")
 
         log(f"timing D psi in {prec}")
         steps = args.steps if prec == args.prec else max(10, min(args.steps, 50))
@@ -799,7 +806,10 @@ def main():
                                  else "FMA-chain probe dd_probe_flops on this GPU"}}
             # parity of the timed launch configuration on a sample of sites
             out_c = torch.empty_like(psi_dev)
-            op.unpack(p, 0, xout, out_c, N)
+            if paired:
+                op.unpack_paired(p, 0, xout, out_c, N)
+            else:
+                op.unpack(p, 0, xout, out_c, N)
             head["_out"] = out_c
         del xin, xout
 

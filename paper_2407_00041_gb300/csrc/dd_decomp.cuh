@@ -113,10 +113,33 @@ __global__ void __launch_bounds__(128) k_face_pack(const DomHopArgs A) {
   if (a.npar == 1 && p == a.p0) return;
   const int lex = ((c[0] * a.g.n[1] + c[1]) * a.g.n[2] + c[2]) * a.g.n[3] + c[3];
   const int s = lex >> 1;
-  cx<R> psi[12];
-  const R scale = load_spinor_unscaled<PIN, R>(a.in[p], a.gstride, (int64_t)s * a.nrhs + r, psi);
   constexpr int TF = DAG ? +1 : -1;
   constexpr int TB = -TF;
+  if constexpr (PG == P16 && PIN == P16) {
+    // the FP16 hop of dd_hop.cuh: half2 projection, mixed-FMA link product
+    __half2 psi[12], h0[3], h1[3];
+    const float scale = load_spinor_h(a.in[p], a.gstride, (int64_t)s * a.nrhs + r, psi);
+    cx<float> f0[3], f1[3];
+    if (!kind) {
+      hop_project_h<MU, TF>(psi, h0, h1);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float2 x0 = __half22float2(h0[c]), x1 = __half22float2(h1[c]);
+        f0[c] = mk(x0.x, x0.y);
+        f1[c] = mk(x1.x, x1.y);
+      }
+      face_store<float>(A.f.lam_send[MU], nf, t, f0, f1, scale, true);
+    } else {
+      hop_project_h<MU, TB>(psi, h0, h1);
+      __half2 u[9];
+      load_link_h(a.U[p], s, a.g.Vh, MU, u);
+      hop_mul_h<true>(u, h0, h1, f0, f1);
+      face_store<float>(A.f.chi_send[MU], nf, t, f0, f1, scale, true);
+    }
+    return;
+  }
+  cx<R> psi[12];
+  const R scale = load_spinor_unscaled<PIN, R>(a.in[p], a.gstride, (int64_t)s * a.nrhs + r, psi);
   cx<R> h0[3], h1[3];
   if (!kind) {
     hop_project<MU, TF, R>(psi, h0, h1);
@@ -177,7 +200,6 @@ __global__ void __launch_bounds__(128, HopMinBlocks<PG>::value) k_hop_dd(const D
 
 #define DD_DHOP(MU)                                                                                      \
   {                                                                                                      \
-    cx<R> psi[12];                                                                                       \
     if (BOUNDARY && A.d.xch[MU] && sc.c[MU] == a.g.n[MU] - 1) {                                          \
       const int64_t nf = A.d.nface[MU] * a.nrhs;                                                         \
       cx<R> h0[3], h1[3], g0[3], g1[3], u[9];                                                            \
@@ -185,14 +207,24 @@ __global__ void __launch_bounds__(128, HopMinBlocks<PG>::value) k_hop_dd(const D
                                  PIN == P16);                                                            \
       R sg = (MU == 0 && sc.c[0] + A.d.off[0] == A.d.N[0] - 1) ? (R)a.g.t_bc : (R)1;                     \
       sg *= scl;                                                                                         \
-      load_link<PG, R>(a.U[p], s, Vh, MU, u, a.recon);                                                   \
-      hop_mul<false, R>(u, h0, h1, g0, g1);                                                              \
+      if constexpr (PG == P16 && PIN == P16) {                                                          \
+        __half2 uh[9], x0[3], x1[3];                                                                     \
+        _Pragma("unroll") for (int c = 0; c < 3; ++c) {                                                  \
+          x0[c] = __floats2half2_rn(h0[c].re, h0[c].im);                                                 \
+          x1[c] = __floats2half2_rn(h1[c].re, h1[c].im);                                                 \
+        }                                                                                                \
+        load_link_h(a.U[p], s, Vh, MU, uh);                                                              \
+        hop_mul_h<false>(uh, x0, x1, g0, g1);                                                            \
+      } else {                                                                                           \
+        load_link<PG, R>(a.U[p], s, Vh, MU, u, a.recon);                                                 \
+        hop_mul<false, R>(u, h0, h1, g0, g1);                                                            \
+      }                                                                                                  \
       hop_reconstruct<MU, TF, R>(acc, g0, g1, sg);                                                       \
     } else {                                                                                             \
       const int nl = nb_fwd(a.g, sc, MU);                                                                \
       R sg = (MU == 0 && sc.c[0] == a.g.n[0] - 1) ? (R)a.g.t_bc : (R)1;                                  \
-      sg *= load_spinor_unscaled<PIN, R>(a.in[q], a.gstride, (int64_t)(nl >> 1) * a.nrhs + r, psi);      \
-      hop<PG, MU, TF, false, R>(acc, psi, a.U[p], s, Vh, sg, a.recon);                                   \
+      hop_from<PG, PIN, MU, TF, false, R>(acc, a.in[q], a.gstride, (int64_t)(nl >> 1) * a.nrhs + r, a.U[p], s, \
+                                          Vh, sg, a.recon);                                              \
     }                                                                                                    \
     if (BOUNDARY && A.d.xch[MU] && sc.c[MU] == 0) {                                                      \
       const int64_t nf = A.d.nface[MU] * a.nrhs;                                                         \
@@ -205,8 +237,8 @@ __global__ void __launch_bounds__(128, HopMinBlocks<PG>::value) k_hop_dd(const D
     } else {                                                                                             \
       const int nl = nb_bwd(a.g, sc, MU);                                                                \
       R sg = (MU == 0 && sc.c[0] == 0) ? (R)a.g.t_bc : (R)1;                                             \
-      sg *= load_spinor_unscaled<PIN, R>(a.in[q], a.gstride, (int64_t)(nl >> 1) * a.nrhs + r, psi);      \
-      hop<PG, MU, TB, true, R>(acc, psi, a.U[q], nl >> 1, Vh, sg, a.recon);                              \
+      hop_from<PG, PIN, MU, TB, true, R>(acc, a.in[q], a.gstride, (int64_t)(nl >> 1) * a.nrhs + r, a.U[q],    \
+                                         nl >> 1, Vh, sg, a.recon);                                      \
     }                                                                                                    \
   }
   DD_DHOP(0)

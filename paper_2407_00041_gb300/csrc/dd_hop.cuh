@@ -207,6 +207,142 @@ __device__ __forceinline__ void hop(cx<R> acc[12], const cx<R> psi[12], const vo
   hop_regs<MU, T, ADJ, R>(acc, psi, u, sign);
 }
 
+// ---- FP16 storage with half2 projection and FP16 x FP16 -> FP32 products ----
+// For FP16 spinors with FP16 links and blocks the hop runs without widening
+// the stored values: the spin projection h = u + T B l is formed in half2
+// arithmetic (each component the exact sum rounded once to FP16), and every
+// product of a link or block element with an FP16 value is one mixed FMA,
+// fma.rn.f32.f16 (exact product of the two FP16 values, FP32 accumulation,
+// one rounding to FP32), in the order of cfma / cfmac.  The reconstruction
+// and the accumulation of the hops stay in FP32.  Compared with widening
+// every value first, the only extra rounding is that of h to FP16.
+
+// c + a b for FP16 a, b with one rounding to FP32
+__device__ __forceinline__ float mfma_h(__half a, __half b, float c) {
+  float d;
+  asm("fma.rn.f32.f16 %0, %1, %2, %3;" : "=f"(d) : "h"(__half_as_ushort(a)), "h"(__half_as_ushort(b)), "f"(c));
+  return d;
+}
+
+// (re, im) -> (im, re)
+__device__ __forceinline__ __half2 h2_swap(__half2 z) { return __lowhigh2highlow(z); }
+
+// h = u + T (B_mu l) per colour on half2 (re, im) words; -i z = swap(z) (1, -1),
+// i z = swap(z) (-1, 1)
+template <int MU, int T>
+__device__ __forceinline__ void hop_project_h(const __half2 psi[12], __half2 h0[3], __half2 h1[3]) {
+  const __half2 pm = __floats2half2_rn((float)T, (float)-T);
+  const __half2 mp = __floats2half2_rn((float)-T, (float)T);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const __half2 u0 = psi[c], u1 = psi[3 + c], l0 = psi[6 + c], l1 = psi[9 + c];
+    if constexpr (MU == 0) {  // b0 = l0, b1 = l1
+      h0[c] = T > 0 ? __hadd2(u0, l0) : __hsub2(u0, l0);
+      h1[c] = T > 0 ? __hadd2(u1, l1) : __hsub2(u1, l1);
+    } else if constexpr (MU == 1) {  // b0 = -i l0, b1 = i l1
+      h0[c] = __hfma2(h2_swap(l0), pm, u0);
+      h1[c] = __hfma2(h2_swap(l1), mp, u1);
+    } else if constexpr (MU == 2) {  // b0 = -l1, b1 = l0
+      h0[c] = T > 0 ? __hsub2(u0, l1) : __hadd2(u0, l1);
+      h1[c] = T > 0 ? __hadd2(u1, l0) : __hsub2(u1, l0);
+    } else {  // b0 = -i l1, b1 = -i l0
+      h0[c] = __hfma2(h2_swap(l1), pm, u0);
+      h1[c] = __hfma2(h2_swap(l0), pm, u1);
+    }
+  }
+}
+
+// g += w h (ADJ = false) or conj(w) h (ADJ = true) for FP16 w, h (nh = -h),
+// in the order of cfma / cfmac
+template <bool ADJ>
+__device__ __forceinline__ void cmac_h(__half2 w, __half2 h, __half2 nh, cx<float>& g) {
+  const __half wr = __low2half(w), wi = __high2half(w);
+  g.re = mfma_h(wr, __low2half(h), g.re);
+  g.re = mfma_h(wi, ADJ ? __high2half(h) : __high2half(nh), g.re);
+  g.im = mfma_h(wr, __high2half(h), g.im);
+  g.im = mfma_h(wi, ADJ ? __low2half(nh) : __low2half(h), g.im);
+}
+
+// g = W h for both spin components (W = U, or U^H with ADJ)
+template <bool ADJ>
+__device__ __forceinline__ void hop_mul_h(const __half2 u[9], const __half2 h0[3], const __half2 h1[3],
+                                          cx<float> g0[3], cx<float> g1[3]) {
+  __half2 n0[3], n1[3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) n0[b] = __hneg2(h0[b]), n1[b] = __hneg2(h1[b]);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    g0[a] = zero<float>();
+    g1[a] = zero<float>();
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const __half2 w = ADJ ? u[3 * b + a] : u[3 * a + b];
+      cmac_h<ADJ>(w, h0[b], n0[b], g0[a]);
+      cmac_h<ADJ>(w, h1[b], n1[b], g1[a]);
+    }
+  }
+}
+
+// The nine FP16 elements of link mu of site s, as stored (four per 16-byte group)
+__device__ __forceinline__ void load_link_h(const void* Ubase, int64_t s, int64_t Vh, int mu, __half2 u[9]) {
+  const uint4* p = reinterpret_cast<const uint4*>(Ubase) + s;
+  const int g0 = (9 * mu) >> 2, off = (9 * mu) & 3;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const uint4 v = __ldg(p + (int64_t)(g0 + k) * Vh);
+    const unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = 4 * k + q - off;
+      if (e >= 0 && e < 9) u[e] = *reinterpret_cast<const __half2*>(&w[q]);
+    }
+  }
+}
+
+// The 12 stored FP16 components of index i (site * N + r); returns the site scale
+__device__ __forceinline__ float load_spinor_h(const HalfField& f, int64_t gstride, int64_t i, __half2 v[12]) {
+  const uint4* b = reinterpret_cast<const uint4*>(f.base) + i;
+  const float sc = __ldg(f.scale + i);
+#pragma unroll
+  for (int g = 0; g < 3; ++g) {
+    const uint4 t = __ldg(b + g * gstride);
+    const unsigned w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[4 * g + k] = *reinterpret_cast<const __half2*>(&w[k]);
+  }
+  return sc;
+}
+
+// acc += sign (I + T gamma_mu) (x) W psi for FP16 psi and links
+template <int MU, int T, bool ADJ>
+__device__ __forceinline__ void hop_h(cx<float> acc[12], const __half2 psi[12], const void* Ubase, int64_t s,
+                                      int64_t Vh, float sign) {
+  __half2 u[9], h0[3], h1[3];
+  load_link_h(Ubase, s, Vh, MU, u);
+  hop_project_h<MU, T>(psi, h0, h1);
+  cx<float> g0[3], g1[3];
+  hop_mul_h<ADJ>(u, h0, h1, g0, g1);
+  hop_reconstruct<MU, T, float>(acc, g0, g1, sign);
+}
+
+// One hop from the stored neighbour spinor i of field f: FP16 spinors with
+// FP16 links take the half2 / mixed-FMA path above, every other precision
+// pair widens to R first.  sg: the boundary sign (the FP16 site scale is
+// folded in here).
+template <int PG, int PIN, int MU, int T, bool ADJ, typename R>
+__device__ __forceinline__ void hop_from(cx<R> acc[12], const HalfField& f, int64_t gstride, int64_t i,
+                                         const void* Ubase, int64_t s, int64_t Vh, R sg, bool recon) {
+  if constexpr (PG == P16 && PIN == P16) {
+    __half2 psi[12];
+    sg *= load_spinor_h(f, gstride, i, psi);
+    hop_h<MU, T, ADJ>(acc, psi, Ubase, s, Vh, sg);
+  } else {
+    cx<R> psi[12];
+    sg *= load_spinor_unscaled<PIN, R>(f, gstride, i, psi);
+    hop<PG, MU, T, ADJ, R>(acc, psi, Ubase, s, Vh, sg, recon);
+  }
+}
+
 // Self-coupling / A_ee^{-1} storage: two Hermitian 6x6 blocks per site, 18
 // elements each: elements 0..2 hold the real diagonal in pairs (d0, d1),
 // (d2, d3), (d4, d5); elements 3..17 the strict upper triangle row by row.
@@ -284,6 +420,41 @@ __device__ __forceinline__ void block_apply(const void* M, int64_t s, int64_t Vh
   block_apply_g<PG, false, R>(M, s, Vh, x, out, true);
 }
 
+// out = M x for FP16 blocks and an FP16 spinor x (stored values, without the
+// site scale), by mixed FMAs in the order of block_apply_g.
+__device__ __forceinline__ void block_apply_h(const void* M, int64_t s, int64_t Vh, const __half2 x[12],
+                                              cx<float> out[12]) {
+  __half2 nx[12];
+#pragma unroll
+  for (int c = 0; c < 12; ++c) nx[c] = __hneg2(x[c]);
+  const uint4* p = reinterpret_cast<const uint4*>(M) + s;
+  unsigned w[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+  for (int E = 0; E < 36; ++E) {
+    if (E % 4 == 0) {
+      const uint4 v = __ldcs(p + (int64_t)(E / 4) * Vh);
+      w[0] = v.x, w[1] = v.y, w[2] = v.z, w[3] = v.w;
+    }
+    const __half2 m = *reinterpret_cast<const __half2*>(&w[E % 4]);
+    const int b = E / 18, k = E % 18;
+    if (k < 3) {
+      const int i0 = 6 * b + 2 * k, i1 = i0 + 1;
+      const __half d0 = __low2half(m), d1 = __high2half(m);
+      out[i0].re = mfma_h(d0, __low2half(x[i0]), 0.f);
+      out[i0].im = mfma_h(d0, __high2half(x[i0]), 0.f);
+      out[i1].re = mfma_h(d1, __low2half(x[i1]), 0.f);
+      out[i1].im = mfma_h(d1, __high2half(x[i1]), 0.f);
+    } else {
+      int i, j;
+      tri_ij(k - 3, i, j);
+      i += 6 * b;
+      j += 6 * b;
+      cmac_h<false>(m, x[j], nx[j], out[i]);  // out_i += m x_j
+      cmac_h<true>(m, x[i], nx[i], out[j]);   // out_j += conj(m) x_i
+    }
+  }
+}
+
 // Epilogue of the one-thread-per-(site, RHS) stencil: combine the hopping
 // sum acc of output site s (parity p), right-hand side r, with the self
 // coupling as EPI says and store.  With NORM it returns |out|^2 of the stored
@@ -295,7 +466,17 @@ __device__ __forceinline__ float hop_epilogue(const HopArgs& a, int p, int s, in
   const int64_t i = (int64_t)s * a.nrhs + r;
   const void* M = a.M[p];
   cx<R> res[12];
-  if constexpr (EPI == EPI_D || EPI == EPI_RESID) {
+  if constexpr (EPI == EPI_D && PG == P16 && PIN == P16) {
+    // M y from the stored FP16 values, then the site scale
+    __half2 yh[12];
+    const float ys = load_spinor_h(a.y[p], a.gstride, i, yh);
+    block_apply_h(M, s, Vh, yh, res);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      res[c].re = ffma(beta, acc[c].re, res[c].re * ys);
+      res[c].im = ffma(beta, acc[c].im, res[c].im * ys);
+    }
+  } else if constexpr (EPI == EPI_D || EPI == EPI_RESID) {
     cx<R> y[12];
     if constexpr (EPI == EPI_D)
       load_spinor<PIN, R>(a.y[p], a.gstride, i, y);
@@ -381,17 +562,16 @@ __device__ __forceinline__ float hop_thread(const HopArgs& a, int64_t tid) {
 #pragma unroll
   for (int c = 0; c < 12; ++c) acc[c] = zero<R>();
 
-#define DD_HOP_DIR(MU)                                                                     \
-  {                                                                                        \
-    cx<R> psi[12];                                                                         \
-    int nl = nb_fwd(a.g, sc, MU);                                                          \
-    R sg = (MU == 0 && sc.c[0] == a.g.n[0] - 1) ? (R)a.g.t_bc : (R)1;                      \
-    sg *= load_spinor_unscaled<PIN, R>(a.in[q], a.gstride, (int64_t)(nl >> 1) * a.nrhs + r, psi); \
-    hop<PG, MU, TF, false, R>(acc, psi, a.U[p], s, Vh, sg, a.recon);                       \
-    nl = nb_bwd(a.g, sc, MU);                                                              \
-    sg = (MU == 0 && sc.c[0] == 0) ? (R)a.g.t_bc : (R)1;                                   \
-    sg *= load_spinor_unscaled<PIN, R>(a.in[q], a.gstride, (int64_t)(nl >> 1) * a.nrhs + r, psi); \
-    hop<PG, MU, TB, true, R>(acc, psi, a.U[q], nl >> 1, Vh, sg, a.recon);                  \
+#define DD_HOP_DIR(MU)                                                                                 \
+  {                                                                                                    \
+    int nl = nb_fwd(a.g, sc, MU);                                                                      \
+    R sg = (MU == 0 && sc.c[0] == a.g.n[0] - 1) ? (R)a.g.t_bc : (R)1;                                  \
+    hop_from<PG, PIN, MU, TF, false, R>(acc, a.in[q], a.gstride, (int64_t)(nl >> 1) * a.nrhs + r, a.U[p], s, \
+                                        Vh, sg, a.recon);                                              \
+    nl = nb_bwd(a.g, sc, MU);                                                                          \
+    sg = (MU == 0 && sc.c[0] == 0) ? (R)a.g.t_bc : (R)1;                                               \
+    hop_from<PG, PIN, MU, TB, true, R>(acc, a.in[q], a.gstride, (int64_t)(nl >> 1) * a.nrhs + r, a.U[q],    \
+                                       nl >> 1, Vh, sg, a.recon);                                      \
   }
   DD_HOP_DIR(0)
   DD_HOP_DIR(1)
