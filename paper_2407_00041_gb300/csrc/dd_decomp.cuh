@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(128) k_face_pack(const DomHopArgs A) {
 // true the rank's boundary sites from its list, taking the hops across the
 // seams from the received messages.
 template <int PG, int PIN, int POUT, bool DAG, int EPI, bool BOUNDARY>
-__global__ void __launch_bounds__(128, HopMinBlocks<PG>::value) k_hop_dd(const DomHopArgs A) {
+__global__ void __launch_bounds__(128, (HopMinBlocks<PG, PIN>::value)) k_hop_dd(const DomHopArgs A) {
   using R = typename Store<PG>::real;
   const HopArgs& a = A.h;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

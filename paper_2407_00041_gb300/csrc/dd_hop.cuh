@@ -683,17 +683,19 @@ __global__ void __launch_bounds__(128, NB >= 4 ? 2 : 3) k_hop_rb(const HopArgs a
   hop_thread_rb<PG, PIN, POUT, DAG, EPI, NB>(a, tid);
 }
 
-// Memory-bound FP32 / FP16 variants ask for at least 5 resident CTAs of 128
+// Memory-bound FP32 variants ask for at least 5 resident CTAs of 128
 // threads (at most 102 registers): measured on the 48^3 x 96 lattice this
-// beats the unconstrained 108-register build by about 5%.  FP64 is bound by
-// the FP64 pipe and keeps the unconstrained allocation.
-template <int PG>
+// beats the unconstrained 108-register build by about 5%.  The FP16-storage
+// stencil (half2 projection, mixed FMAs) asks for 7 (at most 72 registers):
+// 0.738 ms against 0.762 ms with 5 and 0.857 ms with 3 at 48^3 x 96.  FP64 is
+// bound by the FP64 pipe and keeps the unconstrained allocation.
+template <int PG, int PIN = PG>
 struct HopMinBlocks {
-  static constexpr int value = PG == P64 ? 1 : 5;
+  static constexpr int value = PG == P64 ? 1 : (PG == P16 && PIN == P16) ? 7 : 5;
 };
 
 template <int PG, int PIN, int POUT, bool DAG, int EPI>
-__global__ void __launch_bounds__(128, HopMinBlocks<PG>::value) k_hop(const HopArgs a) {
+__global__ void __launch_bounds__(128, (HopMinBlocks<PG, PIN>::value)) k_hop(const HopArgs a) {
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= launch_sites(a.g, a.npar) * a.nrhs) return;
   hop_thread<PG, PIN, POUT, DAG, EPI>(a, tid);
@@ -704,7 +706,7 @@ __global__ void __launch_bounds__(128, HopMinBlocks<PG>::value) k_hop(const HopA
 // FP32), then the four warps' sums in FP64 in order, one partial per block
 // (partials[blockIdx.x].x); threads past the end contribute zero.
 template <int PG, int PIN, int POUT, bool DAG>
-__global__ void __launch_bounds__(128, HopMinBlocks<PG>::value) k_hop_norm(const HopArgs a, double2* partials) {
+__global__ void __launch_bounds__(128, (HopMinBlocks<PG, PIN>::value)) k_hop_norm(const HopArgs a, double2* partials) {
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   float v = 0.f;
   if (tid < launch_sites(a.g, a.npar)) v = hop_thread<PG, PIN, POUT, DAG, EPI_D, true>(a, tid);
