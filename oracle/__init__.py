@@ -17,6 +17,10 @@ Contents and the passage each part follows:
   * ``sap.py``: the Schwarz alternating procedure named in Section 1.3 (red-black
     multiplicative Schwarz with minimal-residual block solves), the smoother
     and flexible preconditioner M_j.
+  * ``amg.py``: the two-level AMG preconditioner of Section 1.3 (aggregation
+    with a chirality split, P from orthonormalised test vectors, R = P^H,
+    D_c = R D P, coarse-grid correction plus SAP post-smoothing, the setup
+    phase).
 
 Array conventions (same as ``synthetic``):
   dims = (nT, nZ, nY, nX); psi [V, 4, 3] (or [V, 12]); U [V, 4, 3, 3];
@@ -32,6 +36,7 @@ import tempfile
 import numpy as np
 
 from .fgmres import fgmres, gmres_right  # noqa: F401
+from . import amg, sap  # noqa: F401
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "wilson_clover.c")
