@@ -135,6 +135,7 @@ typedef struct dd_lattice dd_lattice;
 typedef struct dd_gauge dd_gauge;
 typedef struct dd_clover dd_clover;
 typedef struct dd_batch dd_batch;
+typedef struct dd_amg dd_amg;
 
 /* Human-readable name of a status code (static string). */
 const char* dd_error_string(int status);
@@ -274,6 +275,9 @@ typedef struct {
   int sap_block[4];    /* DD_PRECOND_SAP: block extents (T, Z, Y, X), as for dd_sap */
   int sap_cycles;      /* DD_PRECOND_SAP: red-black cycles per preconditioner application */
   int sap_mr_steps;    /* DD_PRECOND_SAP: minimal-residual steps per block solve */
+  dd_amg* amg;         /* DD_PRECOND_AMG: the two-level preconditioner (dd_amg_create); its fine
+                          precision must be that of the inner vectors (F64 for inner_prec F64,
+                          F32 otherwise) and it must belong to the same operator */
 } dd_solve_params;
 
 #define DD_PRECOND_NONE 0
@@ -281,6 +285,8 @@ typedef struct {
 #define DD_PRECOND_CGNR 2  /* flexible M_j: precond_iters CG steps on A^H A z = A^H v_j */
 #define DD_PRECOND_SAP 3   /* flexible M_j: sap_cycles Schwarz cycles on D (even-odd: the odd half of
                               the cycles applied to (0, v_j), D^{-1}'s odd-odd block being Dhat^{-1}) */
+#define DD_PRECOND_AMG 4   /* flexible M_j: the two-level AMG preconditioner `amg` (even-odd: the odd
+                              half of M^{-1} (0, v_j)) */
 
 typedef struct {
   int converged;             /* 1 if every right-hand side met tol */
@@ -295,7 +301,7 @@ typedef struct {
 
 /* Fill `p` with defaults: tol 1e-10, restart 30, max_restarts 100,
  * max_outer 30, inner_prec F32, inner_tol 1e-6, even_odd 1, precond NONE, gs_passes 1,
- * rhs_batch 0, precond_iters 32, sap_block {4, 4, 4, 4}, sap_cycles 1, sap_mr_steps 4. */
+ * rhs_batch 0, precond_iters 32, sap_block {4, 4, 4, 4}, sap_cycles 1, sap_mr_steps 4, amg NULL. */
 void dd_solve_params_default(dd_solve_params* p);
 
 /*
@@ -336,6 +342,73 @@ int dd_solve(dd_clover* op, const dd_solve_params* params, const void* b, void* 
  */
 int dd_sap(dd_clover* op, int prec, const int block[4], int cycles, int mr_steps, const void* v, void* z, int nrhs,
            int layout, void* stream);
+
+/* ---- two-level algebraic multigrid (AMG) preconditioner ----
+ * Section 1.3: a coarse operator D_c that acts on the near kernel of D (the
+ * eigenvectors of small |eigenvalue|) like D and couples nearest neighbours
+ * only, a restriction R and prolongation P between the lattices built from
+ * test vectors found in a setup phase, and the subspace correction
+ * z <- z + P D_c^{-1} R r together with the SAP smoother as M_j of FGMRES
+ * (Table 5.2: depth-one coarse lattices of 4^4 or 8^4 sites per coarse site,
+ * 24 test vectors, 4 setup iterations).  The thesis gives no formulas for
+ * P, R or the setup; the reading implemented here:
+ *   aggregates: blocks of aggregate[0..3] sites aligned with the origin (each
+ *   extent must divide the lattice extent), numbered lexicographically on the
+ *   coarse lattice (X fastest), each with 2 n_tv coarse degrees of freedom,
+ *   n_tv per chirality (spins 0, 1 and 2, 3);
+ *   P: the n_tv test vectors restricted to (aggregate, chirality),
+ *   orthonormalised by modified Gram-Schmidt in order; R = P^H;
+ *   D_c = R D P (Galerkin);
+ *   M^{-1} v = z with z = P D_c^{-1} R v (the coarse system solved by GMRES
+ *   to coarse_tol), then z += SAP(v - D z) (sap_cycles cycles, 0 = none);
+ *   setup: from the n_tv given vectors w0, init_sap_iters rounds of
+ *   w_i <- SAP(w_i), then setup_iters rounds of w_i <- M^{-1} w_i with M
+ *   built from the current w (every w_i normalised after each round);
+ *   P and D_c are built from the final w.
+ * Coarse vectors and D_c are FP64 on the device; D_c is stored per aggregate
+ * A as nine 2 n_tv x 2 n_tv blocks, column-major: block 0 couples A with
+ * itself, block 1 + 2 mu with the aggregate at +mu, 2 + 2 mu with -mu
+ * (periodic on the coarse lattice).
+ */
+typedef struct {
+  int aggregate[4];         /* aggregate extents (T, Z, Y, X) */
+  int n_tv;                 /* test vectors: 4, 8 or 16 */
+  int setup_iters;          /* rounds of w_i <- M^{-1} w_i */
+  int init_sap_iters;       /* initial rounds of w_i <- SAP(w_i) */
+  int sap_block[4];         /* SAP block extents (as for dd_sap) */
+  int sap_cycles;           /* post-smoothing cycles per application (0: no smoothing) */
+  int sap_mr_steps;         /* MR steps per SAP block solve */
+  double coarse_tol;        /* relative residual asked of the coarse GMRES */
+  int coarse_restart;       /* its restart length (1 .. 32) */
+  int coarse_max_restarts;  /* its restart cycles at most */
+} dd_amg_params;
+
+/* Defaults: aggregate {4,4,4,4}, n_tv 8, setup_iters 2, init_sap_iters 2,
+ * sap_block {4,4,4,4}, sap_cycles 1, sap_mr_steps 4, coarse_tol 5e-2,
+ * coarse_restart 16, coarse_max_restarts 4. */
+void dd_amg_params_default(dd_amg_params* p);
+/* Run the setup and return the preconditioner.  prec: DD_PREC_F64 (FP64
+ * everywhere), DD_PREC_F32, or DD_PREC_F16 (FP16 links and blocks, FP32
+ * vectors) for P, the build of D_c and the smoothing.  w0: the initial test
+ * vectors, canonical device fields [n_tv][V][12] complex double (the caller
+ * draws them; they are not kept).  DD_ERR_ARG on bad parameters,
+ * DD_ERR_SINGULAR if the vectors are linearly dependent on an aggregate.
+ * Synchronises the device.  `op` must outlive the handle. */
+int dd_amg_create(dd_clover* op, int prec, const dd_amg_params* params, const double* w0, dd_amg** out);
+int dd_amg_destroy(dd_amg* amg);
+/* Coarse lattice extents, coarse degrees of freedom per aggregate (2 n_tv),
+ * setup wall time, and Arnoldi steps of the last coarse solve (each pointer
+ * may be NULL). */
+int dd_amg_info(const dd_amg* amg, int* coarse_dims4, int* dof_per_aggregate, double* setup_seconds,
+                int* last_coarse_steps);
+/* D_c to host memory: complex double [n_agg][9][2 n_tv][2 n_tv] as stored
+ * (column-major blocks).  Synchronises the device. */
+int dd_amg_coarse_download(const dd_amg* amg, double* Dc_host);
+/* z = M^{-1} v for nrhs full fields: canonical device fields (complex
+ * double) or native fields of the handle's fine precision.  Workspace is
+ * owned by the handle (and the operator handle's canonical buffers); calls on
+ * one handle must not overlap. */
+int dd_amg_apply(dd_amg* amg, const void* v, void* z, int nrhs, int layout, void* stream);
 
 /* ---- link derivative (not in the thesis) ----
  * For L = Re <phi, D psi> = Re sum_x phi(x)^H (D psi)(x), writes per link

@@ -18,7 +18,7 @@ DD_PREC_F64, DD_PREC_F32, DD_PREC_F16 = 1, 2, 4
 DD_OP_D, DD_OP_DH, DD_OP_DHAT, DD_OP_DHAT_H, DD_OP_SC = 0, 1, 2, 3, 4
 DD_LAYOUT_CANONICAL, DD_LAYOUT_CANONICAL_HOST, DD_LAYOUT_NATIVE, DD_LAYOUT_NATIVE_PAIRED = 0, 1, 2, 3
 
-DD_PRECOND_NONE, DD_PRECOND_NORMAL, DD_PRECOND_CGNR, DD_PRECOND_SAP = 0, 1, 2, 3
+DD_PRECOND_NONE, DD_PRECOND_NORMAL, DD_PRECOND_CGNR, DD_PRECOND_SAP, DD_PRECOND_AMG = 0, 1, 2, 3, 4
 PREC = {"f64": DD_PREC_F64, "f32": DD_PREC_F32, "f16": DD_PREC_F16}
 OPS = {"D": DD_OP_D, "DH": DD_OP_DH, "DHAT": DD_OP_DHAT, "DHAT_H": DD_OP_DHAT_H, "SC": DD_OP_SC}
 
@@ -35,7 +35,15 @@ class SolveParams(ctypes.Structure):
                 ("max_outer", ctypes.c_int), ("inner_prec", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("even_odd", ctypes.c_int), ("verbose", ctypes.c_int), ("precond", ctypes.c_int),
                 ("gs_passes", ctypes.c_int), ("rhs_batch", ctypes.c_int), ("precond_iters", ctypes.c_int),
-                ("sap_block", ctypes.c_int * 4), ("sap_cycles", ctypes.c_int), ("sap_mr_steps", ctypes.c_int)]
+                ("sap_block", ctypes.c_int * 4), ("sap_cycles", ctypes.c_int), ("sap_mr_steps", ctypes.c_int),
+                ("amg", ctypes.c_void_p)]
+
+
+class AmgParams(ctypes.Structure):
+    _fields_ = [("aggregate", ctypes.c_int * 4), ("n_tv", ctypes.c_int), ("setup_iters", ctypes.c_int),
+                ("init_sap_iters", ctypes.c_int), ("sap_block", ctypes.c_int * 4), ("sap_cycles", ctypes.c_int),
+                ("sap_mr_steps", ctypes.c_int), ("coarse_tol", ctypes.c_double), ("coarse_restart", ctypes.c_int),
+                ("coarse_max_restarts", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -75,6 +83,12 @@ SIGNATURES = {
     "dd_solve": (_I, [_P, _P, _P, _P, _I, _I, _P, _P]),
     "dd_force": (_I, [_P, _I, _P, _P, _I, _I, _P, _P, _P]),
     "dd_sap": (_I, [_P, _I, _P, _I, _I, _P, _P, _I, _I, _P]),
+    "dd_amg_params_default": (None, [_P]),
+    "dd_amg_create": (_I, [_P, _I, _P, _P, _P]),
+    "dd_amg_destroy": (_I, [_P]),
+    "dd_amg_info": (_I, [_P, _P, _P, _P, _P]),
+    "dd_amg_coarse_download": (_I, [_P, _P]),
+    "dd_amg_apply": (_I, [_P, _P, _P, _I, _I, _P]),
     "dd_batch_create": (_I, [_P, _I, _I, _P, _P]),
     "dd_batch_destroy": (_I, [_P]),
     "dd_apply_batched": (_I, [_P, _P, _P, _P]),
@@ -239,6 +253,8 @@ class Operator:
         for k, v in kw.items():
             if k == "sap_block":
                 v = (ctypes.c_int * 4)(*v)
+            if k == "amg":
+                v = v.h if isinstance(v, Amg) else v
             setattr(p, k, v)
         st = Stats()
         s = 0 if layout == DD_LAYOUT_CANONICAL_HOST and stream is None else _stream(stream)
@@ -303,3 +319,46 @@ class Decomposition:
         if getattr(self, "h", None) and _lib is not None:
             _lib.dd_decomp_destroy(self.h)
             self.h = None
+
+
+class Amg:
+    """Two-level AMG preconditioner (dd_amg_create); w0: canonical device
+    test vectors [n_tv, V, 12] complex128 (a torch tensor)."""
+
+    def __init__(self, op, prec, w0, **kw):
+        p = AmgParams()
+        _lib.dd_amg_params_default(ctypes.byref(p))
+        for k, v in kw.items():
+            if k in ("aggregate", "sap_block"):
+                v = (ctypes.c_int * 4)(*v)
+            setattr(p, k, v)
+        self.params = p
+        self.op = op  # keeps the operator alive
+        h = ctypes.c_void_p()
+        check(_lib.dd_amg_create(op.h, prec, ctypes.byref(p), _ptr(w0), ctypes.byref(h)), "dd_amg_create")
+        self.h = h
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.dd_amg_destroy(self.h)
+            self.h = None
+
+    def info(self):
+        cd = (ctypes.c_int * 4)()
+        dof, steps = ctypes.c_int(), ctypes.c_int()
+        sec = ctypes.c_double()
+        check(_lib.dd_amg_info(self.h, cd, ctypes.byref(dof), ctypes.byref(sec), ctypes.byref(steps)), "dd_amg_info")
+        return {"coarse_dims": tuple(cd), "dof_per_aggregate": dof.value, "setup_seconds": sec.value,
+                "last_coarse_steps": steps.value}
+
+    def coarse_operator(self):
+        import numpy as np
+        i = self.info()
+        nagg = int(np.prod(i["coarse_dims"]))
+        K = i["dof_per_aggregate"]
+        out = np.empty((nagg, 9, K, K), dtype=np.complex128)
+        check(_lib.dd_amg_coarse_download(self.h, out.ctypes.data), "dd_amg_coarse_download")
+        return out  # [agg][block][col][row]
+
+    def apply(self, v, z, nrhs, layout=DD_LAYOUT_CANONICAL, stream=None):
+        check(_lib.dd_amg_apply(self.h, _ptr(v), _ptr(z), nrhs, layout, _stream(stream)), "dd_amg_apply")

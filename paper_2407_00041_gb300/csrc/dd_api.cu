@@ -8,6 +8,7 @@
 #include "dd_internal.h"
 #include "dd_ops.h"
 #include "dd_sap.h"
+#include "dd_amg.h"
 
 namespace dd {
 const char* last_error();
@@ -451,6 +452,7 @@ void dd_solve_params_default(dd_solve_params* p) {
   for (int mu = 0; mu < 4; ++mu) p->sap_block[mu] = 4;
   p->sap_cycles = 1;
   p->sap_mr_steps = 4;
+  p->amg = nullptr;
 }
 
 int dd_solve(dd_clover* op, const dd_solve_params* params, const void* b, void* x, int nrhs, int layout,
@@ -458,8 +460,14 @@ int dd_solve(dd_clover* op, const dd_solve_params* params, const void* b, void* 
   if (!op || !params || !b || !x || nrhs < 1) return fail(DD_ERR_ARG, "null argument or nrhs < 1");
   if (layout != DD_LAYOUT_CANONICAL && layout != DD_LAYOUT_CANONICAL_HOST)
     return fail(DD_ERR_ARG, "dd_solve takes canonical fields");
-  if (params->precond < DD_PRECOND_NONE || params->precond > DD_PRECOND_SAP)
+  if (params->precond < DD_PRECOND_NONE || params->precond > DD_PRECOND_AMG)
     return fail(DD_ERR_ARG, "unknown preconditioner");
+  if (params->precond == DD_PRECOND_AMG) {
+    if (!params->amg || amg_operator(params->amg) != op)
+      return fail(DD_ERR_ARG, "DD_PRECOND_AMG needs an AMG handle of this operator");
+    if (amg_fine_precision(params->amg) != (params->inner_prec == DD_PREC_F64 ? P64 : P32))
+      return fail(DD_ERR_ARG, "AMG fine precision differs from the inner vector precision");
+  }
   if (params->precond == DD_PRECOND_SAP) {
     DD_TRY(sap_check_blocks(op->lat, params->sap_block, params->inner_prec == DD_PREC_F64 ? P64 : P32));
     if (params->sap_cycles < 1 || params->sap_mr_steps < 1) return fail(DD_ERR_ARG, "SAP cycles and MR steps >= 1");

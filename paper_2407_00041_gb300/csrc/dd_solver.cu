@@ -25,22 +25,29 @@
 //           method on the normal equations A^H A z = A^H v_j (from z = 0), run
 //           on the device with step sizes kept in device memory; Z_m is stored
 //           and x += Z_m y.
+//   amg     the flexible two-level preconditioner of dd_amg.cu (coarse-grid
+//           correction and SAP post-smoothing), for the even-odd system
+//           applied to (0, v_j) like sap;
 //   sap     the flexible preconditioner z_j = n red-black Schwarz cycles on
 //           D z = v_j (dd_sap.cu); for the even-odd system (A = Dhat, whose
 //           inverse is the odd-odd block of D^{-1}) z_j is the odd half of the
 //           cycles applied to the full field (0 on even sites, v_j on odd).
 #include <algorithm>
+#include <new>
 #include <chrono>
 #include <cmath>
 #include <complex>
 #include <cstdio>
 #include <cstdlib>
+#include <functional>
 #include <vector>
 
 #include "dd_blas.h"
 #include "dd_internal.h"
 #include "dd_ops.h"
 #include "dd_sap.h"
+#include "dd_krylov.h"
+#include "dd_amg.h"
 
 namespace dd {
 
@@ -80,6 +87,7 @@ struct Inner {
   int sap_block[4] = {4, 4, 4, 4};
   int sap_cycles = 1, sap_mr = 4;
   DevBuf sv, sz, sr;
+  dd_amg* amg = nullptr;  // DD_PRECOND_AMG
   // CG norms formed by the second stencil launch of Dhat (one RHS, FP32
   // vectors; DD_FUSED_NORM=0 turns it off): per-block partial sums
   bool fuse_norm = false;
@@ -88,6 +96,31 @@ struct Inner {
   Pinned hred, hcoef;
   // counters
   int applies = 0, steps = 0, cycles = 0;
+  // a custom operator (the AMG coarse system): vectors of L double2 groups
+  // (N right-hand sides innermost), FP64, no preconditioner
+  std::function<int(const void*, void*, cudaStream_t)> custom;
+
+  int init_custom(int64_t L_, int N_, int m_) {
+    mode = DD_PRECOND_NONE;
+    normal = false;
+    op = nullptr;
+    pg = pv = P64;
+    eo = false;
+    N = N_;
+    m = m_;
+    L = L_;
+    vbytes = (size_t)L_ * 16;
+    DD_TRY(basis.ensure(vbytes * (m + 1)));
+    DD_TRY(w.ensure(vbytes));
+    DD_TRY(rvec.ensure(vbytes));
+    const size_t nred = (size_t)(2 * (m + 1) + 1) * N;
+    DD_TRY(red.ensure(nred * sizeof(double2)));
+    DD_TRY(partials.ensure((size_t)blas_partials_len(N) * sizeof(double2)));
+    DD_TRY(coef.ensure((size_t)(m + 1) * N * sizeof(double2)));
+    if (!hred.p) DD_TRY(hred.alloc(nred * sizeof(double2)));
+    if (!hcoef.p) DD_TRY(hcoef.alloc((size_t)(m + 1) * N * sizeof(double2)));
+    return DD_OK;
+  }
 
   int init(const dd_clover* op_, int pg_, int pv_, bool eo_, int N_, int m_, int mode_) {
     mode = mode_;
@@ -108,7 +141,7 @@ struct Inner {
       DD_TRY(zt.ensure(vbytes));
       DD_TRY(ut.ensure(vbytes));
     }
-    if (mode == DD_PRECOND_SAP) {
+    if (mode == DD_PRECOND_SAP || mode == DD_PRECOND_AMG) {
       DD_TRY(zbasis.ensure(vbytes * m));
       const size_t fb = field_bytes(lat, pv, 0, N);
       DD_TRY(sv.ensure(fb));
@@ -143,6 +176,7 @@ struct Inner {
     for (int mu = 0; mu < 4; ++mu) sap_block[mu] = prm->sap_block[mu];
     sap_cycles = prm->sap_cycles;
     sap_mr = prm->sap_mr_steps;
+    amg = prm->amg;
   }
 
   void* V(int j) { return reinterpret_cast<char*>(basis.ptr) + vbytes * j; }
@@ -152,6 +186,7 @@ struct Inner {
   // the operator A of the inner system (Dhat or D)
   int apply_op(const void* in, void* out, bool dagger, cudaStream_t st) {
     ++applies;
+    if (custom) return custom(in, out, st);
     void* i = const_cast<void*>(in);
     if (eo) return op_Dhat(op, pg, pv, dagger, fv(i), fv(out), field_view(op->lat, pv, 2, tmp.ptr, N), st);
     return op_D(op, pg, pv, dagger, fv(i), fv(out), st);
@@ -191,6 +226,23 @@ struct Inner {
     DD_CUDA(cudaMemsetAsync(V.h[0].base, 0, hb, st));
     DD_CUDA(cudaMemcpyAsync(V.h[1].base, v, hb, cudaMemcpyDeviceToDevice, st));
     DD_TRY(sap_apply(op, pg, pv, sap_block, sap_cycles, sap_mr, V, Z, R, st));
+    DD_CUDA(cudaMemcpyAsync(z, Z.h[1].base, hb, cudaMemcpyDeviceToDevice, st));
+    return DD_OK;
+  }
+
+  // z = M^{-1} v of the AMG handle (full lattice), or for the even-odd
+  // system the odd half of M^{-1} (0, v)
+  int amgp(const void* v, void* z, cudaStream_t st) {
+    const dd_lattice* lat = op->lat;
+    if (!eo) {
+      Field Vin = field_view(lat, pv, 0, const_cast<void*>(v), N), Zout = field_view(lat, pv, 0, z, N);
+      return amg_apply(amg, Vin, Zout, st);
+    }
+    Field V = field_view(lat, pv, 0, sv.ptr, N), Z = field_view(lat, pv, 0, sz.ptr, N);
+    const size_t hb = field_bytes(lat, pv, 1, N);
+    DD_CUDA(cudaMemsetAsync(V.h[0].base, 0, hb, st));
+    DD_CUDA(cudaMemcpyAsync(V.h[1].base, v, hb, cudaMemcpyDeviceToDevice, st));
+    DD_TRY(amg_apply(amg, V, Z, st));
     DD_CUDA(cudaMemcpyAsync(z, Z.h[1].base, hb, cudaMemcpyDeviceToDevice, st));
     return DD_OK;
   }
@@ -308,11 +360,13 @@ struct Inner {
       int jmax = 0;
       for (int j = 0; j < m; ++j) {
         ++steps;
-        if (mode == DD_PRECOND_CGNR || mode == DD_PRECOND_SAP) {
+        if (mode == DD_PRECOND_CGNR || mode == DD_PRECOND_SAP || mode == DD_PRECOND_AMG) {
           if (mode == DD_PRECOND_CGNR)
             DD_TRY(cgnr(V(j), Zb(j), st));  // z_j = M_j^{-1} v_j
-          else
+          else if (mode == DD_PRECOND_SAP)
             DD_TRY(sap(V(j), Zb(j), st));
+          else
+            DD_TRY(amgp(V(j), Zb(j), st));
           DD_TRY(apply_op(Zb(j), w.ptr, false, st));  // w = A z_j
         } else {
           DD_TRY(apply(V(j), w.ptr, st));  // w = A z_j (z_j = v_j, or A^H v_j for the fixed preconditioner)
@@ -405,7 +459,8 @@ struct Inner {
         }
       DD_CUDA(cudaMemcpyAsync(dcoef, hc, (size_t)jmax * N * sizeof(double2), cudaMemcpyHostToDevice, st));
       VecList vs;
-      for (int i = 0; i < jmax; ++i) vs.p[i] = (mode == DD_PRECOND_CGNR || mode == DD_PRECOND_SAP) ? Zb(i) : V(i);
+      for (int i = 0; i < jmax; ++i)
+        vs.p[i] = (mode == DD_PRECOND_CGNR || mode == DD_PRECOND_SAP || mode == DD_PRECOND_AMG) ? Zb(i) : V(i);
       if (!normal) {
         DD_TRY(axpys(vs, jmax, dcoef, 1.0, e, st));  // e += Z_m y (Z_m = V_m without preconditioner)
       } else {
@@ -752,6 +807,34 @@ int solve(dd_clover* op, const dd_solve_params* prm, const double* b_canon, doub
   if (stats) *stats = s;
   if (status != DD_OK) set_error("solver reached its iteration limits");
   return status;
+}
+
+// ---- GMRES on a custom FP64 operator (the AMG coarse system) ----
+struct CoarseKrylov {
+  Inner inner;
+};
+
+CoarseKrylov* coarse_krylov_create(int64_t L, int N, int m, std::function<int(const void*, void*, cudaStream_t)> op) {
+  CoarseKrylov* k = new (std::nothrow) CoarseKrylov();
+  if (!k) return nullptr;
+  if (k->inner.init_custom(L, N, m) != DD_OK) {
+    delete k;
+    return nullptr;
+  }
+  k->inner.custom = std::move(op);
+  return k;
+}
+
+void coarse_krylov_destroy(CoarseKrylov* k) { delete k; }
+
+int coarse_krylov_solve(CoarseKrylov* k, const void* f, void* e, double tol_rel, int max_restarts, cudaStream_t st,
+                        int* steps) {
+  const int before = k->inner.steps;
+  std::vector<double> tol((size_t)k->inner.N, tol_rel);
+  DD_CUDA(cudaMemsetAsync(e, 0, k->inner.vbytes, st));
+  DD_TRY(k->inner.solve(f, e, tol, max_restarts, st, nullptr));
+  if (steps) *steps = k->inner.steps - before;
+  return DD_OK;
 }
 
 }  // namespace dd
