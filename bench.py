@@ -725,6 +725,22 @@ def run_cpu_solve(args):
             g = gn
         return z
 
+    if args.cpu_dhat_only:
+        # one application of Dhat and of Dhat^H, timed; the full solve makes
+        # about as many applications as the GPU solve with the same settings
+        v = eo.prepare(b).reshape(-1)
+        t0 = time.perf_counter()
+        Dhat(v)
+        t1 = time.perf_counter()
+        DhatH(v)
+        t2 = time.perf_counter()
+        per = 0.5 * ((t1 - t0) + (t2 - t1))
+        line = {"metric": f"CPU oracle time per Dhat application, {args.cpu_solve}, FP64", "value": per, "unit": "s",
+                "higher_is_better": False, "cores": oracle.threads(), "host_cpu": host_cpu_model(),
+                "dhat_s": t1 - t0, "dhatH_s": t2 - t1, "setup_s": t_setup,
+                "solve_estimate_s_for_904_applications": 904 * per}
+        print(json.dumps(line), flush=True)
+        return 0
     t0 = time.perf_counter()
     bhat = eo.prepare(b).reshape(-1)
     x_o, st = oracle.fgmres(Dhat, bhat, m=args.restart, tol=1e-10, max_restarts=200, M=cgnr)
@@ -764,6 +780,8 @@ def main():
     ap.add_argument("--restart", type=int, default=8, help="64^3x128 solve: FGMRES restart length")
     ap.add_argument("--cg-steps", type=int, default=64, help="64^3x128 solve: CG steps per preconditioner application")
     ap.add_argument("--cpu-solve", default=None, help="nT x nZ x nY x nX: time the CPU oracle's FP64 solve in full")
+    ap.add_argument("--cpu-dhat-only", action="store_true",
+                    help="with --cpu-solve: time one oracle Dhat and Dhat^H application instead of the full solve")
     ap.add_argument("--amg-solve", action="store_true", help="run the 48^3x96 solve with the AMG preconditioner")
     ap.add_argument("--amg-settings", default="8:4.4.4.4:1:2,16:4.4.4.4:1:4",
                     help="AMG settings n_tv:aT.aZ.aY.aX:init_sap:setup_iters, comma separated")
