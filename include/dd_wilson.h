@@ -439,7 +439,10 @@ int dd_batch_destroy(dd_batch* b);
 int dd_apply_batched(dd_batch* b, const void* const* ins, void* const* outs, void* stream);
 /* Time candidate launch shapes on `stream` and keep the fastest; optional
  * report of the chosen shape (slots per tile, threads per block, CTAs per SM,
- * where 0 CTAs per SM means one CTA per work item instead of a persistent grid). */
+ * where 0 CTAs per SM means one CTA per work item instead of a persistent
+ * grid, and -1 one launch per lattice with its own best single-lattice kernel
+ * on parallel streams, which dd_apply_batched_graph captures as parallel
+ * graph branches). */
 int dd_batch_tune(dd_batch* b, const void* const* ins, void* const* outs, void* stream, int* chosen3);
 /* Capture the batched launch in a CUDA graph on first call and replay it
  * afterwards (same pointers required; DD_ERR_ARG otherwise). */

@@ -8,9 +8,13 @@
 // in the persistent shape the grid is the resident CTA count (a multiple of
 // the SM count) and every CTA loops over many items; in the flat shape the
 // grid has one CTA per item.  There are no atomics, barriers or waits; each
-// thread finds its lattice in the item prefix table.  The autotuner
-// (dd_batch_tune) times tile sizes and both shapes, and the chosen launch
-// can be captured once in a CUDA graph and replayed.
+// thread finds its lattice in the item prefix table.  A third shape launches
+// every lattice with its own best single-lattice kernel (one thread per site
+// and RHS, or blocks of 2 or 4 RHS, each with its own register allocation) on
+// forked streams joined again at the end, which a CUDA graph captures as
+// parallel branches.  The autotuner (dd_batch_tune) times tile sizes and all
+// three shapes, and the chosen launch can be captured once in a CUDA graph
+// and replayed.
 #include <algorithm>
 #include <vector>
 
@@ -35,10 +39,17 @@ struct dd_batch {
   cudaGraph_t graph = nullptr;
   std::vector<const void*> g_in;
   std::vector<void*> g_out;
+  // the per-lattice shape (ctas_per_sm == -1): forked streams and events,
+  // lattices in decreasing order of work
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> order;
   ~dd_batch() {
     if (gexec) cudaGraphExecDestroy(gexec);
     if (graph) cudaGraphDestroy(graph);
     if (h_args) cudaFreeHost(h_args);
+    for (cudaStream_t q : side) cudaStreamDestroy(q);
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
   }
 };
 
@@ -125,8 +136,32 @@ void launch_t(dd_batch* b, unsigned grid, cudaStream_t st) {
                                         b->total_items);
 }
 
-// ctas_per_sm == 0 selects the flat shape (one CTA per item).
+// every lattice with its own kernel on a forked stream, joined back into st
+int launch_per_lattice(dd_batch* b, cudaStream_t st) {
+  if (b->side.empty()) {
+    b->side.resize(b->count);
+    b->ev.resize(b->count + 1);
+    for (int i = 0; i < b->count; ++i) DD_CUDA(cudaStreamCreateWithFlags(&b->side[i], cudaStreamNonBlocking));
+    for (int i = 0; i <= b->count; ++i) DD_CUDA(cudaEventCreateWithFlags(&b->ev[i], cudaEventDisableTiming));
+  }
+  DD_CUDA(cudaEventRecord(b->ev[b->count], st));
+  for (int k = 0; k < b->count; ++k) {
+    const int i = b->order[k];
+    dd_clover* op = b->ops[i];
+    Field fi = field_view(op->lat, b->prec, 0, const_cast<void*>(b->last_in[i]), b->nrhs[i]);
+    Field fo = field_view(op->lat, b->prec, 0, b->last_out[i], b->nrhs[i]);
+    DD_CUDA(cudaStreamWaitEvent(b->side[k], b->ev[b->count], 0));
+    DD_TRY(op_D(op, b->prec, b->prec, false, fi, fo, b->side[k]));
+    DD_CUDA(cudaEventRecord(b->ev[k], b->side[k]));
+  }
+  for (int k = 0; k < b->count; ++k) DD_CUDA(cudaStreamWaitEvent(st, b->ev[k], 0));
+  return DD_OK;
+}
+
+// ctas_per_sm == 0 selects the flat shape (one CTA per item), -1 the
+// per-lattice shape.
 int launch(dd_batch* b, cudaStream_t st) {
+  if (b->ctas_per_sm < 0) return launch_per_lattice(b, st);
   const int64_t g = b->ctas_per_sm > 0 ? (int64_t)b->sms * b->ctas_per_sm : b->total_items;
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, b->total_items));
   if (b->prec == P32) {
@@ -184,6 +219,11 @@ int dd_batch_create(dd_clover* const* ops, int count, int prec, const int* nrhs,
   dd_batch* b = new dd_batch;
   b->ops.assign(ops, ops + count);
   b->nrhs.assign(nrhs, nrhs + count);
+  b->order.resize(count);
+  for (int i = 0; i < count; ++i) b->order[i] = i;
+  std::sort(b->order.begin(), b->order.end(), [&](int x, int y) {
+    return ops[x]->lat->V * (int64_t)nrhs[x] > ops[y]->lat->V * (int64_t)nrhs[y];
+  });
   b->prec = prec;
   b->count = count;
   int dev = 0;
@@ -230,9 +270,10 @@ int dd_batch_tune(dd_batch* b, const void* const* ins, void* const* outs, void* 
   const int tiles[3] = {64, 128, 256};
   for (int ti = 0; ti < 3; ++ti) {
     const int cap = max_ctas(b->prec, tiles[ti]);
-    // persistent shapes at full and reduced residency, then the flat shape
-    const int shapes[4] = {cap, std::max(1, cap - 1), std::max(1, cap / 2), 0};
-    for (int ci = 0; ci < 4; ++ci) {
+    // persistent shapes at full and reduced residency, the flat shape, and
+    // (once) one launch per lattice
+    const int shapes[5] = {cap, std::max(1, cap - 1), std::max(1, cap / 2), 0, -1};
+    for (int ci = 0; ci < (ti == 0 ? 5 : 4); ++ci) {
       b->tile = tiles[ti];
       b->ctas_per_sm = shapes[ci];
       DD_TRY(stage(b, ins, outs, st));

@@ -256,7 +256,76 @@ __device__ __forceinline__ void atomic_add_m3(float* G, const M3<float>& m, bool
   for (int q = 0; q < kGf / 4; ++q) red_add_v4(G + 4 * q, v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
 }
 
-// One thread per site: self-coupling contribution, accumulated atomically.
+// The self-coupling contribution of site c for plane (mu, nu): T' from the
+// spinors (summed over right-hand sides), then for each of the four leaves
+// of Q_munu(x) (Eq. 1.12) the derivatives R_k of its four factors, handed to
+// emit(site coordinates, direction, R_k, add R_k^H instead).
+template <typename R, typename Emit>
+__device__ __forceinline__ void clover_plane_leaves(const FGeom& g, const double2* __restrict__ U64,
+                                                    const double2* __restrict__ phi, const double2* __restrict__ psi,
+                                                    int nrhs, double csw, const int c[4], int mu, int nu, Emit emit) {
+  const int x = ((c[0] * g.n[1] + c[1]) * g.n[2] + c[2]) * g.n[3] + c[3];
+  cx<R> ph[12], ps[12];
+  // T[b][a] = -(c_sw/32) sum_{s,s'} gg[s][s'] psi[s'][b] conj(phi[s][a]), summed over RHS
+  M3<R> T;
+  for (int e = 0; e < 9; ++e) T.m[e] = zero<R>();
+  for (int r = 0; r < nrhs; ++r) {
+    load_canon<R>(phi + (int64_t)r * g.V * 12, x, ph);
+    load_canon<R>(psi + (int64_t)r * g.V * 12, x, ps);
+    for (int s = 0; s < 4; ++s)
+      for (int sp = 0; sp < 4; ++sp) {
+        const cx<double> w = gg(mu, nu, s, sp);
+        if (w.re == 0.0 && w.im == 0.0) continue;
+        const cx<R> wr = mk<R>((R)w.re, (R)w.im);
+        for (int b = 0; b < 3; ++b)
+          for (int a = 0; a < 3; ++a)
+            T.m[3 * b + a] = cfmac(ph[3 * s + a], cmul(wr, ps[3 * sp + b]), T.m[3 * b + a]);
+      }
+  }
+  // T' = 2 (T - T^H) scaled by -(c_sw / 32)
+  M3<R> Tp;
+  const R f = (R)(-2.0 * csw / 32.0);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      Tp.m[3 * i + j] = f * mk(T.m[3 * i + j].re - T.m[3 * j + i].re, T.m[3 * i + j].im + T.m[3 * j + i].im);
+  // the four leaves of Q_munu(x), Eq. 1.12: factor sites, directions, daggers
+  int xpm[4], xpn[4], xmm[4], xmn[4], xmm_pn[4], xmm_mn[4], xmn_pm[4];
+  auto sh = [&](const int* a, int d, int st, int* o) {
+    for (int i = 0; i < 4; ++i) o[i] = a[i];
+    o[d] = (a[d] + st + g.n[d]) % g.n[d];
+  };
+  sh(c, mu, +1, xpm);
+  sh(c, nu, +1, xpn);
+  sh(c, mu, -1, xmm);
+  sh(c, nu, -1, xmn);
+  sh(xmm, nu, +1, xmm_pn);
+  sh(xmm, nu, -1, xmm_mn);
+  sh(xmn, mu, +1, xmn_pm);
+  const int* site[4][4] = {{c, xpm, xpn, c}, {c, xmm_pn, xmm, xmm}, {xmm, xmm_mn, xmm_mn, xmn}, {xmn, xmn, xmn_pm, c}};
+  const int dir[4][4] = {{mu, nu, mu, nu}, {nu, mu, nu, mu}, {mu, nu, mu, nu}, {nu, mu, nu, mu}};
+  const int dag[4][4] = {{0, 0, 1, 1}, {0, 1, 1, 0}, {1, 1, 0, 0}, {1, 0, 0, 1}};
+  for (int l = 0; l < 4; ++l) {
+    M3<R> F[4];
+    for (int k = 0; k < 4; ++k) {
+      M3<R> u = load_link<R>(g, U64, site[l][k], dir[l][k]);
+      F[k] = dag[l][k] ? mdag(u) : u;
+    }
+    // R_k = F_{k+1} .. F_3 T' F_0 .. F_{k-1} from the suffix products
+    // S_k = F_{k+1} .. F_3 T' and the prefix products P_k = F_0 .. F_{k-1}:
+    // eight 3x3 products per leaf instead of twelve
+    const M3<R> S2 = mmul(F[3], Tp);
+    const M3<R> S1 = mmul(F[2], S2);
+    emit(site[l][0], dir[l][0], mmul(F[1], S1), dag[l][0] == 0);
+    emit(site[l][1], dir[l][1], mmul(S1, F[0]), dag[l][1] == 0);
+    const M3<R> P2 = mmul(F[0], F[1]);
+    emit(site[l][2], dir[l][2], mmul(S2, P2), dag[l][2] == 0);
+    emit(site[l][3], dir[l][3], mmul(Tp, mmul(P2, F[2])), dag[l][3] == 0);
+  }
+}
+
+// One thread per site: self-coupling contribution, accumulated atomically in
+// G (FP64 atomics) or in the padded FP32 workspace (16-byte vector
+// reductions).
 template <typename R, typename GT>
 __global__ void k_force_clover(FGeom g, const double2* __restrict__ U64, const double2* __restrict__ phi,
                                const double2* __restrict__ psi, int nrhs, double csw, GT* G) {
@@ -265,70 +334,13 @@ __global__ void k_force_clover(FGeom g, const double2* __restrict__ U64, const d
   if (x >= g.V) return;
   int c[4];
   coords_of(g, x, c);
-  cx<R> ph[12], ps[12];
   for (int mu = 0; mu < 4; ++mu)
-    for (int nu = mu + 1; nu < 4; ++nu) {
-      // T[b][a] = -(c_sw/32) sum_{s,s'} gg[s][s'] psi[s'][b] conj(phi[s][a]), summed over RHS
-      M3<R> T;
-      for (int e = 0; e < 9; ++e) T.m[e] = zero<R>();
-      for (int r = 0; r < nrhs; ++r) {
-        load_canon<R>(phi + (int64_t)r * g.V * 12, x, ph);
-        load_canon<R>(psi + (int64_t)r * g.V * 12, x, ps);
-        for (int s = 0; s < 4; ++s)
-          for (int sp = 0; sp < 4; ++sp) {
-            const cx<double> w = gg(mu, nu, s, sp);
-            if (w.re == 0.0 && w.im == 0.0) continue;
-            const cx<R> wr = mk<R>((R)w.re, (R)w.im);
-            for (int b = 0; b < 3; ++b)
-              for (int a = 0; a < 3; ++a)
-                T.m[3 * b + a] = cfmac(ph[3 * s + a], cmul(wr, ps[3 * sp + b]), T.m[3 * b + a]);
-          }
-      }
-      // T' = 2 (T - T^H) scaled by -(c_sw / 32)
-      M3<R> Tp;
-      const R f = (R)(-2.0 * csw / 32.0);
-      for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j)
-          Tp.m[3 * i + j] = f * mk(T.m[3 * i + j].re - T.m[3 * j + i].re, T.m[3 * i + j].im + T.m[3 * j + i].im);
-      // the four leaves of Q_munu(x), Eq. 1.12: factor sites, directions, daggers
-      int xpm[4], xpn[4], xmm[4], xmn[4], xmm_pn[4], xmm_mn[4], xmn_pm[4];
-      auto sh = [&](const int* a, int d, int st, int* o) {
-        for (int i = 0; i < 4; ++i) o[i] = a[i];
-        o[d] = (a[d] + st + g.n[d]) % g.n[d];
-      };
-      sh(c, mu, +1, xpm);
-      sh(c, nu, +1, xpn);
-      sh(c, mu, -1, xmm);
-      sh(c, nu, -1, xmn);
-      sh(xmm, nu, +1, xmm_pn);
-      sh(xmm, nu, -1, xmm_mn);
-      sh(xmn, mu, +1, xmn_pm);
-      const int* site[4][4] = {{c, xpm, xpn, c}, {c, xmm_pn, xmm, xmm}, {xmm, xmm_mn, xmm_mn, xmn}, {xmn, xmn, xmn_pm, c}};
-      const int dir[4][4] = {{mu, nu, mu, nu}, {nu, mu, nu, mu}, {mu, nu, mu, nu}, {nu, mu, nu, mu}};
-      const int dag[4][4] = {{0, 0, 1, 1}, {0, 1, 1, 0}, {1, 1, 0, 0}, {1, 0, 0, 1}};
-      for (int l = 0; l < 4; ++l) {
-        M3<R> F[4];
-        for (int k = 0; k < 4; ++k) {
-          M3<R> u = load_link<R>(g, U64, site[l][k], dir[l][k]);
-          F[k] = dag[l][k] ? mdag(u) : u;
-        }
-        // R_k = F_{k+1} .. F_3 T' F_0 .. F_{k-1} from the suffix products
-        // S_k = F_{k+1} .. F_3 T' and the prefix products P_k = F_0 .. F_{k-1}:
-        // eight 3x3 products per leaf instead of twelve
-        auto emit = [&](int k, const M3<R>& Rk) {
-          const int* sc = site[l][k];
-          const int lex = ((sc[0] * g.n[1] + sc[1]) * g.n[2] + sc[2]) * g.n[3] + sc[3];
-          atomic_add_m3(G + ((int64_t)lex * 4 + dir[l][k]) * kStride, Rk, dag[l][k] == 0);
-        };
-        const M3<R> S2 = mmul(F[3], Tp);
-        const M3<R> S1 = mmul(F[2], S2);
-        emit(0, mmul(F[1], S1));
-        emit(1, mmul(S1, F[0]));
-        const M3<R> P2 = mmul(F[0], F[1]);
-        emit(2, mmul(S2, P2));
-        emit(3, mmul(Tp, mmul(P2, F[2])));
-      }
-    }
+    for (int nu = mu + 1; nu < 4; ++nu)
+      clover_plane_leaves<R>(g, U64, phi, psi, nrhs, csw, c, mu, nu,
+                             [&](const int* sc, int d, const M3<R>& Rk, bool dagger) {
+                               const int lex = ((sc[0] * g.n[1] + sc[1]) * g.n[2] + sc[2]) * g.n[3] + sc[3];
+                               atomic_add_m3(G + ((int64_t)lex * 4 + d) * kStride, Rk, dagger);
+                             });
 }
 
 __device__ __forceinline__ cx<double> load_g(const double2* G, int64_t t, int e) {
