@@ -69,14 +69,17 @@ def log(msg):
     print(f"[bench {time.time() - _T0:7.1f}s] {msg}", file=sys.stderr, flush=True)
 
 
-LINK_ROWS_F32 = [3]  # rows per FP32 link read by single-RHS applies (set once the gauge exists)
+LINK_REALS_F32 = [18]  # reals per FP32 link read by single-RHS applies (set once the gauge exists)
+LINK_REALS_F16 = [18]  # the same for FP16 links
 HBM_PEAK = [6800.0]  # GB/s, replaced by the measured copy bandwidth at start
 
 
 def bytes_per_site(prec, nrhs=1):
     a, b = BYTES[prec]
-    if prec == "f32" and nrhs == 1 and LINK_ROWS_F32[0] == 2:
-        a -= 96  # two-row FP32 links: 192 instead of 288 B per site
+    if prec == "f32" and nrhs == 1:
+        a -= 288 - 16 * LINK_REALS_F32[0]  # compressed FP32 links: 192 (12 reals) or 128 (8) instead of 288 B
+    if prec == "f16" and nrhs == 1:
+        a -= 144 - 8 * LINK_REALS_F16[0]  # two-row FP16 links: 96 instead of 144 B
     return a + b * nrhs
 
 
@@ -237,7 +240,8 @@ def kernel_source_hash():
     h = hashlib.sha256()
     for f in sorted(glob.glob(os.path.join(ROOT, "paper_2407_00041_gb300", "csrc", "dd_hop*")) +
                     [os.path.join(ROOT, "paper_2407_00041_gb300", "csrc", "dd_device.cuh"),
-                     os.path.join(ROOT, "paper_2407_00041_gb300", "csrc", "dd_ops.h")]):
+                     os.path.join(ROOT, "paper_2407_00041_gb300", "csrc", "dd_ops.h"),
+                     os.path.join(ROOT, "paper_2407_00041_gb300", "csrc", "dd_link8.cuh")]):
         with open(f, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -411,7 +415,7 @@ def extra_measurements(dd, torch, stream, op48, psi48, V48, tdist, clocks, alu_p
                                                       dd.DD_LAYOUT_NATIVE, st), "Dhat"), 20)
         # two half-lattice hops read every link twice; A_oo and A_ee^-1 once;
         # five half-field spinor passes (psi_o twice, t_e written and read, out_o)
-        link, clov, spin = {"f32": (96 * LINK_ROWS_F32[0], 288, 96), "f16": (144, 144, 52)}[name]
+        link, clov, spin = {"f32": (16 * LINK_REALS_F32[0], 288, 96), "f16": (8 * LINK_REALS_F16[0], 144, 52)}[name]
         bytes_ = 2 * link * V48 + clov * V48 + 5 * spin * (V48 // 2)
         out[f"dhat_{name}"] = {"ms": t * 1e3, "gbs_formula": bytes_ / t / 1e9}
     # domain-decomposed D psi (Algorithm 3 on virtual ranks of this GPU): the
@@ -769,6 +773,7 @@ def main():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the multi-RHS, batch, Dhat and adjoint lines")
+    ap.add_argument("--no-link8", action="store_true", help="skip the eight-real FP32 link apply and solve")
     ap.add_argument("--solve-inner", default="f32", choices=["f32", "f16"])
     ap.add_argument("--dims", default="96x48x48x48", help="nT x nZ x nY x nX (a smaller lattice for profiling)")
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides of the timed D psi (profiling)")
@@ -827,8 +832,10 @@ def main():
     op = dd.Operator(gauge, M0, CSW)
     # SU(3) links: the FP32 copy keeps two rows per link (192 instead of 288 B)
     rows32 = dd.lib.dd_gauge_stored_rows(gauge.h, dd.DD_PREC_F32)
-    LINK_ROWS_F32[0] = rows32
-    log(f"handles ready (single-RHS FP32 applies read {rows32} rows per link)")
+    reals32 = gauge.link_reals(dd.DD_PREC_F32)
+    LINK_REALS_F32[0] = reals32
+    LINK_REALS_F16[0] = gauge.link_reals(dd.DD_PREC_F16)
+    log(f"handles ready (single-RHS FP32 applies read {reals32} reals per link)")
     psi_dev = torch.from_numpy(psi).to("cuda")
 
     gpu_launches = 0
@@ -882,13 +889,15 @@ def main():
                           "roof_frac": frac, "bytes_per_site": bytes_per_site(prec, N)}
         rooflines[prec] = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": frac,
                            "traffic": (profile_traffic(prec) if N == 1 and dims == DIMS and
-                                       (prec != "f32" or LINK_ROWS_F32[0] == 2) else None),
+                                       (prec != "f32" or LINK_REALS_F32[0] == 12) and
+                                       (prec != "f16" or LINK_REALS_F16[0] == 12) else None),
                            "ms_per_apply": kern * 1e3,
                            "peak_source": f"{peak_kind} MEASURED_PEAKS.json hbm_gbs" if bound == "hbm"
                            else "FMA-chain probe dd_probe_flops on this GPU (FP64 pipe)" if prec == "f64"
                            else "FMA-chain probe dd_probe_flops on this GPU (FP32 pipe)"}
         if prec == args.prec:
-            traffic = (profile_traffic(prec) if N == 1 and dims == DIMS and (prec != "f32" or LINK_ROWS_F32[0] == 2)
+            traffic = (profile_traffic(prec) if N == 1 and dims == DIMS and (prec != "f32" or LINK_REALS_F32[0] == 12) and
+                       (prec != "f16" or LINK_REALS_F16[0] == 12)
                        else None)  # the captured launch: 48^3x96, one RHS, two-row FP32 links
             head = {"value": gbs, "ms": ms, "kernel_s": kern,
                     "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": frac,
@@ -903,6 +912,72 @@ def main():
                 op.unpack(p, 0, xout, out_c, N)
             head["_out"] = out_c
         del xin, xout
+
+    # the eight-real FP32 links (dd_gauge_compress_links): the FP32 apply
+    # reading 128 instead of 192 B of links per site, checked against the
+    # two-row result of the same input
+    if N == 1 and reals32 == 12 and not args.no_link8:
+        try:
+            gauge.compress_links(8)
+        except dd.DDError as e:
+            log(f"eight-real FP32 links not available: {e}")
+        else:
+            LINK_REALS_F32[0] = 8
+            p = PREC["f32"]
+            xin = torch.empty(op.field_bytes(p, 0, N), dtype=torch.uint8, device="cuda")
+            xout = torch.empty_like(xin)
+            op.pack(p, 0, psi_dev, xin, N)
+
+            def step8():
+                dd.check(dd.lib.dd_apply(op.h, dd.DD_OP_D, p, xin.data_ptr(), xout.data_ptr(), N,
+                                         dd.DD_LAYOUT_NATIVE, stream.cuda_stream), "dd_apply")
+
+            log("timing D psi in f32 with eight-real links")
+            steps = max(10, min(args.steps, 50))
+            total, per = time_steps(step8, steps, args.warmup, stream, tdist, None)
+            kern = statistics.mean(per)
+            out8 = torch.empty_like(psi_dev)
+            op.unpack(p, 0, xout, out8, N)
+            v = {"ms_per_apply": total / steps * 1e3, "kernel_ms": kern * 1e3,
+                 "bytes_per_site": bytes_per_site("f32", N),
+                 "hbm_frac": bytes_per_site("f32", N) * V / kern / 1e9 / peaks["hbm_gbs"],
+                 "gbs": aggregate_gbs(bytes_per_site("f32", N), V, world, total / steps)}
+            if "f32" in variants:
+                v["speedup_over_two_row"] = variants["f32"]["ms_per_apply"] / v["ms_per_apply"]
+            gauge.compress_links(12)
+            LINK_REALS_F32[0] = 12
+            step8()  # the same apply with the two-row links
+            out12 = torch.empty_like(psi_dev)
+            op.unpack(p, 0, xout, out12, N)
+            torch.cuda.synchronize()
+            v["rel_diff_vs_two_row"] = ((out8 - out12).norm() / out12.norm()).item()
+            variants["f32_link8"] = v
+            del xin, xout, out8, out12
+
+    # the FP16 apply with three-row FP16 links, beside the two-row default
+    if N == 1 and LINK_REALS_F16[0] == 12 and "f16" in variants and not args.no_link8:
+        gauge.compress_links(18, dd.DD_PREC_F16)
+        LINK_REALS_F16[0] = 18
+        p = PREC["f16"]
+        xin = torch.empty(op.field_bytes(p, 0, N), dtype=torch.uint8, device="cuda")
+        xout = torch.empty_like(xin)
+        op.pack(p, 0, psi_dev, xin, N)
+
+        def step18():
+            dd.check(dd.lib.dd_apply(op.h, dd.DD_OP_D, p, xin.data_ptr(), xout.data_ptr(), N,
+                                     dd.DD_LAYOUT_NATIVE, stream.cuda_stream), "dd_apply")
+
+        log("timing D psi in f16 with three-row links")
+        steps = max(10, min(args.steps, 50))
+        total, per = time_steps(step18, steps, args.warmup, stream, tdist, None)
+        kern = statistics.mean(per)
+        variants["f16_link18"] = {"ms_per_apply": total / steps * 1e3, "kernel_ms": kern * 1e3,
+                                  "bytes_per_site": bytes_per_site("f16", N),
+                                  "hbm_frac": bytes_per_site("f16", N) * V / kern / 1e9 / peaks["hbm_gbs"],
+                                  "two_row_speedup": total / steps * 1e3 / variants["f16"]["ms_per_apply"]}
+        del xin, xout
+        gauge.compress_links(12, dd.DD_PREC_F16)
+        LINK_REALS_F16[0] = 12
 
     # e2e through the C ABI on pinned host buffers
     p = PREC[args.prec]
@@ -934,18 +1009,25 @@ def main():
         # settings that suit its less accurate inner operator (measured: 2.0 s
         # with 32 CG steps and inner tolerance 1e-3 against 2.8 s with the
         # FP32 settings)
-        legs = [("mixed", PREC[args.solve_inner], 8, 64, 1e-6), ("fp64", PREC["f64"], 8, 64, 1e-6)]
+        # the last field: reals per FP32 link of the inner operator
+        legs = [("mixed", PREC[args.solve_inner], 8, 64, 1e-6, reals32), ("fp64", PREC["f64"], 8, 64, 1e-6, reals32)]
         if args.solve_inner != "f16":
-            legs.insert(1, ("mixed_f16", PREC["f16"], 8, 32, 1e-3))
-        for name, inner, restart, cg, tol_in in legs:
+            legs.insert(1, ("mixed_f16", PREC["f16"], 8, 32, 1e-3, reals32))
+        if args.solve_inner == "f32" and "f32_link8" in variants:
+            legs.insert(1, ("mixed_link8", PREC["f32"], 8, 64, 1e-6, 8))
+        for name, inner, restart, cg, tol_in, reals in legs:
             x = torch.zeros_like(b)
             log(f"solve {name}")
+            if reals != reals32:
+                gauge.compress_links(reals)
             barrier(tdist)
             w0 = time.time()
             status, st = op.solve(b, x, 1, tol=1e-10, inner_prec=inner, restart=restart, max_restarts=100,
                                   max_outer=20, precond=dd.DD_PRECOND_CGNR, precond_iters=cg, inner_tol=tol_in)
             w1 = time.time()
             clocks.window(w0, w1)
+            if reals != reals32:
+                gauge.compress_links(reals32)
             sols[name] = x
             log(f"solve {name}: {st}")
             solve[name] = {"seconds": max_over_ranks(tdist, st["seconds"]), "status": status,
@@ -953,6 +1035,7 @@ def main():
                            "inner_steps": st["inner_iterations"], "applies_inner": st["applies_inner"],
                            "applies_fp64": st["applies_fp64"],
                            "inner_prec": {1: "f64", 2: "f32", 4: "f16 links/clover, f32 vectors"}[inner],
+                           "f32_link_reals": reals,
                            "method": f"even-odd FGMRES({restart}), M_j = {cg} CG steps on Dhat^H Dhat, "
                                      f"inner tolerance {tol_in:g}, FP64 refinement"}
         d = (sols["mixed"] - sols["fp64"]).norm().item() / sols["fp64"].norm().item()
@@ -962,6 +1045,10 @@ def main():
             solve["mixed_f16_vs_fp64_solution_rel_diff"] = \
                 (sols["mixed_f16"] - sols["fp64"]).norm().item() / sols["fp64"].norm().item()
             solve["speedup_mixed_f16_over_fp64"] = solve["fp64"]["seconds"] / solve["mixed_f16"]["seconds"]
+        if "mixed_link8" in solve:
+            solve["mixed_link8_vs_fp64_solution_rel_diff"] = \
+                (sols["mixed_link8"] - sols["fp64"]).norm().item() / sols["fp64"].norm().item()
+            solve["speedup_mixed_link8_over_fp64"] = solve["fp64"]["seconds"] / solve["mixed_link8"]["seconds"]
 
     extra = None
     if not args.no_extra:
@@ -996,6 +1083,7 @@ def main():
         "config": {"workload": (WORKLOAD if dims == DIMS else WORKLOAD.replace("48^3x96", args.dims)).replace(
                        "1 RHS", f"{N} RHS"),
                    "precision": args.prec, "nrhs": N, "sites": V, "f32_link_rows_single_rhs": rows32,
+                   "f32_link_reals_single_rhs": reals32, "f16_link_reals_single_rhs": LINK_REALS_F16[0],
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "inputs (>8 GB) larger than L2; no flush"},
         "roofline": head["roofline"], "roofline_by_precision": rooflines, "variants": variants, "e2e": e2e,

@@ -73,7 +73,11 @@
  * thread.
  *
  * Environment (each read once per process, at first use; all optional):
- *   DD_RECON=0          no two-row FP32 link copy at dd_gauge_create (the
+ *   DD_RECON=r          form of the compressed FP32 / FP16 link copies made
+ *                       at dd_gauge_create for SU(3) links (see
+ *                       dd_gauge_compress_links): 12 two rows (default), 8
+ *                       eight reals for FP32 (two rows where they do not
+ *                       rebuild to 1e-6) and two rows for FP16, 0 none (the
  *                       single-RHS kernels then read three rows).
  *   DD_RHS_BLOCK=n      largest RHS block of the multi-RHS stencil (1, 2 or
  *                       4; default 4; 1 gives one thread per site and RHS,
@@ -154,16 +158,56 @@ int dd_lattice_destroy(dd_lattice* lat);
 int64_t dd_lattice_volume(const dd_lattice* lat);
 
 /* Rows per link that single-RHS applies read in precision `prec`
- * (DD_PREC_F64 / F32 / F16): 3, or 2 for DD_PREC_F32 when every link passed
- * to dd_gauge_create is an SU(3) matrix to 1e-6 (max of |U U^H - 1| and
- * |det U - 1|).  The gauge handle then holds a second FP32 copy with rows 0
- * and 1 only (192 instead of 288 bytes per site), and single-RHS stencils
- * rebuild row 2 as the complex conjugate of the cross product of rows 0 and
- * 1, which holds for SU(3) matrices (Section 1.1 of the thesis defines the
- * links as SU(3) elements); several-RHS launches keep reading three rows.
- * The environment variable DD_RECON=0, read at gauge creation, skips the
- * two-row copy.  DD_ERR_UNSUPPORTED if the copy of `prec` was not created. */
+ * (DD_PREC_F64 / F32 / F16): 3, or 2 for DD_PREC_F32 and DD_PREC_F16 when
+ * every link passed to dd_gauge_create is an SU(3) matrix to 1e-6 (max of
+ * |U U^H - 1| and |det U - 1|).  The gauge handle then holds second FP32 and
+ * FP16 copies with rows 0 and 1 only (FP32 192 instead of 288 bytes per site,
+ * FP16 96 instead of 144), and single-RHS stencils rebuild row 2 as the
+ * complex conjugate of the cross product of rows 0 and 1, which holds for
+ * SU(3) matrices (Section 1.1 of the thesis defines the links as SU(3)
+ * elements); several-RHS launches keep reading three rows.  The environment
+ * variable DD_RECON=0, read at gauge creation, skips the two-row copies.
+ * DD_ERR_UNSUPPORTED if the copy of `prec` was not created.  With the
+ * eight-real FP32 copy (dd_gauge_compress_links) this returns 3 for
+ * DD_PREC_F32: use dd_gauge_link_reals. */
 int dd_gauge_stored_rows(const dd_gauge* g, int prec);
+
+/* Real numbers per link that single-RHS applies read in precision `prec`:
+ * 18 (three rows), 12 (two rows, DD_PREC_F32 / F16) or 8 (DD_PREC_F32).
+ * DD_ERR_ARG / DD_ERR_UNSUPPORTED as dd_gauge_stored_rows. */
+int dd_gauge_link_reals(const dd_gauge* g, int prec);
+
+/* Choose the compressed link copy that single-RHS applies of precision
+ * `prec` (DD_PREC_F32 or DD_PREC_F16) read (Section 2.3 stores the links of
+ * the stencil; an SU(3) matrix has 8 real degrees of freedom, Section 1.1):
+ *   reals = 18  no copy: the three-row links (FP32 288 bytes per site, FP16
+ *               144);
+ *   reals = 12  rows 0 and 1 (FP32 192 bytes per site, FP16 96), row 2
+ *               rebuilt as the complex conjugate of the cross product of rows
+ *               0 and 1 (FP16: exact products of the stored values, FP32
+ *               sums, one rounding to FP16);
+ *   reals = 8   FP32 only: two float4 words per link (128 bytes per site):
+ *               W = S U C, C a cyclic column shift putting the largest
+ *               element of row 0 first, S keeping rows 1, 2 or replacing them
+ *               by (row 2, -row 1) so that the stored lower entry of column 0
+ *               is the smaller one; stored are W01, W02, W10 and the phases
+ *               of W00 and W20 (divided by pi), the shift and swap in the
+ *               lowest mantissa bits of three of the stored values.  The
+ *               stencil rebuilds |W00| and |W20| from the unit norms of row 0
+ *               and column 0, W11 and W12 from the orthogonality of rows 0
+ *               and 1 and from W20 = conj(W01 W12 - W02 W11) (a 2x2 solve of
+ *               determinant |W01|^2 + |W02|^2), and row 2 as for 12.
+ * 12 and 8 need links of `prec` in the handle and every link SU(3) to 1e-6
+ * (dd_gauge_stored_rows); 8 also checks every rebuilt element against the
+ * FP64 link and keeps the previous form when one is off by more than 1e-6
+ * (the parametrisation is singular where W01 = W02 = 0, e.g. unit links).
+ * Several-RHS launches always read the three-row links.  Domains made by
+ * dd_decomp_create copy the FP32 two-row form current at their creation
+ * (they read three rows with the eight-real form and in FP16).
+ * Synchronises the device; no launch may use the handle meanwhile.
+ * DD_ERR_ARG for another `prec` or `reals`; DD_ERR_UNSUPPORTED (previous form
+ * kept) when the links or the precision do not allow the form. */
+int dd_gauge_compress_links(dd_gauge* g, int prec, int reals);
 
 /*
  * Gauge field U_mu(x) in SU(3) (Section 1.1), given as complex double

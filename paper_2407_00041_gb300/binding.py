@@ -98,6 +98,8 @@ SIGNATURES = {
     "dd_probe_flops": (_I, [_I, _P, _P]),
     "dd_device_status": (_I, [_P]),
     "dd_gauge_stored_rows": (_I, [_P, _I]),
+    "dd_gauge_link_reals": (_I, [_P, _I]),
+    "dd_gauge_compress_links": (_I, [_P, _I, _I]),
     "dd_dot_noalloc": (_I, [_P, _P, _L, _I, _P, _P]),
     "dd_decomp_create": (_I, [_P, _P, _P]),
     "dd_decomp_destroy": (_I, [_P]),
@@ -201,6 +203,16 @@ class Gauge:
         else:
             check(_lib.dd_gauge_download(self.h, _ptr(out), 1 if out.is_cuda else 0), "dd_gauge_download")
         return out
+
+    def link_reals(self, prec=DD_PREC_F32):
+        """Reals per link read by single-RHS applies in `prec` (18, 12 or 8)."""
+        r = _lib.dd_gauge_link_reals(self.h, prec)
+        check(min(r, 0), "dd_gauge_link_reals")
+        return r
+
+    def compress_links(self, reals, prec=DD_PREC_F32):
+        """Compressed link copy of `prec` with 18 (none), 12 or (FP32) 8 reals per link."""
+        check(_lib.dd_gauge_compress_links(self.h, prec, reals), "dd_gauge_compress_links")
 
     def __del__(self):
         if getattr(self, "h", None) and _lib is not None:

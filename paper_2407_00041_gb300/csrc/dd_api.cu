@@ -207,14 +207,59 @@ int gauge_alloc(const dd_lattice* lat, unsigned prec_mask, dd_gauge** out) {
   return DD_OK;
 }
 
-// After the links are in place: SU(3) check, the two-row FP32 copy when
-// every link is SU(3) to FP32 accuracy (DD_RECON=0 keeps all three rows),
-// and a device synchronisation.
+constexpr double kSu3Tol = 1e-6;    // links taken as SU(3) (max |U U^H - 1|, |det U - 1|)
+constexpr double kLink8Tol = 1e-6;  // largest element error of the eight-real copy
+
+// The compressed copy of precision `prec` with `reals` per link (FP32: 18
+// none, 12 two rows, 8 eight reals; FP16: 18, 12); on DD_ERR_UNSUPPORTED the
+// previous form is kept.
+int compress_links(dd_gauge* g, int prec, int reals) {
+  if (prec == DD_PREC_F16) {
+    if (reals == 18) {
+      g->links16r.release();
+      g->recon16 = 0;
+      return DD_OK;
+    }
+    if (reals != 12) return fail(DD_ERR_UNSUPPORTED, "FP16 links take 18 or 12 reals");
+    if (!(g->prec_mask & DD_PREC_F16)) return fail(DD_ERR_UNSUPPORTED, "no FP16 links in the gauge handle");
+    if (!(g->su3_deviation < kSu3Tol)) return fail(DD_ERR_UNSUPPORTED, "links are not SU(3) to 1e-6");
+    return links_to_recon16(g, 0);
+  }
+  if (reals == 18) {
+    g->links32r.release();
+    g->recon32 = 0;
+    return DD_OK;
+  }
+  if (!(g->prec_mask & DD_PREC_F32)) return fail(DD_ERR_UNSUPPORTED, "no FP32 links in the gauge handle");
+  if (!(g->su3_deviation < kSu3Tol)) return fail(DD_ERR_UNSUPPORTED, "links are not SU(3) to 1e-6");
+  if (reals == 12) return links_to_recon32(g, 0);
+  const int before = g->recon32;
+  double dev = 0.0;
+  DD_TRY(links_to_recon8(g, &dev, 0));
+  if (dev <= kLink8Tol) return DD_OK;
+  const int s = before == 12 ? links_to_recon32(g, 0) : compress_links(g, prec, 18);
+  if (s != DD_OK) return s;
+  return fail(DD_ERR_UNSUPPORTED, "eight-real links rebuild to " + std::to_string(dev) + " > 1e-6");
+}
+
+// After the links are in place: SU(3) check, the compressed FP32 and FP16
+// copies when every link is SU(3) to FP32 accuracy (DD_RECON: 12 rows 0 and
+// 1, the default; 8 eight reals for FP32, else two rows; 0 none), and a
+// device synchronisation.
 int gauge_finish(dd_gauge* g) {
   int s = links_su3_deviation(g, &g->su3_deviation, 0);
-  if (s == DD_OK && (g->prec_mask & DD_PREC_F32) && g->su3_deviation < 1e-6) {
-    const char* e = getenv("DD_RECON");
-    if (!e || atoi(e) != 0) s = links_to_recon32(g, 0);
+  const char* e = getenv("DD_RECON");
+  const int want = e ? atoi(e) : 12;
+  if (s == DD_OK && want != 0 && g->su3_deviation < kSu3Tol) {
+    if (g->prec_mask & DD_PREC_F32) {
+      if (want == 8) {
+        s = compress_links(g, DD_PREC_F32, 8);
+        if (s == DD_ERR_UNSUPPORTED) s = compress_links(g, DD_PREC_F32, 12);
+      } else {
+        s = compress_links(g, DD_PREC_F32, 12);
+      }
+    }
+    if (s == DD_OK && (g->prec_mask & DD_PREC_F16)) s = compress_links(g, DD_PREC_F16, 12);
   }
   if (s == DD_OK && cudaDeviceSynchronize() != cudaSuccess) s = cuda_fail(cudaGetLastError(), "link conversion");
   return s;
@@ -268,7 +313,25 @@ int dd_gauge_stored_rows(const dd_gauge* g, int prec) {
   if (!g) return fail(DD_ERR_ARG, "null gauge");
   if (prec != DD_PREC_F64 && prec != DD_PREC_F32 && prec != DD_PREC_F16) return fail(DD_ERR_ARG, "bad precision");
   if (!(g->prec_mask & (unsigned)prec)) return fail(DD_ERR_UNSUPPORTED, "precision not created in the gauge handle");
-  return prec == DD_PREC_F32 && g->recon32 ? 2 : 3;
+  return (prec == DD_PREC_F32 && g->recon32 == 12) || (prec == DD_PREC_F16 && g->recon16) ? 2 : 3;
+}
+
+int dd_gauge_link_reals(const dd_gauge* g, int prec) {
+  if (!g) return fail(DD_ERR_ARG, "null gauge");
+  if (prec != DD_PREC_F64 && prec != DD_PREC_F32 && prec != DD_PREC_F16) return fail(DD_ERR_ARG, "bad precision");
+  if (!(g->prec_mask & (unsigned)prec)) return fail(DD_ERR_UNSUPPORTED, "precision not created in the gauge handle");
+  if (prec == DD_PREC_F32 && g->recon32) return g->recon32;
+  return prec == DD_PREC_F16 && g->recon16 ? 12 : 18;
+}
+
+int dd_gauge_compress_links(dd_gauge* g, int prec, int reals) {
+  if (!g) return fail(DD_ERR_ARG, "null gauge");
+  if (prec != DD_PREC_F32 && prec != DD_PREC_F16) return fail(DD_ERR_ARG, "precision must be F32 or F16");
+  if (reals != 18 && reals != 12 && reals != 8) return fail(DD_ERR_ARG, "reals per link must be 18, 12 or 8");
+  if (cudaDeviceSynchronize() != cudaSuccess) return cuda_fail(cudaGetLastError(), "before link compression");
+  int s = compress_links(g, prec, reals);
+  if (cudaDeviceSynchronize() != cudaSuccess && s == DD_OK) s = cuda_fail(cudaGetLastError(), "link compression");
+  return s;
 }
 
 int dd_gauge_destroy(dd_gauge* g) {

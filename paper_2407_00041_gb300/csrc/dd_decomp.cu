@@ -138,12 +138,22 @@ int rank_setup(dd_decomp* D, dd_decomp::Rank& r, cudaStream_t st) {
       DD_TRY(dom_copy<uint4>(m, p, G->U(pi, p), reinterpret_cast<char*>(r.gauge.links[pi].ptr) + (size_t)p * ng * Vh * 16,
                              ng, 1, 1, st));
   }
-  if (G->recon32 && G->links32r.ptr) {
-    DD_TRY(r.gauge.links32r.alloc((size_t)2 * 12 * Vh * 16));
+  // the two-row copies (domains read three rows when the parent holds the
+  // eight-real FP32 form)
+  if (G->recon32 == 12 && G->links32r.ptr) {
+    const int ng = G->recon_groups();
+    DD_TRY(r.gauge.links32r.alloc((size_t)2 * ng * Vh * 16));
     for (int p = 0; p < 2; ++p)
-      DD_TRY(dom_copy<uint4>(m, p, G->U2(p), reinterpret_cast<char*>(r.gauge.links32r.ptr) + (size_t)p * 12 * Vh * 16,
-                             12, 1, 1, st));
-    r.gauge.recon32 = 1;
+      DD_TRY(dom_copy<uint4>(m, p, G->U2(p), reinterpret_cast<char*>(r.gauge.links32r.ptr) + (size_t)p * ng * Vh * 16,
+                             ng, 1, 1, st));
+    r.gauge.recon32 = G->recon32;
+  }
+  if (G->recon16 && G->links16r.ptr) {
+    DD_TRY(r.gauge.links16r.alloc((size_t)2 * 6 * Vh * 16));
+    for (int p = 0; p < 2; ++p)
+      DD_TRY(dom_copy<uint4>(m, p, G->U2h(p), reinterpret_cast<char*>(r.gauge.links16r.ptr) + (size_t)p * 6 * Vh * 16,
+                             6, 1, 1, st));
+    r.gauge.recon16 = G->recon16;
   }
   r.clov.gauge = &r.gauge;
   r.clov.lat = &r.lat;
@@ -239,10 +249,10 @@ DomHopArgs rank_args(dd_decomp* D, dd_decomp::Rank& r, int prec, int nrhs) {
     a.U[p] = r.gauge.U(pi, p);
     a.M[p] = r.clov.M(pi, p);
   }
-  a.recon = prec == P32 && nrhs == 1 && r.gauge.recon32;
+  a.recon = prec == P32 && nrhs == 1 ? r.gauge.recon32 : prec == P16 && nrhs == 1 && r.gauge.recon16 ? 12 : 0;
   if (a.recon) {
-    a.U[0] = r.gauge.U2(0);
-    a.U[1] = r.gauge.U2(1);
+    a.U[0] = prec == P32 ? r.gauge.U2(0) : r.gauge.U2h(0);
+    a.U[1] = prec == P32 ? r.gauge.U2(1) : r.gauge.U2h(1);
   }
   a.rhs_block = 1;
   for (int mu = 0; mu < 4; ++mu) {

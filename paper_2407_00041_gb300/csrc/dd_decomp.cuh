@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(128) k_face_pack(const DomHopArgs A) {
     } else {
       hop_project_h<MU, TB>(psi, h0, h1);
       __half2 u[9];
-      load_link_h(a.U[p], s, a.g.Vh, MU, u);
+      load_link_h(a.U[p], s, a.g.Vh, MU, u, a.recon ? 12 : 0);
       hop_mul_h<true>(u, h0, h1, f0, f1);
       face_store<float>(A.f.chi_send[MU], nf, t, f0, f1, scale, true);
     }
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(128) k_face_pack(const DomHopArgs A) {
   } else {
     hop_project<MU, TB, R>(psi, h0, h1);
     cx<R> u[9], g0[3], g1[3];
-    load_link<PG, R>(a.U[p], s, a.g.Vh, MU, u, a.recon);
+    load_link<PG, R>(a.U[p], s, a.g.Vh, MU, u, (PG != P64 && a.recon) ? 12 : 0);
     hop_mul<true, R>(u, h0, h1, g0, g1);
     face_store<R>(A.f.chi_send[MU], nf, t, g0, g1, (float)scale, PIN == P16);
   }
@@ -213,10 +213,10 @@ __global__ void __launch_bounds__(128, (HopMinBlocks<PG, PIN>::value)) k_hop_dd(
           x0[c] = __floats2half2_rn(h0[c].re, h0[c].im);                                                 \
           x1[c] = __floats2half2_rn(h1[c].re, h1[c].im);                                                 \
         }                                                                                                \
-        load_link_h(a.U[p], s, Vh, MU, uh);                                                              \
+        load_link_h(a.U[p], s, Vh, MU, uh, a.recon ? 12 : 0);                                           \
         hop_mul_h<false>(uh, x0, x1, g0, g1);                                                            \
       } else {                                                                                           \
-        load_link<PG, R>(a.U[p], s, Vh, MU, u, a.recon);                                                 \
+        load_link<PG, R>(a.U[p], s, Vh, MU, u, (PG != P64 && a.recon) ? 12 : 0);                                        \
         hop_mul<false, R>(u, h0, h1, g0, g1);                                                            \
       }                                                                                                  \
       hop_reconstruct<MU, TF, R>(acc, g0, g1, sg);                                                       \
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(128, (HopMinBlocks<PG, PIN>::value)) k_hop_dd(
       const int nl = nb_fwd(a.g, sc, MU);                                                                \
       R sg = (MU == 0 && sc.c[0] == a.g.n[0] - 1) ? (R)a.g.t_bc : (R)1;                                  \
       hop_from<PG, PIN, MU, TF, false, R>(acc, a.in[q], a.gstride, (int64_t)(nl >> 1) * a.nrhs + r, a.U[p], s, \
-                                          Vh, sg, a.recon);                                              \
+                                          Vh, sg, (PG != P64 && a.recon) ? 12 : 0);                                     \
     }                                                                                                    \
     if (BOUNDARY && A.d.xch[MU] && sc.c[MU] == 0) {                                                      \
       const int64_t nf = A.d.nface[MU] * a.nrhs;                                                         \
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(128, (HopMinBlocks<PG, PIN>::value)) k_hop_dd(
       const int nl = nb_bwd(a.g, sc, MU);                                                                \
       R sg = (MU == 0 && sc.c[0] == 0) ? (R)a.g.t_bc : (R)1;                                             \
       hop_from<PG, PIN, MU, TB, true, R>(acc, a.in[q], a.gstride, (int64_t)(nl >> 1) * a.nrhs + r, a.U[q],    \
-                                         nl >> 1, Vh, sg, a.recon);                                      \
+                                         nl >> 1, Vh, sg, (PG != P64 && a.recon) ? 12 : 0);                             \
     }                                                                                                    \
   }
   DD_DHOP(0)

@@ -20,6 +20,7 @@
 #include <cstdlib>
 
 #include "dd_blas.h"
+#include "dd_link8.cuh"
 #include "dd_ops.h"
 
 namespace dd {
@@ -137,13 +138,26 @@ __device__ __forceinline__ void hop_regs(cx<R> acc[12], const cx<R> psi[12], con
 // one element per group, FP32 two, FP16 four.  Direction mu uses elements
 // 9 mu .. 9 mu + 8, i.e. 9, 5 or 3 group loads; a group shared by two
 // directions is read twice (the second time from cache).
-// FP32 with `recon`: the copy keeps rows 0 and 1 only ([12 groups][Vh],
+// FP32 with `recon` = 12: the copy keeps rows 0 and 1 only ([12 groups][Vh],
 // direction mu in groups 3 mu .. 3 mu + 2) and row 2 of the SU(3) matrix is
 // rebuilt as the complex conjugate of the cross product of rows 0 and 1.
+// FP32 with `recon` = 8: eight reals per link ([8 groups][Vh], direction mu
+// in groups 2 mu, 2 mu + 1), rebuilt by link8_decode.  FP16 with `recon`
+// (12): rows 0 and 1 ([6 groups][Vh], elements 6 mu .. 6 mu + 5 four per
+// group), row 2 rebuilt in R from the widened rows.
 template <int PG, typename R>
 __device__ __forceinline__ void load_link(const void* Ubase, int64_t s, int64_t Vh, int mu, cx<R> u[9],
-                                          bool recon = false) {
+                                          int recon = 0) {
   if constexpr (PG == P32) {
+    if (recon == 8) {
+      const float4* p = reinterpret_cast<const float4*>(Ubase) + s;
+      const float4 w0 = __ldg(p + (int64_t)(2 * mu) * Vh), w1 = __ldg(p + (int64_t)(2 * mu + 1) * Vh);
+      float2 f[9];
+      link8_decode(w0, w1, f);
+#pragma unroll
+      for (int e = 0; e < 9; ++e) u[e] = mk<R>(f[e].x, f[e].y);
+      return;
+    }
     if (recon) {
       const float4* p = reinterpret_cast<const float4*>(Ubase) + s;
 #pragma unroll
@@ -181,6 +195,30 @@ __device__ __forceinline__ void load_link(const void* Ubase, int64_t s, int64_t 
     }
   } else {
     const uint4* p = reinterpret_cast<const uint4*>(Ubase) + s;
+    if (recon) {  // FP16 rows 0 and 1 ([6 groups][Vh], elements 6 mu .. 6 mu + 5)
+      const int g0 = (6 * mu) >> 2, off = (6 * mu) & 3;
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const uint4 v = __ldg(p + (int64_t)(g0 + k) * Vh);
+        unsigned int w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int e = 4 * k + q - off;
+          if (e >= 0 && e < 6) {
+            const float2 f = __half22float2(*reinterpret_cast<__half2*>(&w[q]));
+            u[e] = mk<R>(f.x, f.y);
+          }
+        }
+      }
+      auto cross = [](cx<R> a, cx<R> b, cx<R> c, cx<R> d) {  // conj(a b - c d)
+        const cx<R> t = cfma(neg(c), d, cmul(a, b));
+        return mk(t.re, -t.im);
+      };
+      u[6] = cross(u[1], u[5], u[2], u[4]);
+      u[7] = cross(u[2], u[3], u[0], u[5]);
+      u[8] = cross(u[0], u[4], u[1], u[3]);
+      return;
+    }
     const int g0 = (9 * mu) >> 2, off = (9 * mu) & 3;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -201,7 +239,7 @@ __device__ __forceinline__ void load_link(const void* Ubase, int64_t s, int64_t 
 // The same with the link read from its native layout.
 template <int PG, int MU, int T, bool ADJ, typename R>
 __device__ __forceinline__ void hop(cx<R> acc[12], const cx<R> psi[12], const void* Ubase, int64_t s, int64_t Vh,
-                                    R sign, bool recon) {
+                                    R sign, int recon) {
   cx<R> u[9];
   load_link<PG, R>(Ubase, s, Vh, MU, u, recon);
   hop_regs<MU, T, ADJ, R>(acc, psi, u, sign);
@@ -283,9 +321,46 @@ __device__ __forceinline__ void hop_mul_h(const __half2 u[9], const __half2 h0[3
   }
 }
 
-// The nine FP16 elements of link mu of site s, as stored (four per 16-byte group)
-__device__ __forceinline__ void load_link_h(const void* Ubase, int64_t s, int64_t Vh, int mu, __half2 u[9]) {
+// The nine FP16 elements of link mu of site s, as stored (four per 16-byte
+// group).  With `recon` (12) the copy holds rows 0 and 1 ([6 groups][Vh]);
+// row 2 = conj(row 0 x row 1) is formed with mixed FMAs (exact products of
+// the stored FP16 values, FP32 sums) and rounded once to FP16.
+__device__ __forceinline__ void load_link_h(const void* Ubase, int64_t s, int64_t Vh, int mu, __half2 u[9],
+                                            int recon = 0) {
   const uint4* p = reinterpret_cast<const uint4*>(Ubase) + s;
+  if (recon) {
+    const int g0 = (6 * mu) >> 2, off = (6 * mu) & 3;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const uint4 v = __ldg(p + (int64_t)(g0 + k) * Vh);
+      const unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int e = 4 * k + q - off;
+        if (e >= 0 && e < 6) u[e] = *reinterpret_cast<const __half2*>(&w[q]);
+      }
+    }
+    // conj(a b - c d): re = ar br - ai bi - cr dr + ci di, im = -(ar bi + ai br - cr di - ci dr)
+    auto cross = [](__half2 a, __half2 b, __half2 c, __half2 d) {
+      const __half2 nc = __hneg2(c);
+      const __half ar = __low2half(a), ai = __high2half(a), br = __low2half(b), bi = __high2half(b);
+      const __half ci = __high2half(c), ncr = __low2half(nc), nci = __high2half(nc);
+      const __half dr = __low2half(d), di = __high2half(d);
+      float re = mfma_h(ar, br, 0.f);
+      re = mfma_h(__hneg(ai), bi, re);
+      re = mfma_h(ncr, dr, re);
+      re = mfma_h(ci, di, re);
+      float im = mfma_h(ar, bi, 0.f);
+      im = mfma_h(ai, br, im);
+      im = mfma_h(ncr, di, im);
+      im = mfma_h(nci, dr, im);
+      return __floats2half2_rn(re, -im);
+    };
+    u[6] = cross(u[1], u[5], u[2], u[4]);
+    u[7] = cross(u[2], u[3], u[0], u[5]);
+    u[8] = cross(u[0], u[4], u[1], u[3]);
+    return;
+  }
   const int g0 = (9 * mu) >> 2, off = (9 * mu) & 3;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
@@ -316,9 +391,9 @@ __device__ __forceinline__ float load_spinor_h(const HalfField& f, int64_t gstri
 // acc += sign (I + T gamma_mu) (x) W psi for FP16 psi and links
 template <int MU, int T, bool ADJ>
 __device__ __forceinline__ void hop_h(cx<float> acc[12], const __half2 psi[12], const void* Ubase, int64_t s,
-                                      int64_t Vh, float sign) {
+                                      int64_t Vh, float sign, int recon = 0) {
   __half2 u[9], h0[3], h1[3];
-  load_link_h(Ubase, s, Vh, MU, u);
+  load_link_h(Ubase, s, Vh, MU, u, recon);
   hop_project_h<MU, T>(psi, h0, h1);
   cx<float> g0[3], g1[3];
   hop_mul_h<ADJ>(u, h0, h1, g0, g1);
@@ -331,11 +406,11 @@ __device__ __forceinline__ void hop_h(cx<float> acc[12], const __half2 psi[12], 
 // folded in here).
 template <int PG, int PIN, int MU, int T, bool ADJ, typename R>
 __device__ __forceinline__ void hop_from(cx<R> acc[12], const HalfField& f, int64_t gstride, int64_t i,
-                                         const void* Ubase, int64_t s, int64_t Vh, R sg, bool recon) {
+                                         const void* Ubase, int64_t s, int64_t Vh, R sg, int recon) {
   if constexpr (PG == P16 && PIN == P16) {
     __half2 psi[12];
     sg *= load_spinor_h(f, gstride, i, psi);
-    hop_h<MU, T, ADJ>(acc, psi, Ubase, s, Vh, sg);
+    hop_h<MU, T, ADJ>(acc, psi, Ubase, s, Vh, sg, recon);
   } else {
     cx<R> psi[12];
     sg *= load_spinor_unscaled<PIN, R>(f, gstride, i, psi);
@@ -531,7 +606,11 @@ __device__ __forceinline__ float hop_epilogue(const HopArgs& a, int p, int s, in
 // The work of one thread: output slot `tid` in [0, npar * Vh * nrhs).  With
 // NORM it returns |out|^2 of the stored FP32 result (summed in FP32 over the
 // 12 components), else 0.
-template <int PG, int PIN, int POUT, bool DAG, int EPI, bool NORM = false>
+// LF: the form of the links the launch reads: 0 three rows, 12 rows 0 and 1
+// (FP16), 8 eight reals (FP32), fixed at compile time; -1 (FP32) three or
+// two rows by a.recon at run time (ptxas allocates this variant of the FP32
+// stencil without the spills of the compile-time two-row one).
+template <int PG, int PIN, int POUT, bool DAG, int EPI, bool NORM = false, int LF = 0>
 __device__ __forceinline__ float hop_thread(const HopArgs& a, int64_t tid) {
   using R = typename Store<PG>::real;
   using E = typename Store<PG>::elem;
@@ -557,6 +636,7 @@ __device__ __forceinline__ float hop_thread(const HopArgs& a, int64_t tid) {
   // forward hop: (I - gamma) for D, (I + gamma) for D^H; backward the opposite
   constexpr int TF = DAG ? +1 : -1;
   constexpr int TB = -TF;
+  const int rc = LF >= 0 ? LF : (a.recon ? 12 : 0);
 
   cx<R> acc[12];
 #pragma unroll
@@ -567,11 +647,11 @@ __device__ __forceinline__ float hop_thread(const HopArgs& a, int64_t tid) {
     int nl = nb_fwd(a.g, sc, MU);                                                                      \
     R sg = (MU == 0 && sc.c[0] == a.g.n[0] - 1) ? (R)a.g.t_bc : (R)1;                                  \
     hop_from<PG, PIN, MU, TF, false, R>(acc, a.in[q], a.gstride, (int64_t)(nl >> 1) * a.nrhs + r, a.U[p], s, \
-                                        Vh, sg, a.recon);                                              \
+                                        Vh, sg, rc);                                                   \
     nl = nb_bwd(a.g, sc, MU);                                                                          \
     sg = (MU == 0 && sc.c[0] == 0) ? (R)a.g.t_bc : (R)1;                                               \
     hop_from<PG, PIN, MU, TB, true, R>(acc, a.in[q], a.gstride, (int64_t)(nl >> 1) * a.nrhs + r, a.U[q],    \
-                                       nl >> 1, Vh, sg, a.recon);                                      \
+                                       nl >> 1, Vh, sg, rc);                                           \
   }
   DD_HOP_DIR(0)
   DD_HOP_DIR(1)
@@ -694,22 +774,22 @@ struct HopMinBlocks {
   static constexpr int value = PG == P64 ? 1 : (PG == P16 && PIN == P16) ? 7 : 5;
 };
 
-template <int PG, int PIN, int POUT, bool DAG, int EPI>
+template <int PG, int PIN, int POUT, bool DAG, int EPI, int LF = 0>
 __global__ void __launch_bounds__(128, (HopMinBlocks<PG, PIN>::value)) k_hop(const HopArgs a) {
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= launch_sites(a.g, a.npar) * a.nrhs) return;
-  hop_thread<PG, PIN, POUT, DAG, EPI>(a, tid);
+  hop_thread<PG, PIN, POUT, DAG, EPI, false, LF>(a, tid);
 }
 
 // EPI_D stencil of one right-hand side that also reduces |out|^2 over the
 // block: FP32 warp shuffles (32 sites, as the dot kernel sums short runs in
 // FP32), then the four warps' sums in FP64 in order, one partial per block
 // (partials[blockIdx.x].x); threads past the end contribute zero.
-template <int PG, int PIN, int POUT, bool DAG>
+template <int PG, int PIN, int POUT, bool DAG, int LF = 0>
 __global__ void __launch_bounds__(128, (HopMinBlocks<PG, PIN>::value)) k_hop_norm(const HopArgs a, double2* partials) {
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   float v = 0.f;
-  if (tid < launch_sites(a.g, a.npar)) v = hop_thread<PG, PIN, POUT, DAG, EPI_D, true>(a, tid);
+  if (tid < launch_sites(a.g, a.npar)) v = hop_thread<PG, PIN, POUT, DAG, EPI_D, true, LF>(a, tid);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
   __shared__ float sw[4];
@@ -752,6 +832,37 @@ namespace dd {
 // 5 RHS 0.57 vs 0.64 ms, 17 RHS 1.68 vs 1.73 ms).
 inline bool rb_worth(int nrhs) { return nrhs >= 2 && (nrhs % 2 == 0 || nrhs >= 5); }
 
+// One thread per (site, RHS) with the epilogue `epi`.
+template <int PG, int PIN, int POUT, int LF>
+cudaError_t launch_hop_single(const HopArgs& a, bool dagger, int epi, unsigned blocks, int threads, cudaStream_t st) {
+  switch (epi * 2 + (dagger ? 1 : 0)) {
+    case EPI_D * 2:
+      k_hop<PG, PIN, POUT, false, EPI_D, LF><<<blocks, threads, 0, st>>>(a);
+      break;
+    case EPI_D * 2 + 1:
+      k_hop<PG, PIN, POUT, true, EPI_D, LF><<<blocks, threads, 0, st>>>(a);
+      break;
+    case EPI_AINV * 2:
+      k_hop<PG, PIN, POUT, false, EPI_AINV, LF><<<blocks, threads, 0, st>>>(a);
+      break;
+    case EPI_AINV * 2 + 1:
+      k_hop<PG, PIN, POUT, true, EPI_AINV, LF><<<blocks, threads, 0, st>>>(a);
+      break;
+    case EPI_RESID * 2:
+      k_hop<PG, PIN, POUT, false, EPI_RESID, LF><<<blocks, threads, 0, st>>>(a);
+      break;
+    case EPI_ADD * 2:
+      k_hop<PG, PIN, POUT, false, EPI_ADD, LF><<<blocks, threads, 0, st>>>(a);
+      break;
+    case EPI_AINV_ADD * 2:
+      k_hop<PG, PIN, POUT, false, EPI_AINV_ADD, LF><<<blocks, threads, 0, st>>>(a);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 // Host launchers; the instantiation units explicitly instantiate one
 // precision triple each, other units only see the declarations in dd_ops.h.
 template <int PG, int PIN, int POUT>
@@ -792,32 +903,13 @@ cudaError_t launch_hop(const HopArgs& args, bool dagger, int epi, cudaStream_t s
     }
     return cudaGetLastError();
   }
-  switch (epi * 2 + (dagger ? 1 : 0)) {
-    case EPI_D * 2:
-      k_hop<PG, PIN, POUT, false, EPI_D><<<blocks, threads, 0, st>>>(a);
-      break;
-    case EPI_D * 2 + 1:
-      k_hop<PG, PIN, POUT, true, EPI_D><<<blocks, threads, 0, st>>>(a);
-      break;
-    case EPI_AINV * 2:
-      k_hop<PG, PIN, POUT, false, EPI_AINV><<<blocks, threads, 0, st>>>(a);
-      break;
-    case EPI_AINV * 2 + 1:
-      k_hop<PG, PIN, POUT, true, EPI_AINV><<<blocks, threads, 0, st>>>(a);
-      break;
-    case EPI_RESID * 2:
-      k_hop<PG, PIN, POUT, false, EPI_RESID><<<blocks, threads, 0, st>>>(a);
-      break;
-    case EPI_ADD * 2:
-      k_hop<PG, PIN, POUT, false, EPI_ADD><<<blocks, threads, 0, st>>>(a);
-      break;
-    case EPI_AINV_ADD * 2:
-      k_hop<PG, PIN, POUT, false, EPI_AINV_ADD><<<blocks, threads, 0, st>>>(a);
-      break;
-    default:
-      return cudaErrorInvalidValue;
+  if constexpr (PG == P32) {
+    if (a.recon == 8) return launch_hop_single<PG, PIN, POUT, 8>(a, dagger, epi, blocks, threads, st);
+    return launch_hop_single<PG, PIN, POUT, -1>(a, dagger, epi, blocks, threads, st);
+  } else {
+    if (PG == P16 && a.recon) return launch_hop_single<PG, PIN, POUT, PG == P16 ? 12 : 0>(a, dagger, epi, blocks, threads, st);
+    return launch_hop_single<PG, PIN, POUT, 0>(a, dagger, epi, blocks, threads, st);
   }
-  return cudaGetLastError();
 }
 
 // One right-hand side, EPI_D, out written in FP32: the stencil plus
@@ -836,10 +928,31 @@ cudaError_t launch_hop_norm(const HopArgs& args, bool dagger, double2* partials,
   const int threads = 128;
   const int64_t blocks = hop_norm_blocks(n);
   if (blocks > INT32_MAX || blocks + blas_reduce_scratch((int)blocks, 1) > npartials) return cudaErrorInvalidValue;
-  if (dagger)
-    k_hop_norm<PG, PIN, POUT, true><<<(unsigned)blocks, threads, 0, st>>>(a, partials);
-  else
-    k_hop_norm<PG, PIN, POUT, false><<<(unsigned)blocks, threads, 0, st>>>(a, partials);
+  const unsigned nb = (unsigned)blocks;
+  if constexpr (PG == P32) {
+    if (a.recon == 8) {
+      if (dagger)
+        k_hop_norm<PG, PIN, POUT, true, 8><<<nb, threads, 0, st>>>(a, partials);
+      else
+        k_hop_norm<PG, PIN, POUT, false, 8><<<nb, threads, 0, st>>>(a, partials);
+    } else if (dagger) {
+      k_hop_norm<PG, PIN, POUT, true, -1><<<nb, threads, 0, st>>>(a, partials);
+    } else {
+      k_hop_norm<PG, PIN, POUT, false, -1><<<nb, threads, 0, st>>>(a, partials);
+    }
+  } else {
+    constexpr int LF = PG == P16 ? 12 : 0;
+    if (PG == P16 && a.recon) {
+      if (dagger)
+        k_hop_norm<PG, PIN, POUT, true, LF><<<nb, threads, 0, st>>>(a, partials);
+      else
+        k_hop_norm<PG, PIN, POUT, false, LF><<<nb, threads, 0, st>>>(a, partials);
+    } else if (dagger) {
+      k_hop_norm<PG, PIN, POUT, true><<<nb, threads, 0, st>>>(a, partials);
+    } else {
+      k_hop_norm<PG, PIN, POUT, false><<<nb, threads, 0, st>>>(a, partials);
+    }
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return blas_reduce_partials(partials, (int)blocks, 1, norm_out, 0, st, partials + blocks) == 0 ? cudaSuccess

@@ -73,14 +73,21 @@ struct dd_gauge {
   // native links per precision (index 0: F64, 1: F32, 2: F16):
   // [parity][mu][9][Vh] complex elements, in 16-byte groups for F32 / F16
   dd::DevBuf links[3];
-  // when every link is SU(3): a second FP32 copy with rows 0 and 1 only
-  // ([parity][12 float4 groups][Vh]; the kernels rebuild row 2), used by
-  // single-RHS launches
+  // when every link is SU(3): a second, compressed FP32 copy used by
+  // single-RHS launches, either rows 0 and 1 only (recon32 = 12,
+  // [parity][12 float4 groups][Vh]; the kernels rebuild row 2) or eight reals
+  // per link (recon32 = 8, [parity][8 float4 groups][Vh], dd_link8.cuh)
   dd::DevBuf links32r;
   int recon32 = 0;
+  int recon_groups() const { return recon32 == 8 ? 8 : 12; }  // float4 groups per site
+  // the same for FP16: rows 0 and 1 only (recon16 = 12, [parity][6 uint4
+  // groups][Vh], element 6 mu + e of a site in group (6 mu + e) / 4)
+  dd::DevBuf links16r;
+  int recon16 = 0;
   double su3_deviation = 0.0;  // max over links of |U U^H - 1| and |det U - 1|
   const void* U(int pi, int parity) const;
-  const void* U2(int parity) const;  // the two-row FP32 copy
+  const void* U2(int parity) const;   // the compressed FP32 copy
+  const void* U2h(int parity) const;  // the two-row FP16 copy
 };
 
 struct dd_clover {
@@ -159,6 +166,9 @@ int links_generate(const dd_lattice* lat, uint64_t seed, double eps, dd_gauge* g
 int links_su3_deviation(const dd_gauge* g, double* dev, cudaStream_t st);
 // build the two-row FP32 copy: [parity][12 groups][Vh] float4
 int links_to_recon32(dd_gauge* g, cudaStream_t st);
+// eight-real FP32 copy; *dev = max |rebuilt - FP64 link| over all elements
+int links_to_recon8(dd_gauge* g, double* dev, cudaStream_t st);
+int links_to_recon16(dd_gauge* g, cudaStream_t st);
 int links_to_canonical(const dd_gauge* g, double* U_canon_dev, cudaStream_t st);
 int clover_build(dd_clover* op, cudaStream_t st);  // FP64 blocks, A_ee^{-1}, demoted copies
 int clover_to_dense(const dd_clover* op, double* A_dev /*[V][144] complex*/, cudaStream_t st);

@@ -187,12 +187,12 @@ HopArgs base_args(const dd_clover* op, int pg, int nrhs) {
   a.beta = -0.5;
   a.rhs_block = 1;
   a.paired = 0;
-  // single right-hand side: the two-row FP32 links (fewer bytes; the
+  // single right-hand side: the compressed FP32 links (fewer bytes; the
   // RHS-blocked kernels of several RHS are faster with three rows)
-  a.recon = pg == P32 && nrhs == 1 && op->gauge->recon32;
+  a.recon = pg == P32 && nrhs == 1 ? op->gauge->recon32 : pg == P16 && nrhs == 1 && op->gauge->recon16 ? 12 : 0;
   if (a.recon) {
-    a.U[0] = op->gauge->U2(0);
-    a.U[1] = op->gauge->U2(1);
+    a.U[0] = pg == P32 ? op->gauge->U2(0) : op->gauge->U2h(0);
+    a.U[1] = pg == P32 ? op->gauge->U2(1) : op->gauge->U2h(1);
   }
   return a;
 }
@@ -414,7 +414,12 @@ const void* dd_gauge::U(int pi, int parity) const {
 
 const void* dd_gauge::U2(int parity) const {
   if (!links32r.ptr) return nullptr;
-  return reinterpret_cast<const char*>(links32r.ptr) + (size_t)parity * 24 * lat->Vh * sizeof(float2);
+  return reinterpret_cast<const char*>(links32r.ptr) + (size_t)parity * recon_groups() * lat->Vh * sizeof(float4);
+}
+
+const void* dd_gauge::U2h(int parity) const {
+  if (!links16r.ptr) return nullptr;
+  return reinterpret_cast<const char*>(links16r.ptr) + (size_t)parity * 6 * lat->Vh * sizeof(uint4);
 }
 
 const void* dd_clover::M(int pi, int parity) const {

@@ -32,7 +32,7 @@ struct HopArgs {
   double beta;
   int rhs_block;  // batched launch: right-hand sides per thread (1 or 2)
   FastDiv fblk;   // division of the thread index by the RHS slots per site (set by the launcher)
-  int recon;      // FP32 links stored as rows 0 and 1 (the third row is rebuilt)
+  int recon;      // FP32 link form: 0 three rows, 12 rows 0 and 1 (row 2 rebuilt), 8 eight reals (dd_link8.cuh)
   int paired;     // fields in the paired-RHS layout (dd_pair.cuh; nrhs even, FP32 / FP16)
 };
 

@@ -3,8 +3,9 @@
 // conversion.
 #include <cstring>
 
-#include "dd_pair.cuh"
 #include "dd_internal.h"
+#include "dd_link8.cuh"
+#include "dd_pair.cuh"
 
 namespace dd {
 
@@ -225,6 +226,67 @@ __global__ void k_links_recon32(int64_t nlinks, const double2* __restrict__ U64,
     const int64_t E = 6 * mu + e;
     U32[p * 24 * Vh + ((E >> 1) * Vh + s) * 2 + (E & 1)] = make_float2((float)v.x, (float)v.y);
   }
+}
+
+// FP16 copy with rows 0 and 1: element E = 6 mu + e (e < 6) of a site in
+// slot E % 4 of uint4 group E / 4, [parity][6 groups][Vh], rounded as the
+// three-row FP16 links
+__global__ void k_links_recon16(int64_t nlinks, const double2* __restrict__ U64, int64_t Vh, __half2* U16) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nlinks) return;
+  const int64_t s = t % Vh, pm = t / Vh;
+  const int64_t p = pm / 4, mu = pm % 4;
+  const double2* b = U64 + pm * 9 * Vh + s;
+  for (int e = 0; e < 6; ++e) {
+    const double2 v = b[e * Vh];
+    const int64_t E = 6 * mu + e;
+    U16[p * 24 * Vh + ((E >> 2) * Vh + s) * 4 + (E & 3)] = __floats2half2_rn((float)v.x, (float)v.y);
+  }
+}
+
+// Eight-real FP32 copy: link (parity p, mu) of site s in float4 groups
+// 2 mu, 2 mu + 1 of [p][8 groups][Vh] (dd_link8.cuh)
+__global__ void k_links_recon8(int64_t nlinks, const double2* __restrict__ U64, int64_t Vh, float4* U8) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nlinks) return;
+  const int64_t s = t % Vh, pm = t / Vh;
+  const int64_t p = pm / 4, mu = pm % 4;
+  const double2* b = U64 + pm * 9 * Vh + s;
+  double2 u[9];
+  for (int e = 0; e < 9; ++e) u[e] = b[e * Vh];
+  float4 w0, w1;
+  link8_encode(u, w0, w1);
+  U8[(p * 8 + 2 * mu) * Vh + s] = w0;
+  U8[(p * 8 + 2 * mu + 1) * Vh + s] = w1;
+}
+
+// max |decoded - U| over the elements of every link (the decoder of the
+// stencil), reduced like k_su3_deviation
+__global__ void k_links_recon8_error(int64_t nlinks, const double2* __restrict__ U64, const float4* __restrict__ U8,
+                                     int64_t Vh, unsigned* out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float dev = 0.f;
+  if (t < nlinks) {
+    const int64_t s = t % Vh, pm = t / Vh;
+    const int64_t p = pm / 4, mu = pm % 4;
+    float2 u[9];
+    link8_decode(U8[(p * 8 + 2 * mu) * Vh + s], U8[(p * 8 + 2 * mu + 1) * Vh + s], u);
+    const double2* b = U64 + pm * 9 * Vh + s;
+    double m = 0.0;
+    for (int e = 0; e < 9; ++e) {
+      const double2 v = b[e * Vh];
+      m = fmax(m, fmax(fabs((double)u[e].x - v.x), fabs((double)u[e].y - v.y)));
+    }
+    dev = isfinite(m) ? (float)fmin(m, 1e30) : 1e30f;
+  }
+  __shared__ float red[256];
+  red[threadIdx.x] = dev;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicMax(out, __float_as_uint(red[0]));
 }
 
 __global__ void k_links_to_canonical(LexGeom g, const double2* __restrict__ U64, double2* Uc) {
@@ -693,7 +755,39 @@ int links_to_recon32(dd_gauge* g, cudaStream_t st) {
   k_links_recon32<<<nblk(n, 128), 128, 0, st>>>(n, reinterpret_cast<const double2*>(g->links[0].ptr), g->lat->Vh,
                                                reinterpret_cast<float2*>(g->links32r.ptr));
   DD_CUDA(cudaGetLastError());
-  g->recon32 = 1;
+  g->recon32 = 12;
+  return DD_OK;
+}
+
+int links_to_recon16(dd_gauge* g, cudaStream_t st) {
+  const int64_t n = g->lat->V * 4;
+  DD_TRY(g->links16r.alloc((size_t)g->lat->V * 6 * sizeof(uint4)));
+  k_links_recon16<<<nblk(n, 128), 128, 0, st>>>(n, reinterpret_cast<const double2*>(g->links[0].ptr), g->lat->Vh,
+                                               reinterpret_cast<__half2*>(g->links16r.ptr));
+  DD_CUDA(cudaGetLastError());
+  g->recon16 = 12;
+  return DD_OK;
+}
+
+int links_to_recon8(dd_gauge* g, double* dev, cudaStream_t st) {
+  const int64_t n = g->lat->V * 4;
+  DD_TRY(g->links32r.alloc((size_t)g->lat->V * 8 * sizeof(float4)));
+  g->recon32 = 8;
+  const double2* U64 = reinterpret_cast<const double2*>(g->links[0].ptr);
+  float4* U8 = reinterpret_cast<float4*>(g->links32r.ptr);
+  k_links_recon8<<<nblk(n, 128), 128, 0, st>>>(n, U64, g->lat->Vh, U8);
+  DD_CUDA(cudaGetLastError());
+  DevBuf out;
+  DD_TRY(out.alloc(sizeof(unsigned)));
+  DD_CUDA(cudaMemsetAsync(out.ptr, 0, sizeof(unsigned), st));
+  k_links_recon8_error<<<nblk(n, 256), 256, 0, st>>>(n, U64, U8, g->lat->Vh, reinterpret_cast<unsigned*>(out.ptr));
+  DD_CUDA(cudaGetLastError());
+  unsigned bits = 0;
+  DD_CUDA(cudaMemcpyAsync(&bits, out.ptr, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  DD_CUDA(cudaStreamSynchronize(st));
+  float f;
+  memcpy(&f, &bits, sizeof(f));
+  *dev = f;
   return DD_OK;
 }
 

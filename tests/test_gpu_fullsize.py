@@ -64,6 +64,10 @@ def test_48c96_all_precisions_sampled():
         out = _native_apply(op, prec, psi_dev, 1)
         _check_sites(U, dims, psi, out, sites, [0], TOL[prec])
         del out
+    g.compress_links(8)  # the eight-real FP32 links rebuild within 1e-6 on all 42M links
+    assert g.link_reals(dd.DD_PREC_F32) == 8
+    out = _native_apply(op, dd.DD_PREC_F32, psi_dev, 1)
+    _check_sites(U, dims, psi, out, sites, [0], TOL[dd.DD_PREC_F32])
 
 
 def test_32c4_twelve_rhs_sampled():

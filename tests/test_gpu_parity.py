@@ -174,22 +174,113 @@ def test_host_layout_pipelined_equals_device(dims, prec):
         assert np.array_equal(host, dev)
 
 
-def test_two_row_fp32_links_and_non_su3_fallback():
-    """SU(3) links: single-RHS FP32 applies read a two-row copy and rebuild
-    the third row; links that are not SU(3) get no two-row copy.  Both match
-    the oracle, which uses the links as given."""
+def test_two_row_links_and_non_su3_fallback():
+    """SU(3) links: single-RHS FP32 and FP16 applies read two-row copies and
+    rebuild the third row; links that are not SU(3) get no two-row copy.  Both
+    match the oracle, which uses the links as given."""
     dims = (6, 4, 2, 8)
     U = synthetic.gauge(dims)
     _, lat, g, op = make(dims, U=U)
     assert dd.lib.dd_gauge_stored_rows(g.h, dd.DD_PREC_F32) == 2
+    assert dd.lib.dd_gauge_stored_rows(g.h, dd.DD_PREC_F16) == 2
     assert dd.lib.dd_gauge_stored_rows(g.h, dd.DD_PREC_F64) == 3
+    assert g.link_reals(dd.DD_PREC_F16) == 12
     # a non-unitary perturbation of every link
     W = U * (1.0 + 0.01 * synthetic.gaussian(U.size, seed=9).real.reshape(U.shape))
     _, lat2, g2, op2 = make(dims, U=W)
     assert dd.lib.dd_gauge_stored_rows(g2.h, dd.DD_PREC_F32) == 3
-    psi = synthetic.spinor(dims, nrhs=1)  # one RHS: the launches that read the two-row copy
+    assert dd.lib.dd_gauge_stored_rows(g2.h, dd.DD_PREC_F16) == 3
+    psi = synthetic.spinor(dims, nrhs=1)  # one RHS: the launches that read the two-row copies
     for links, o in ((U, op), (W, op2)):
         A = oracle.clover(links, dims, M0, CSW)
-        for which, ref_fn in ((dd.DD_OP_D, oracle.apply_D), (dd.DD_OP_DH, oracle.apply_DH)):
-            got = apply(o, which, dd.DD_PREC_F32, psi)
-            assert rel(got[0], ref_fn(links, A, psi[0].reshape(-1, 12), dims)) < TOL[dd.DD_PREC_F32]
+        for prec in (dd.DD_PREC_F32, dd.DD_PREC_F16):
+            for which, ref_fn in ((dd.DD_OP_D, oracle.apply_D), (dd.DD_OP_DH, oracle.apply_DH)):
+                got = apply(o, which, prec, psi)
+                assert rel(got[0], ref_fn(links, A, psi[0].reshape(-1, 12), dims)) < TOL[prec]
+
+
+def test_fp16_two_row_against_three_row():
+    """FP16 single-RHS D, D^H and Dhat from the two-row copy (row 2 from
+    exact products of the stored halves, rounded once) against the three-row
+    FP16 links of the same handle and the oracle; the rebuilt row differs from
+    the stored one by FP16 rounding only."""
+    dims = (4, 8, 8, 8)
+    U = synthetic.gauge(dims, eps=1.0)
+    _, lat, g, op = make(dims, U=U)
+    A = oracle.clover(U, dims, M0, CSW)
+    eo = oracle.EvenOdd(U, A, dims)
+    psi = synthetic.spinor(dims, nrhs=1)
+    v = psi[0].reshape(-1, 12)[eo.odd][None]
+    got = {}
+    for reals in (12, 18):
+        g.compress_links(reals, dd.DD_PREC_F16)
+        assert g.link_reals(dd.DD_PREC_F16) == reals
+        got[reals] = [apply(op, w, dd.DD_PREC_F16, psi) for w in (dd.DD_OP_D, dd.DD_OP_DH)] + \
+                     [apply(op, w, dd.DD_PREC_F16, v) for w in (dd.DD_OP_DHAT, dd.DD_OP_DHAT_H)]
+        refs = [oracle.apply_D(U, A, psi[0].reshape(-1, 12), dims), oracle.apply_DH(U, A, psi[0].reshape(-1, 12), dims),
+                eo.Dhat(v[0]), eo.DhatH(v[0])]
+        for a, b in zip(got[reals], refs):
+            assert rel(a[0], b) < TOL[dd.DD_PREC_F16]
+    for a, b in zip(got[12], got[18]):
+        assert rel(a, b) < 2e-3
+
+
+@pytest.mark.parametrize("eps", [0.3, 1.0, 3.0])
+def test_eight_real_fp32_links(eps):
+    """The eight-real FP32 copy (column shift, row swap and phases in two
+    float4 words per link): single-RHS D, D^H and Dhat match the oracle at the
+    FP32 tolerance for smooth and rough SU(3) fields (eps = 1 and 3 take all
+    three column shifts); switching back to 12 and 18 reals reproduces the
+    two-row and three-row results."""
+    dims = (6, 4, 2, 8)
+    U = synthetic.gauge(dims, eps=eps)
+    _, lat, g, op = make(dims, U=U)
+    assert g.link_reals(dd.DD_PREC_F32) == 12 and g.link_reals(dd.DD_PREC_F64) == 18
+    psi = synthetic.spinor(dims, nrhs=1)
+    A = oracle.clover(U, dims, M0, CSW)
+    ref12 = {w: apply(op, w, dd.DD_PREC_F32, psi) for w in (dd.DD_OP_D, dd.DD_OP_DH)}
+    g.compress_links(8)
+    assert g.link_reals(dd.DD_PREC_F32) == 8
+    assert dd.lib.dd_gauge_stored_rows(g.h, dd.DD_PREC_F32) == 3
+    for which, ref_fn in ((dd.DD_OP_D, oracle.apply_D), (dd.DD_OP_DH, oracle.apply_DH)):
+        got = apply(op, which, dd.DD_PREC_F32, psi)
+        assert rel(got[0], ref_fn(U, A, psi[0].reshape(-1, 12), dims)) < TOL[dd.DD_PREC_F32]
+        assert rel(got, ref12[which]) < 1e-6
+    eo = oracle.EvenOdd(U, A, dims)
+    v = psi[0].reshape(-1, 12)[eo.odd][None]
+    for which, ref_fn in ((dd.DD_OP_DHAT, eo.Dhat), (dd.DD_OP_DHAT_H, eo.DhatH)):
+        got = apply(op, which, dd.DD_PREC_F32, v)
+        assert rel(got[0], ref_fn(v[0])) < TOL[dd.DD_PREC_F32]
+    g.compress_links(12)
+    assert g.link_reals(dd.DD_PREC_F32) == 12
+    assert np.array_equal(apply(op, dd.DD_OP_D, dd.DD_PREC_F32, psi), ref12[dd.DD_OP_D])
+    g.compress_links(18)
+    assert g.link_reals(dd.DD_PREC_F32) == 18
+    got = apply(op, dd.DD_OP_D, dd.DD_PREC_F32, psi)
+    assert rel(got[0], oracle.apply_D(U, A, psi[0].reshape(-1, 12), dims)) < TOL[dd.DD_PREC_F32]
+
+
+def test_eight_real_needs_su3_links_and_valid_forms():
+    dims = (4, 4, 2, 4)
+    U = synthetic.gauge(dims)
+    W = U * (1.0 + 0.01 * synthetic.gaussian(U.size, seed=9).real.reshape(U.shape))
+    _, lat, g, op = make(dims, U=W)
+    assert g.link_reals(dd.DD_PREC_F32) == 18
+    for reals in (8, 12):
+        with pytest.raises(dd.DDError) as e:
+            g.compress_links(reals)
+        assert e.value.status == dd.DD_ERR_UNSUPPORTED
+        assert g.link_reals(dd.DD_PREC_F32) == 18
+    _, lat2, g2, op2 = make(dims, U=U)
+    for reals, prec in ((0, dd.DD_PREC_F32), (9, dd.DD_PREC_F32), (16, dd.DD_PREC_F16), (12, dd.DD_PREC_F64)):
+        with pytest.raises(dd.DDError) as e:
+            g2.compress_links(reals, prec)
+        assert e.value.status == dd.DD_ERR_ARG
+    with pytest.raises(dd.DDError) as e:
+        g2.compress_links(8, dd.DD_PREC_F16)
+    assert e.value.status == dd.DD_ERR_UNSUPPORTED
+    assert g2.link_reals(dd.DD_PREC_F32) == 12 and g2.link_reals(dd.DD_PREC_F16) == 12
+    g64 = dd.Gauge(lat2, U, precisions=dd.DD_PREC_F64)
+    with pytest.raises(dd.DDError) as e:
+        g64.compress_links(8)
+    assert e.value.status == dd.DD_ERR_UNSUPPORTED
