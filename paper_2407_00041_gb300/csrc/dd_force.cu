@@ -74,6 +74,23 @@ __device__ __forceinline__ M3<R> load_link(const FGeom& g, const double2* U64, c
   return r;
 }
 
+// The same from the FP32 native copy: element E = 9 mu + e of a site in
+// slot E & 1 of float4 group E / 2, [parity][18 groups][Vh]
+template <typename R>
+__device__ __forceinline__ M3<R> load_link(const FGeom& g, const float2* U32, const int c[4], int mu) {
+  const int lex = ((c[0] * g.n[1] + c[1]) * g.n[2] + c[2]) * g.n[3] + c[3];
+  const int p = (c[0] + c[1] + c[2] + c[3]) & 1;
+  const float2* b = U32 + (int64_t)p * 36 * g.Vh + 2 * (int64_t)(lex >> 1);
+  M3<R> r;
+#pragma unroll
+  for (int e = 0; e < 9; ++e) {
+    const int E = 9 * mu + e;
+    const float2 v = b[(int64_t)(E >> 1) * 2 * g.Vh + (E & 1)];
+    r.m[e] = mk<R>((R)v.x, (R)v.y);
+  }
+  return r;
+}
+
 template <typename R>
 __device__ __forceinline__ M3<R> mmul(const M3<R>& a, const M3<R>& b) {
   M3<R> r;
@@ -125,6 +142,25 @@ __device__ __forceinline__ void load_canon(const double2* f, int64_t site, cx<R>
     v[c] = mk<R>((R)d.x, (R)d.y);
   }
 }
+// canonical FP32 copy ([nrhs][V][12] float2, 16-byte loads)
+template <typename R>
+__device__ __forceinline__ void load_canon(const float2* f, int64_t site, cx<R> v[12]) {
+  const float4* q = reinterpret_cast<const float4*>(f + site * 12);
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    const float4 d = q[c];
+    v[2 * c] = mk<R>((R)d.x, (R)d.y);
+    v[2 * c + 1] = mk<R>((R)d.z, (R)d.w);
+  }
+}
+
+// canonical FP64 spinors -> FP32 (the input of the FP32 force kernels)
+__global__ void k_canon_to_f32(int64_t n, const double2* __restrict__ in, float2* out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const double2 v = in[t];
+  out[t] = make_float2((float)v.x, (float)v.y);
+}
 
 // G storage: FP64 as 9 double2 per link; the FP32 path accumulates in 20
 // floats per link (18 used) and converts at the end.
@@ -142,9 +178,8 @@ __device__ __forceinline__ void store_link_g(float* G, int64_t t, const cx<float
 }
 
 // One thread per link (x, mu): hopping contribution, written (not added).
-template <typename R, typename GT>
-__global__ void k_force_hop(FGeom g, const double2* __restrict__ phi, const double2* __restrict__ psi, int nrhs,
-                            GT* G) {
+template <typename R, typename GT, typename ST>
+__global__ void k_force_hop(FGeom g, const ST* __restrict__ phi, const ST* __restrict__ psi, int nrhs, GT* G) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= g.V * 4) return;
   const int x = (int)(t >> 2), mu = (int)(t & 3);
@@ -162,8 +197,8 @@ __global__ void k_force_hop(FGeom g, const double2* __restrict__ phi, const doub
 #pragma unroll
   for (int e = 0; e < 9; ++e) acc[e] = zero<R>();
   for (int r = 0; r < nrhs; ++r) {
-    const double2* ph = phi + (int64_t)r * g.V * 12;
-    const double2* ps = psi + (int64_t)r * g.V * 12;
+    const ST* ph = phi + (int64_t)r * g.V * 12;
+    const ST* ps = psi + (int64_t)r * g.V * 12;
     cx<R> v[12], hA[2][3], hB[2][3];
     // h-(phi(x)) (x) conj(h-(psi(y)))
     load_canon<R>(ph, x, v);
@@ -260,24 +295,29 @@ __device__ __forceinline__ void atomic_add_m3(float* G, const M3<float>& m, bool
 // spinors (summed over right-hand sides), then for each of the four leaves
 // of Q_munu(x) (Eq. 1.12) the derivatives R_k of its four factors, handed to
 // emit(site coordinates, direction, R_k, add R_k^H instead).
-template <typename R, typename Emit>
-__device__ __forceinline__ void clover_plane_leaves(const FGeom& g, const double2* __restrict__ U64,
-                                                    const double2* __restrict__ phi, const double2* __restrict__ psi,
-                                                    int nrhs, double csw, const int c[4], int mu, int nu, Emit emit) {
+template <typename R, int mu, int nu, typename UT, typename ST, typename Emit>
+__device__ __forceinline__ void clover_plane_leaves(const FGeom& g, const UT* __restrict__ U,
+                                                    const ST* __restrict__ phi, const ST* __restrict__ psi,
+                                                    int nrhs, double csw, const int c[4], Emit emit) {
   const int x = ((c[0] * g.n[1] + c[1]) * g.n[2] + c[2]) * g.n[3] + c[3];
   cx<R> ph[12], ps[12];
   // T[b][a] = -(c_sw/32) sum_{s,s'} gg[s][s'] psi[s'][b] conj(phi[s][a]), summed over RHS
   M3<R> T;
+#pragma unroll
   for (int e = 0; e < 9; ++e) T.m[e] = zero<R>();
   for (int r = 0; r < nrhs; ++r) {
     load_canon<R>(phi + (int64_t)r * g.V * 12, x, ph);
     load_canon<R>(psi + (int64_t)r * g.V * 12, x, ps);
+#pragma unroll
     for (int s = 0; s < 4; ++s)
+#pragma unroll
       for (int sp = 0; sp < 4; ++sp) {
         const cx<double> w = gg(mu, nu, s, sp);
         if (w.re == 0.0 && w.im == 0.0) continue;
         const cx<R> wr = mk<R>((R)w.re, (R)w.im);
+#pragma unroll
         for (int b = 0; b < 3; ++b)
+#pragma unroll
           for (int a = 0; a < 3; ++a)
             T.m[3 * b + a] = cfmac(ph[3 * s + a], cmul(wr, ps[3 * sp + b]), T.m[3 * b + a]);
       }
@@ -285,62 +325,73 @@ __device__ __forceinline__ void clover_plane_leaves(const FGeom& g, const double
   // T' = 2 (T - T^H) scaled by -(c_sw / 32)
   M3<R> Tp;
   const R f = (R)(-2.0 * csw / 32.0);
+#pragma unroll
   for (int i = 0; i < 3; ++i)
+#pragma unroll
     for (int j = 0; j < 3; ++j)
       Tp.m[3 * i + j] = f * mk(T.m[3 * i + j].re - T.m[3 * j + i].re, T.m[3 * i + j].im + T.m[3 * j + i].im);
-  // the four leaves of Q_munu(x), Eq. 1.12: factor sites, directions, daggers
-  int xpm[4], xpn[4], xmm[4], xmn[4], xmm_pn[4], xmm_mn[4], xmn_pm[4];
-  auto sh = [&](const int* a, int d, int st, int* o) {
-    for (int i = 0; i < 4; ++i) o[i] = a[i];
-    o[d] = (a[d] + st + g.n[d]) % g.n[d];
-  };
-  sh(c, mu, +1, xpm);
-  sh(c, nu, +1, xpn);
-  sh(c, mu, -1, xmm);
-  sh(c, nu, -1, xmn);
-  sh(xmm, nu, +1, xmm_pn);
-  sh(xmm, nu, -1, xmm_mn);
-  sh(xmn, mu, +1, xmn_pm);
-  const int* site[4][4] = {{c, xpm, xpn, c}, {c, xmm_pn, xmm, xmm}, {xmm, xmm_mn, xmm_mn, xmn}, {xmn, xmn, xmn_pm, c}};
-  const int dir[4][4] = {{mu, nu, mu, nu}, {nu, mu, nu, mu}, {mu, nu, mu, nu}, {nu, mu, nu, mu}};
-  const int dag[4][4] = {{0, 0, 1, 1}, {0, 1, 1, 0}, {1, 1, 0, 0}, {1, 0, 0, 1}};
+  // the four leaves of Q_munu(x), Eq. 1.12.  Factor k of leaf l sits at
+  // c + dm mu^ + dn nu^ (the offsets below), points along mu when l + k is
+  // even (else nu), and enters daggered when (l + k) mod 4 >= 2:
+  //   l = 0: U_mu(c) U_nu(c+mu) U_mu(c+nu)^H U_nu(c)^H
+  //   l = 1: U_nu(c) U_mu(c-mu+nu)^H U_nu(c-mu)^H U_mu(c-mu)
+  //   l = 2: U_mu(c-mu)^H U_nu(c-mu-nu)^H U_mu(c-mu-nu) U_nu(c-nu)
+  //   l = 3: U_nu(c-nu)^H U_mu(c-nu) U_nu(c-nu+mu) U_mu(c)^H
+  constexpr signed char kDm[4][4] = {{0, 1, 0, 0}, {0, -1, -1, -1}, {-1, -1, -1, 0}, {0, 0, 1, 0}};
+  constexpr signed char kDn[4][4] = {{0, 0, 1, 0}, {0, 1, 0, 0}, {0, -1, -1, -1}, {-1, -1, -1, 0}};
   for (int l = 0; l < 4; ++l) {
     M3<R> F[4];
+    int fs[4][4];  // factor sites (coordinates)
+#pragma unroll
     for (int k = 0; k < 4; ++k) {
-      M3<R> u = load_link<R>(g, U64, site[l][k], dir[l][k]);
-      F[k] = dag[l][k] ? mdag(u) : u;
+      const int dm = kDm[l][k], dn = kDn[l][k];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) fs[k][i] = c[i];
+      fs[k][mu] = (c[mu] + dm + g.n[mu]) % g.n[mu];
+      fs[k][nu] = (c[nu] + dn + g.n[nu]) % g.n[nu];
+      const M3<R> u = load_link<R>(g, U, fs[k], ((l + k) & 1) ? nu : mu);
+      F[k] = ((l + k) & 3) >= 2 ? mdag(u) : u;
     }
+    auto dirk = [&](int k) { return ((l + k) & 1) ? nu : mu; };
+    auto plain = [&](int k) { return ((l + k) & 3) < 2; };  // factor k is U (not U^H)
     // R_k = F_{k+1} .. F_3 T' F_0 .. F_{k-1} from the suffix products
     // S_k = F_{k+1} .. F_3 T' and the prefix products P_k = F_0 .. F_{k-1}:
     // eight 3x3 products per leaf instead of twelve
     const M3<R> S2 = mmul(F[3], Tp);
     const M3<R> S1 = mmul(F[2], S2);
-    emit(site[l][0], dir[l][0], mmul(F[1], S1), dag[l][0] == 0);
-    emit(site[l][1], dir[l][1], mmul(S1, F[0]), dag[l][1] == 0);
+    emit(fs[0], dirk(0), mmul(F[1], S1), plain(0));
+    emit(fs[1], dirk(1), mmul(S1, F[0]), plain(1));
     const M3<R> P2 = mmul(F[0], F[1]);
-    emit(site[l][2], dir[l][2], mmul(S2, P2), dag[l][2] == 0);
-    emit(site[l][3], dir[l][3], mmul(Tp, mmul(P2, F[2])), dag[l][3] == 0);
+    emit(fs[2], dirk(2), mmul(S2, P2), plain(2));
+    emit(fs[3], dirk(3), mmul(Tp, mmul(P2, F[2])), plain(3));
   }
 }
 
-// One thread per site: self-coupling contribution, accumulated atomically in
-// G (FP64 atomics) or in the padded FP32 workspace (16-byte vector
-// reductions).
-template <typename R, typename GT>
-__global__ void k_force_clover(FGeom g, const double2* __restrict__ U64, const double2* __restrict__ phi,
-                               const double2* __restrict__ psi, int nrhs, double csw, GT* G) {
+// One thread per site and plane (mu, nu) (grid row blockIdx.y): self-coupling
+// contribution, accumulated atomically in G (FP64 atomics) or in the padded
+// FP32 workspace (16-byte vector reductions).
+template <typename R, typename GT, typename UT, typename ST>
+__global__ void k_force_clover(FGeom g, const UT* __restrict__ U, const ST* __restrict__ phi,
+                               const ST* __restrict__ psi, int nrhs, double csw, GT* G) {
   constexpr int kStride = sizeof(GT) == sizeof(float) ? kGf : 9;  // elements of GT per link
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= g.V) return;
   int c[4];
   coords_of(g, x, c);
-  for (int mu = 0; mu < 4; ++mu)
-    for (int nu = mu + 1; nu < 4; ++nu)
-      clover_plane_leaves<R>(g, U64, phi, psi, nrhs, csw, c, mu, nu,
-                             [&](const int* sc, int d, const M3<R>& Rk, bool dagger) {
-                               const int lex = ((sc[0] * g.n[1] + sc[1]) * g.n[2] + sc[2]) * g.n[3] + sc[3];
-                               atomic_add_m3(G + ((int64_t)lex * 4 + d) * kStride, Rk, dagger);
-                             });
+  auto emit = [&](const int* sc, int d, const M3<R>& Rk, bool dagger) {
+    const int lex = ((sc[0] * g.n[1] + sc[1]) * g.n[2] + sc[2]) * g.n[3] + sc[3];
+    atomic_add_m3(G + ((int64_t)lex * 4 + d) * kStride, Rk, dagger);
+  };
+  // one plane (mu, nu) per grid row: every index into the coordinate arrays
+  // is a compile-time constant
+  switch (blockIdx.y) {
+    case 0: clover_plane_leaves<R, 0, 1>(g, U, phi, psi, nrhs, csw, c, emit); break;
+    case 1: clover_plane_leaves<R, 0, 2>(g, U, phi, psi, nrhs, csw, c, emit); break;
+    case 2: clover_plane_leaves<R, 0, 3>(g, U, phi, psi, nrhs, csw, c, emit); break;
+    case 3: clover_plane_leaves<R, 1, 2>(g, U, phi, psi, nrhs, csw, c, emit); break;
+    case 4: clover_plane_leaves<R, 1, 3>(g, U, phi, psi, nrhs, csw, c, emit); break;
+    default: clover_plane_leaves<R, 2, 3>(g, U, phi, psi, nrhs, csw, c, emit); break;
+  }
 }
 
 __device__ __forceinline__ cx<double> load_g(const double2* G, int64_t t, int e) {
@@ -357,24 +408,28 @@ __global__ void k_force_widen(int64_t nlinks, const float* __restrict__ Gf, doub
   for (int e = 0; e < 9; ++e) G[t * 9 + e] = make_double2((double)Gf[t * kGf + 2 * e], (double)Gf[t * kGf + 2 * e + 1]);
 }
 
-// F = P(G U^H)
-template <typename GT>
-__global__ void k_force_project(FGeom g, const double2* __restrict__ U64, const GT* __restrict__ G, double2* F) {
+// F = P(G U^H), in R (FP64, or FP32 for the FP32 accumulator and links)
+template <typename R, typename GT, typename UT>
+__global__ void k_force_project(FGeom g, const UT* __restrict__ U, const GT* __restrict__ G, double2* F) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= g.V * 4) return;
   const int x = (int)(t >> 2), mu = (int)(t & 3);
   int c[4];
   coords_of(g, x, c);
-  M3<double> u = load_link<double>(g, U64, c, mu), gm;
-  for (int e = 0; e < 9; ++e) gm.m[e] = load_g(G, t, e);
-  M3<double> M = mmul(gm, mdag(u));
-  cx<double> f[9];
+  M3<R> u = load_link<R>(g, U, c, mu), gm;
+  for (int e = 0; e < 9; ++e) {
+    const cx<double> v = load_g(G, t, e);
+    gm.m[e] = mk<R>((R)v.re, (R)v.im);
+  }
+  M3<R> M = mmul(gm, mdag(u));
+  cx<R> f[9];
+  const R half = (R)0.5, third = (R)(1.0 / 3.0);
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j)
-      f[3 * i + j] = mk(0.5 * (M.m[3 * i + j].re - M.m[3 * j + i].re), 0.5 * (M.m[3 * i + j].im + M.m[3 * j + i].im));
-  const cx<double> tr = mk((f[0].re + f[4].re + f[8].re) / 3.0, (f[0].im + f[4].im + f[8].im) / 3.0);
+      f[3 * i + j] = mk(half * (M.m[3 * i + j].re - M.m[3 * j + i].re), half * (M.m[3 * i + j].im + M.m[3 * j + i].im));
+  const cx<R> tr = mk((f[0].re + f[4].re + f[8].re) * third, (f[0].im + f[4].im + f[8].im) * third);
   for (int i = 0; i < 3; ++i) f[4 * i] = f[4 * i] - tr;
-  for (int e = 0; e < 9; ++e) F[t * 9 + e] = make_double2(f[e].re, f[e].im);
+  for (int e = 0; e < 9; ++e) F[t * 9 + e] = make_double2((double)f[e].re, (double)f[e].im);
 }
 
 }  // namespace
@@ -397,21 +452,35 @@ int force(dd_clover* op, int prec, const double* phi, const double* psi, int nrh
       DD_TRY(gtmp.alloc((size_t)nl * 9 * sizeof(double2)));
       Gd = reinterpret_cast<double2*>(gtmp.ptr);
     }
-    k_force_hop<double, double2><<<bl, 128, 0, st>>>(g, ph, ps, nrhs, Gd);
-    if (clover) k_force_clover<double, double2><<<bs, 64, 0, st>>>(g, U64, ph, ps, nrhs, op->csw, Gd);
-    if (F) k_force_project<double2><<<bl, 128, 0, st>>>(g, U64, Gd, reinterpret_cast<double2*>(F));
+    k_force_hop<double, double2, double2><<<bl, 128, 0, st>>>(g, ph, ps, nrhs, Gd);
+    if (clover) k_force_clover<double, double2, double2, double2><<<dim3(bs, 6), 64, 0, st>>>(g, U64, ph, ps, nrhs, op->csw, Gd);
+    if (F) k_force_project<double, double2, double2><<<bl, 128, 0, st>>>(g, U64, Gd, reinterpret_cast<double2*>(F));
     DD_CUDA(cudaGetLastError());
     if (!G) DD_CUDA(cudaStreamSynchronize(st));  // the temporary G is released on return
     return DD_OK;
   }
-  // FP32: accumulate in the operator's padded FP32 workspace (vector
-  // reductions), then widen into G and / or project into F
-  DD_TRY(op->ws_force.ensure((size_t)nl * kGf * sizeof(float)));
+  // FP32: the spinors converted once to FP32 (canonical), the links read from
+  // the FP32 native copy when the gauge handle has one; accumulate in the
+  // operator's padded FP32 workspace (vector reductions), then widen into G
+  // and / or project into F in FP32
+  const size_t nsp = (size_t)nrhs * lat->V * 12;
+  DD_TRY(op->ws_force.ensure((size_t)nl * kGf * sizeof(float) + 2 * nsp * sizeof(float2)));
   float* Gf = reinterpret_cast<float*>(op->ws_force.ptr);
-  k_force_hop<float, float><<<bl, 128, 0, st>>>(g, ph, ps, nrhs, Gf);
-  if (clover) k_force_clover<float, float><<<bs, 64, 0, st>>>(g, U64, ph, ps, nrhs, op->csw, Gf);
+  float2* ph32 = reinterpret_cast<float2*>(Gf + (size_t)nl * kGf);
+  float2* ps32 = ph32 + nsp;
+  const unsigned bc = (unsigned)((nsp + 255) / 256);
+  k_canon_to_f32<<<bc, 256, 0, st>>>((int64_t)nsp, ph, ph32);
+  k_canon_to_f32<<<bc, 256, 0, st>>>((int64_t)nsp, ps, ps32);
+  k_force_hop<float, float, float2><<<bl, 128, 0, st>>>(g, ph32, ps32, nrhs, Gf);
+  const float2* U32 = reinterpret_cast<const float2*>(op->gauge->links[1].ptr);
+  if (U32) {
+    if (clover) k_force_clover<float, float, float2, float2><<<dim3(bs, 6), 64, 0, st>>>(g, U32, ph32, ps32, nrhs, op->csw, Gf);
+    if (F) k_force_project<float, float, float2><<<bl, 128, 0, st>>>(g, U32, Gf, reinterpret_cast<double2*>(F));
+  } else {
+    if (clover) k_force_clover<float, float, double2, float2><<<dim3(bs, 6), 64, 0, st>>>(g, U64, ph32, ps32, nrhs, op->csw, Gf);
+    if (F) k_force_project<float, float, double2><<<bl, 128, 0, st>>>(g, U64, Gf, reinterpret_cast<double2*>(F));
+  }
   if (G) k_force_widen<<<bl, 128, 0, st>>>(nl, Gf, reinterpret_cast<double2*>(G));
-  if (F) k_force_project<float><<<bl, 128, 0, st>>>(g, U64, Gf, reinterpret_cast<double2*>(F));
   DD_CUDA(cudaGetLastError());
   return DD_OK;
 }
