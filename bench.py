@@ -53,8 +53,8 @@ DIMS = (96, 48, 48, 48)  # nT, nZ, nY, nX
 M0, CSW, EPS = -0.4, 1.0, 0.3
 WORKLOAD = "48^3x96 Wilson-clover D.psi, 1 RHS, eps=0.3 SU(3) links, m0=-0.4, c_sw=1.0, antiperiodic T"
 METRIC = "D.psi HBM GB/s (algorithmic) at 48^3x96; mixed vs FP64 FGMRES time-to-1e-10"
-BYTES = {"f64": (1152, 384), "f32": (576, 192), "f16": (288, 104)}
-PREC = {"f64": 1, "f32": 2, "f16": 4}
+BYTES = {"f64": (1152, 384), "f32": (576, 192), "f16": (288, 104), "df64": (1152, 384)}
+PREC = {"f64": 1, "f32": 2, "f16": 4, "df64": 8}  # df64: FP64-accurate FP32-pair arithmetic
 FLOPS_PER_SITE = 1848  # nominal: hopping 1320 + self coupling 504 + combine 24
 # link force with the clover term, one RHS, as the kernels compute it (an FMA
 # counts 2): hopping outer products 4 x 336, clover leaf derivatives 6 planes x
@@ -769,11 +769,12 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="f32", choices=["f64", "f32", "f16"], help="headline precision")
+    ap.add_argument("--prec", default="f32", choices=["f64", "f32", "f16", "df64"], help="headline precision")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the multi-RHS, batch, Dhat and adjoint lines")
     ap.add_argument("--no-link8", action="store_true", help="skip the eight-real FP32 link apply and solve")
+    ap.add_argument("--no-df64", action="store_true", help="skip the FP64-accurate FP32-pair apply")
     ap.add_argument("--solve-inner", default="f32", choices=["f32", "f16"])
     ap.add_argument("--dims", default="96x48x48x48", help="nT x nZ x nY x nX (a smaller lattice for profiling)")
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides of the timed D psi (profiling)")
@@ -828,8 +829,9 @@ def main():
     psi = synthetic.spinor(dims, nrhs=N)
     log("building gauge and operator handles")
     lat = dd.Lattice(dims, -1)
-    gauge = dd.Gauge(lat, U)
-    op = dd.Operator(gauge, M0, CSW)
+    precs = dd.DD_PREC_F64 | dd.DD_PREC_F32 | dd.DD_PREC_F16 | (0 if args.no_df64 else dd.DD_PREC_DF64)
+    gauge = dd.Gauge(lat, U, precisions=precs)
+    op = dd.Operator(gauge, M0, CSW, precisions=precs)
     # SU(3) links: the FP32 copy keeps two rows per link (192 instead of 288 B)
     rows32 = dd.lib.dd_gauge_stored_rows(gauge.h, dd.DD_PREC_F32)
     reals32 = gauge.link_reals(dd.DD_PREC_F32)
@@ -848,14 +850,15 @@ def main():
     dd.check(dd.lib.dd_probe_flops(dd.DD_PREC_F32, fl.ctypes.data, stream.cuda_stream), "probe")
     f32_peak = float(fl[0])
 
-    order = ["f64", "f32", "f16"]
+    order = ["f64", "f32", "f16"] + ([] if args.no_df64 else ["df64"])
+    out_f64 = None
     head = None
     for prec in order:
         p = PREC[prec]
         nbytes = op.field_bytes(p, 0, N)
         xin = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
         xout = torch.empty_like(xin)
-        paired = args.layout == "paired" and prec != "f64" and N % 2 == 0
+        paired = args.layout == "paired" and prec in ("f32", "f16") and N % 2 == 0
         if paired:
             op.pack_paired(p, 0, psi_dev, xin, N)
         else:
@@ -887,6 +890,16 @@ def main():
         variants[prec] = {"gbs": gbs, "ms_per_apply": ms, "hbm_frac": bytes_per_site(prec, N) * V / kern / 1e9 /
                           peaks["hbm_gbs"], "gflops_nominal": gflops, "bound": bound,
                           "roof_frac": frac, "bytes_per_site": bytes_per_site(prec, N)}
+        if prec in ("f64", "df64") and not paired:  # the FP32-pair result against the FP64 one
+            o = torch.empty_like(psi_dev)
+            op.unpack(p, 0, xout, o, N)
+            if prec == "f64":
+                out_f64 = o
+            elif out_f64 is not None:
+                variants[prec]["rel_diff_vs_f64"] = ((o - out_f64).norm() / out_f64.norm()).item()
+                variants[prec]["speedup_over_f64"] = variants["f64"]["ms_per_apply"] / ms
+                out_f64 = None
+            del o
         rooflines[prec] = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": frac,
                            "traffic": (profile_traffic(prec) if N == 1 and dims == DIMS and
                                        (prec != "f32" or LINK_REALS_F32[0] == 12) and
@@ -1079,7 +1092,8 @@ def main():
         "metric": METRIC,
         "value": head["value"], "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"f64": "f64", "f32": "f32", "f16": "f32 (fp16 storage)"}[args.prec], "data": "synthetic",
+        "dtype": {"f64": "f64", "f32": "f32", "f16": "f32 (fp16 storage)",
+                  "df64": "f64 (FP32-pair arithmetic)"}[args.prec], "data": "synthetic",
         "config": {"workload": (WORKLOAD if dims == DIMS else WORKLOAD.replace("48^3x96", args.dims)).replace(
                        "1 RHS", f"{N} RHS"),
                    "precision": args.prec, "nrhs": N, "sites": V, "f32_link_rows_single_rhs": rows32,

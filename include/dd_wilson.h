@@ -121,6 +121,18 @@ extern "C" {
 #define DD_PREC_F64 1  /* FP64 storage and arithmetic */
 #define DD_PREC_F32 2  /* FP32 storage and arithmetic */
 #define DD_PREC_F16 4  /* FP16 storage (spinors with a per-site FP32 scale), FP32 arithmetic */
+/* FP64-accurate arithmetic in pairs of FP32 numbers x = h + l, |l| <= ulp(h)/2
+ * (Dekker's double-word arithmetic: about 48 significant bits, from the FP32
+ * pipes), with links, blocks and native fields stored as such pairs: one
+ * complex = (re.h, re.l, im.h, im.l), 16 bytes, in the FP64 layouts (native
+ * fields of this precision have the FP64 byte count).  Accepted by
+ * dd_gauge_create / dd_gauge_generate / dd_clover_create (precision masks),
+ * dd_field_bytes, dd_pack, dd_unpack and dd_apply (all operators, native
+ * and canonical layouts except the paired one); not by the solver, SAP,
+ * AMG, the batch, the domain decomposition or dd_force (DD_ERR_ARG or
+ * DD_ERR_UNSUPPORTED).  Canonical inputs are split into pairs exactly to
+ * about 2^-48 relative; results are rounded to FP64 by h + l. */
+#define DD_PREC_DF64 8
 
 /* ---- operators ---- */
 #define DD_OP_D 0       /* D, Eq. 1.13 */

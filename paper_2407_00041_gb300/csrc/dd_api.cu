@@ -27,6 +27,8 @@ namespace {
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 bool valid_prec(int p) { return p == DD_PREC_F64 || p == DD_PREC_F32 || p == DD_PREC_F16; }
+// precisions of dd_apply, dd_pack, dd_unpack and dd_field_bytes
+bool valid_apply_prec(int p) { return valid_prec(p) || p == DD_PREC_DF64; }
 
 // Copy a canonical field into device memory when it lives on the host.
 int stage_in(DevBuf& buf, const void* src, size_t bytes, int layout, const double** dev, cudaStream_t st) {
@@ -261,6 +263,7 @@ int gauge_finish(dd_gauge* g) {
     }
     if (s == DD_OK && (g->prec_mask & DD_PREC_F16)) s = compress_links(g, DD_PREC_F16, 12);
   }
+  if (s == DD_OK && (g->prec_mask & DD_PREC_DF64)) s = links_to_pairs(g, 0);
   if (s == DD_OK && cudaDeviceSynchronize() != cudaSuccess) s = cuda_fail(cudaGetLastError(), "link conversion");
   return s;
 }
@@ -270,7 +273,7 @@ int gauge_finish(dd_gauge* g) {
 int dd_gauge_create(const dd_lattice* lat, const double* U, int location, unsigned prec_mask, dd_gauge** out) {
   if (!lat || !U || !out) return fail(DD_ERR_ARG, "null argument");
   if (location != 0 && location != 1) return fail(DD_ERR_ARG, "location must be 0 (host) or 1 (device)");
-  if (prec_mask & ~7u) return fail(DD_ERR_ARG, "bad precision mask");
+  if (prec_mask & ~15u) return fail(DD_ERR_ARG, "bad precision mask");
   dd_gauge* g = nullptr;
   DD_TRY(gauge_alloc(lat, prec_mask, &g));
   const size_t bytes = (size_t)lat->V * 4 * 9 * 16;
@@ -295,7 +298,7 @@ int dd_gauge_create(const dd_lattice* lat, const double* U, int location, unsign
 
 int dd_gauge_generate(const dd_lattice* lat, uint64_t seed, double eps, unsigned prec_mask, dd_gauge** out) {
   if (!lat || !out) return fail(DD_ERR_ARG, "null argument");
-  if (prec_mask & ~7u) return fail(DD_ERR_ARG, "bad precision mask");
+  if (prec_mask & ~15u) return fail(DD_ERR_ARG, "bad precision mask");
   if (!(eps >= 0.0 && eps <= 1e6)) return fail(DD_ERR_ARG, "eps must be finite and >= 0");
   dd_gauge* g = nullptr;
   DD_TRY(gauge_alloc(lat, prec_mask, &g));
@@ -311,14 +314,14 @@ int dd_gauge_generate(const dd_lattice* lat, uint64_t seed, double eps, unsigned
 
 int dd_gauge_stored_rows(const dd_gauge* g, int prec) {
   if (!g) return fail(DD_ERR_ARG, "null gauge");
-  if (prec != DD_PREC_F64 && prec != DD_PREC_F32 && prec != DD_PREC_F16) return fail(DD_ERR_ARG, "bad precision");
+  if (!valid_apply_prec(prec)) return fail(DD_ERR_ARG, "bad precision");
   if (!(g->prec_mask & (unsigned)prec)) return fail(DD_ERR_UNSUPPORTED, "precision not created in the gauge handle");
   return (prec == DD_PREC_F32 && g->recon32 == 12) || (prec == DD_PREC_F16 && g->recon16) ? 2 : 3;
 }
 
 int dd_gauge_link_reals(const dd_gauge* g, int prec) {
   if (!g) return fail(DD_ERR_ARG, "null gauge");
-  if (prec != DD_PREC_F64 && prec != DD_PREC_F32 && prec != DD_PREC_F16) return fail(DD_ERR_ARG, "bad precision");
+  if (!valid_apply_prec(prec)) return fail(DD_ERR_ARG, "bad precision");
   if (!(g->prec_mask & (unsigned)prec)) return fail(DD_ERR_UNSUPPORTED, "precision not created in the gauge handle");
   if (prec == DD_PREC_F32 && g->recon32) return g->recon32;
   return prec == DD_PREC_F16 && g->recon16 ? 12 : 18;
@@ -356,7 +359,7 @@ int dd_gauge_download(const dd_gauge* g, double* U, int location) {
 
 int dd_clover_create(const dd_gauge* g, double m0, double csw, unsigned prec_mask, dd_clover** out) {
   if (!g || !out) return fail(DD_ERR_ARG, "null argument");
-  if (prec_mask & ~7u) return fail(DD_ERR_ARG, "bad precision mask");
+  if (prec_mask & ~15u) return fail(DD_ERR_ARG, "bad precision mask");
   dd_clover* op = new (std::nothrow) dd_clover;
   if (!op) return fail(DD_ERR_OOM, "host allocation failed");
   op->gauge = g;
@@ -390,20 +393,20 @@ int dd_clover_download(const dd_clover* op, double* A_host) {
 }
 
 size_t dd_field_bytes(const dd_clover* op, int prec, int subset, int nrhs) {
-  if (!op || !valid_prec(prec) || nrhs < 1 || (subset != 0 && subset != 1)) return 0;
+  if (!op || !valid_apply_prec(prec) || nrhs < 1 || (subset != 0 && subset != 1)) return 0;
   return field_bytes(op->lat, prec, subset, nrhs);
 }
 
 int dd_pack(const dd_clover* op, int prec, int subset, const double* canon, void* native, int nrhs, void* stream) {
   if (!op || !canon || !native || nrhs < 1) return fail(DD_ERR_ARG, "null argument or nrhs < 1");
-  if (!valid_prec(prec) || subset < 0 || subset > 2) return fail(DD_ERR_ARG, "bad precision or subset");
+  if (!valid_apply_prec(prec) || subset < 0 || subset > 2) return fail(DD_ERR_ARG, "bad precision or subset");
   Field f = field_view(op->lat, prec, subset, native, nrhs);
   return pack(op->lat, prec, subset, canon, f, as_stream(stream));
 }
 
 int dd_unpack(const dd_clover* op, int prec, int subset, const void* native, double* canon, int nrhs, void* stream) {
   if (!op || !canon || !native || nrhs < 1) return fail(DD_ERR_ARG, "null argument or nrhs < 1");
-  if (!valid_prec(prec) || subset < 0 || subset > 2) return fail(DD_ERR_ARG, "bad precision or subset");
+  if (!valid_apply_prec(prec) || subset < 0 || subset > 2) return fail(DD_ERR_ARG, "bad precision or subset");
   Field f = field_view(op->lat, prec, subset, const_cast<void*>(native), nrhs);
   return unpack(op->lat, prec, subset, f, canon, as_stream(stream));
 }
@@ -430,7 +433,7 @@ int dd_unpack_paired(const dd_clover* op, int prec, int subset, const void* pair
 
 int dd_apply(dd_clover* op, int which, int prec, const void* in, void* out, int nrhs, int layout, void* stream) {
   if (!op || !in || !out || nrhs < 1) return fail(DD_ERR_ARG, "null argument or nrhs < 1");
-  if (!valid_prec(prec)) return fail(DD_ERR_ARG, "bad precision");
+  if (!valid_apply_prec(prec)) return fail(DD_ERR_ARG, "bad precision");
   if (which < DD_OP_D || which > DD_OP_SC) return fail(DD_ERR_ARG, "bad operator");
   if (layout < DD_LAYOUT_CANONICAL || layout > DD_LAYOUT_NATIVE_PAIRED) return fail(DD_ERR_ARG, "bad layout");
   if (layout == DD_LAYOUT_NATIVE_PAIRED) {

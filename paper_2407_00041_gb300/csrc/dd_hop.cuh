@@ -27,6 +27,7 @@ namespace dd {
 
 __device__ __forceinline__ float ffma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double ffma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ df ffma(df a, df b, df c) { return df_fma(a, b, c); }
 
 // (B_mu l) for spin component 0 / 1 of the lower pair
 template <int MU, typename R>
@@ -106,6 +107,8 @@ __device__ __forceinline__ void hop_mul(const cx<R> u[9], const cx<R> h0[3], con
         g1[a] = cfma(u[3 * a + b], h1[b], g1[a]);
       }
     }
+    renorm(g0[a]);
+    renorm(g1[a]);
   }
 }
 
@@ -176,7 +179,11 @@ __device__ __forceinline__ void load_link(const void* Ubase, int64_t s, int64_t 
       return;
     }
   }
-  if constexpr (PG == P64) {
+  if constexpr (PG == PDF) {
+    const float4* p = reinterpret_cast<const float4*>(Ubase) + (int64_t)(9 * mu) * Vh + s;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) u[e] = df_cx(__ldg(p + e * Vh));
+  } else if constexpr (PG == P64) {
     const double2* p = reinterpret_cast<const double2*>(Ubase) + (int64_t)(9 * mu) * Vh + s;
 #pragma unroll
     for (int e = 0; e < 9; ++e) {
@@ -426,7 +433,7 @@ __device__ __forceinline__ void hop_from(cx<R> acc[12], const HalfField& f, int6
 // (8 halves), so a site's blocks take 36, 18 or 9 loads.
 template <int PG>
 struct BlockGroups {
-  static constexpr int PER = PG == P64 ? 1 : PG == P32 ? 2 : 4;  // elements per group
+  static constexpr int PER = (PG == P64 || PG == PDF) ? 1 : PG == P32 ? 2 : 4;  // elements per group
 };
 
 // (i, j) of the strict upper-triangle element o = 0..14 of a 6x6 block
@@ -440,7 +447,10 @@ __device__ __forceinline__ void tri_ij(int o, int& i, int& j) {
 template <int PG, typename R>
 __device__ __forceinline__ void load_block_group(const void* M, int64_t s, int64_t Vh, int g, cx<R> e[4],
                                                  bool streaming) {
-  if constexpr (PG == P64) {
+  if constexpr (PG == PDF) {
+    const float4* p = reinterpret_cast<const float4*>(M) + (int64_t)g * Vh + s;
+    e[0] = df_cx(streaming ? __ldcs(p) : __ldg(p));
+  } else if constexpr (PG == P64) {
     const double2* p = reinterpret_cast<const double2*>(M) + (int64_t)g * Vh + s;
     const double2 v = streaming ? __ldcs(p) : __ldg(p);
     e[0] = mk<R>(v.x, v.y);
@@ -487,6 +497,8 @@ __device__ __forceinline__ void block_apply_g(const void* M, int64_t s, int64_t 
       out[6 * b + j] = cfmac(m, x[6 * b + i], out[6 * b + j]);
     }
   }
+#pragma unroll
+  for (int c = 0; c < 12; ++c) renorm(out[c]);
 }
 
 // out = M x with M the parity base pointer of the block array and s the site
@@ -536,6 +548,8 @@ __device__ __forceinline__ void block_apply_h(const void* M, int64_t s, int64_t 
 // FP32 result (summed in FP32 over the 12 components), else 0.
 template <int PG, int PIN, int POUT, int EPI, bool NORM, typename R>
 __device__ __forceinline__ float hop_epilogue(const HopArgs& a, int p, int s, int r, cx<R> acc[12]) {
+#pragma unroll
+  for (int c = 0; c < 12; ++c) renorm(acc[c]);  // FP32 pairs: the hops accumulate lazily
   const int64_t Vh = a.g.Vh;
   const R beta = (R)a.beta;
   const int64_t i = (int64_t)s * a.nrhs + r;
@@ -603,6 +617,92 @@ __device__ __forceinline__ float hop_epilogue(const HopArgs& a, int p, int s, in
   return n2;
 }
 
+// FP32-pair arithmetic: the eight hops of a site in one rolled loop.  Each
+// pair operation takes 7-15 FP32 instructions, and the unrolled eight hops
+// (4 directions x 2, each with its own projection and colour product code)
+// did not fit the instruction cache (ncu at 48 x 24^3: warps stalled on
+// instruction fetch 7.7 times per issue, issue active 27%); here one copy of
+// the colour product serves all hops: the backward hops take U^H by
+// conjugating and transposing the nine elements in registers, and the
+// projection B_mu l and reconstruction B_mu^H g select their components and
+// factors (1, i, -1, -i) from small tables.
+// f z for f = i^k, k = 0..3
+template <typename R>
+__device__ __forceinline__ cx<R> mul_ipow(cx<R> z, int k) {
+  const bool sw = k & 1;
+  const R re = sw ? z.im : z.re, im = sw ? z.re : z.im;
+  return mk((k == 1 || k == 2) ? -re : re, (k >= 2) ? -im : im);
+}
+
+template <int PG, int PIN, bool DAG, typename R>
+__device__ __forceinline__ void hops_rolled(const HopArgs& a, const SiteCoord& sc, int p, int s, int r,
+                                            cx<R> acc[12]) {
+  const int q = p ^ 1;
+  const int64_t Vh = a.g.Vh;
+  constexpr int TF = DAG ? +1 : -1;
+  int nidx[8];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    nidx[2 * m] = nb_fwd(a.g, sc, m);
+    nidx[2 * m + 1] = nb_bwd(a.g, sc, m);
+  }
+  const R sf0 = sc.c[0] == a.g.n[0] - 1 ? (R)a.g.t_bc : (R)1;
+  const R sb0 = sc.c[0] == 0 ? (R)a.g.t_bc : (R)1;
+#pragma unroll 1
+  for (int k = 0; k < 8; ++k) {
+    const int mu = k >> 1;
+    const bool bwd = k & 1;
+    int nl = nidx[0];
+#pragma unroll
+    for (int j = 1; j < 8; ++j)
+      if (k == j) nl = nidx[j];
+    const int T = bwd ? -TF : TF;
+    const R sign = mu == 0 ? (bwd ? sb0 : sf0) : (R)1;
+    cx<R> psi[12], u[9];
+    load_spinor<PIN, R>(a.in[q], a.gstride, (int64_t)(nl >> 1) * a.nrhs + r, psi);
+    if (bwd)
+      load_link<PG, R>(a.U[q], nl >> 1, Vh, mu, u);
+    else
+      load_link<PG, R>(a.U[p], s, Vh, mu, u);
+    if (bwd) {  // U^H
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        u[4 * i] = mk(u[4 * i].re, -u[4 * i].im);
+#pragma unroll
+        for (int j = i + 1; j < 3; ++j) {
+          const cx<R> t = u[3 * i + j];
+          u[3 * i + j] = mk(u[3 * j + i].re, -u[3 * j + i].im);
+          u[3 * j + i] = mk(t.re, -t.im);
+        }
+      }
+    }
+    // B_mu l: b0 = i^k0 l_j0, b1 = i^k1 l_j1; B_mu^H g: b0 = i^m0 g_i0, b1 = i^m1 g_i1
+    const int j0 = mu >= 2, j1 = mu < 2;
+    const int k0 = mu == 0 ? 0 : mu == 1 ? 3 : mu == 2 ? 2 : 3;
+    const int k1 = mu == 0 ? 0 : mu == 1 ? 1 : mu == 2 ? 0 : 3;
+    const int i0 = mu == 2 || mu == 3, i1 = mu < 2;
+    const int m0 = mu == 0 ? 0 : mu == 1 ? 1 : mu == 2 ? 0 : 1;
+    const int m1 = mu == 0 ? 0 : mu == 1 ? 3 : mu == 2 ? 2 : 1;
+    cx<R> h0[3], h1[3], g0[3], g1[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const cx<R> b0 = mul_ipow(j0 ? psi[9 + c] : psi[6 + c], k0);
+      const cx<R> b1 = mul_ipow(j1 ? psi[9 + c] : psi[6 + c], k1);
+      h0[c] = T > 0 ? psi[c] + b0 : psi[c] - b0;
+      h1[c] = T > 0 ? psi[3 + c] + b1 : psi[3 + c] - b1;
+    }
+    hop_mul<false, R>(u, h0, h1, g0, g1);
+    const R sb = T > 0 ? sign : -sign;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      acc[c] = caxpy(sign, g0[c], acc[c]);
+      acc[3 + c] = caxpy(sign, g1[c], acc[3 + c]);
+      acc[6 + c] = caxpy(sb, mul_ipow(i0 ? g1[c] : g0[c], m0), acc[6 + c]);
+      acc[9 + c] = caxpy(sb, mul_ipow(i1 ? g1[c] : g0[c], m1), acc[9 + c]);
+    }
+  }
+}
+
 // The work of one thread: output slot `tid` in [0, npar * Vh * nrhs).  With
 // NORM it returns |out|^2 of the stored FP32 result (summed in FP32 over the
 // 12 components), else 0.
@@ -653,10 +753,14 @@ __device__ __forceinline__ float hop_thread(const HopArgs& a, int64_t tid) {
     hop_from<PG, PIN, MU, TB, true, R>(acc, a.in[q], a.gstride, (int64_t)(nl >> 1) * a.nrhs + r, a.U[q],    \
                                        nl >> 1, Vh, sg, rc);                                           \
   }
-  DD_HOP_DIR(0)
-  DD_HOP_DIR(1)
-  DD_HOP_DIR(2)
-  DD_HOP_DIR(3)
+  if constexpr (PG == PDF) {
+    hops_rolled<PG, PIN, DAG, R>(a, sc, p, s, r, acc);
+  } else {
+    DD_HOP_DIR(0)
+    DD_HOP_DIR(1)
+    DD_HOP_DIR(2)
+    DD_HOP_DIR(3)
+  }
 #undef DD_HOP_DIR
 
   return hop_epilogue<PG, PIN, POUT, EPI, NORM, R>(a, p, s, r, acc);
@@ -771,7 +875,7 @@ __global__ void __launch_bounds__(128, NB >= 4 ? 2 : 3) k_hop_rb(const HopArgs a
 // bound by the FP64 pipe and keeps the unconstrained allocation.
 template <int PG, int PIN = PG>
 struct HopMinBlocks {
-  static constexpr int value = PG == P64 ? 1 : (PG == P16 && PIN == P16) ? 7 : 5;
+  static constexpr int value = PG == P64 ? 1 : PG == PDF ? 3 : (PG == P16 && PIN == P16) ? 7 : 5;
 };
 
 template <int PG, int PIN, int POUT, bool DAG, int EPI, int LF = 0>
@@ -884,7 +988,8 @@ cudaError_t launch_hop(const HopArgs& args, bool dagger, int epi, cudaStream_t s
     if (epi == EPI_D && launch_stage<PG>(a, dagger, st, &e)) return e;
   }
 
-  if (PG != P64 && rbmax >= 2 && (epi == EPI_D || epi == EPI_AINV) && a.nrhs >= 2 && a.nrhs % 2 == 0) {
+  if constexpr (PG != P64 && PG != PDF) {
+  if (rbmax >= 2 && (epi == EPI_D || epi == EPI_AINV) && a.nrhs >= 2 && a.nrhs % 2 == 0) {
     // measured on 32^4: blocks of 4 win from 16 RHS up, blocks of 2 below
     const int NBsel = (a.nrhs % 4 == 0 && a.nrhs >= 16 && rbmax >= 4) ? 4 : 2;
     a.fblk = make_fastdiv((uint32_t)((a.nrhs + NBsel - 1) / NBsel));
@@ -902,6 +1007,7 @@ cudaError_t launch_hop(const HopArgs& args, bool dagger, int epi, cudaStream_t s
       default: k_hop_rb<PG, PIN, POUT, true, EPI_AINV, 4><<<bl, threads, 0, st>>>(a); break;
     }
     return cudaGetLastError();
+  }
   }
   if constexpr (PG == P32) {
     if (a.recon == 8) return launch_hop_single<PG, PIN, POUT, 8>(a, dagger, epi, blocks, threads, st);

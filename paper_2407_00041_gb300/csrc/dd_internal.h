@@ -31,7 +31,7 @@ int cuda_fail(cudaError_t e, const char* where);
     if (s_ != DD_OK) return s_; \
   } while (0)
 
-inline int prec_index(int prec) { return prec == P64 ? 0 : prec == P32 ? 1 : prec == P16 ? 2 : -1; }
+inline int prec_index(int prec) { return prec == P64 ? 0 : prec == P32 ? 1 : prec == P16 ? 2 : prec == PDF ? 3 : -1; }
 
 // Device buffer owned by a handle.
 struct DevBuf {
@@ -70,9 +70,10 @@ struct dd_lattice {
 struct dd_gauge {
   const dd_lattice* lat;
   unsigned prec_mask;
-  // native links per precision (index 0: F64, 1: F32, 2: F16):
-  // [parity][mu][9][Vh] complex elements, in 16-byte groups for F32 / F16
-  dd::DevBuf links[3];
+  // native links per precision (index 0: F64, 1: F32, 2: F16, 3: FP32
+  // pairs): [parity][mu][9][Vh] complex elements, in 16-byte groups for F32 /
+  // F16 (FP32 pairs: one float4 (re.h, re.l, im.h, im.l) per element)
+  dd::DevBuf links[4];
   // when every link is SU(3): a second, compressed FP32 copy used by
   // single-RHS launches, either rows 0 and 1 only (recon32 = 12,
   // [parity][12 float4 groups][Vh]; the kernels rebuild row 2) or eight reals
@@ -96,9 +97,9 @@ struct dd_clover {
   double m0, csw;
   unsigned prec_mask;
   // self-coupling blocks per precision: [parity][36][Vh] elements
-  dd::DevBuf clov[3];
+  dd::DevBuf clov[4];
   // A_ee^{-1} per precision: [36][Vh] elements (even sites)
-  dd::DevBuf ainv[3];
+  dd::DevBuf ainv[4];
   // workspace for canonical-layout calls and operator intermediates
   dd::DevBuf ws_in, ws_out, ws_tmp, ws_canon_in, ws_canon_out;
   // residual workspace of dd_sap
@@ -169,6 +170,8 @@ int links_to_recon32(dd_gauge* g, cudaStream_t st);
 // eight-real FP32 copy; *dev = max |rebuilt - FP64 link| over all elements
 int links_to_recon8(dd_gauge* g, double* dev, cudaStream_t st);
 int links_to_recon16(dd_gauge* g, cudaStream_t st);
+// the FP32-pair copy of the FP64 links (links[3])
+int links_to_pairs(dd_gauge* g, cudaStream_t st);
 int links_to_canonical(const dd_gauge* g, double* U_canon_dev, cudaStream_t st);
 int clover_build(dd_clover* op, cudaStream_t st);  // FP64 blocks, A_ee^{-1}, demoted copies
 int clover_to_dense(const dd_clover* op, double* A_dev /*[V][144] complex*/, cudaStream_t st);

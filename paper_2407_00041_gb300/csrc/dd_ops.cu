@@ -54,7 +54,7 @@ void DevBuf::release() {
 
 // ---------------------------------------------------------------- fields
 size_t field_bytes(const dd_lattice* lat, int prec, int subset, int nrhs) {
-  size_t h = prec == P64   ? half_field_bytes<P64>(lat->Vh, nrhs)
+  size_t h = (prec == P64 || prec == PDF) ? half_field_bytes<P64>(lat->Vh, nrhs)
              : prec == P32 ? half_field_bytes<P32>(lat->Vh, nrhs)
                            : half_field_bytes<P16>(lat->Vh, nrhs);
   return subset == 0 ? 2 * h : h;
@@ -89,7 +89,7 @@ Field field_view(const dd_lattice* lat, int prec, int subset, void* base, int nr
 }
 
 int64_t stencil_bytes_per_site(int pg, int nrhs) {
-  return pg == P64 ? 1152 + 384 * nrhs : pg == P32 ? 576 + 192 * nrhs : 288 + 104 * nrhs;
+  return (pg == P64 || pg == PDF) ? 1152 + 384 * nrhs : pg == P32 ? 576 + 192 * nrhs : 288 + 104 * nrhs;
 }
 
 // Depth of the Z-slabs of the full-lattice traversal: the largest divisor of
@@ -148,6 +148,8 @@ int run_hop(int pg, int pv, const HopArgs& a, bool dag, int epi, cudaStream_t st
   }
   if (pg == P64 && pv == P64)
     e = launch_hop<P64, P64, P64>(a, dag, epi, st);
+  else if (pg == PDF && pv == PDF)
+    e = launch_hop<PDF, PDF, PDF>(a, dag, epi, st);
   else if (pg == P32 && pv == P32)
     e = launch_hop<P32, P32, P32>(a, dag, epi, st);
   else if (pg == P16 && pv == P16)
@@ -232,6 +234,8 @@ int run_block(int pg, int pv, const BlockArgs& a, cudaStream_t st) {
   cudaError_t e;
   if (pg == P64 && pv == P64)
     e = launch_block<P64, P64, P64>(a, st);
+  else if (pg == PDF && pv == PDF)
+    e = launch_block<PDF, PDF, PDF>(a, st);
   else if (pg == P32 && pv == P32)
     e = launch_block<P32, P32, P32>(a, st);
   else if (pg == P16 && pv == P16)
@@ -408,7 +412,7 @@ dd::Geom dd_lattice::geom() const {
 
 const void* dd_gauge::U(int pi, int parity) const {
   if (!links[pi].ptr) return nullptr;
-  const size_t elem = pi == 0 ? 16 : pi == 1 ? 8 : 4;
+  const size_t elem = (pi == 0 || pi == 3) ? 16 : pi == 1 ? 8 : 4;
   return reinterpret_cast<const char*>(links[pi].ptr) + (size_t)parity * 36 * lat->Vh * elem;
 }
 
@@ -424,7 +428,7 @@ const void* dd_gauge::U2h(int parity) const {
 
 const void* dd_clover::M(int pi, int parity) const {
   if (!clov[pi].ptr) return nullptr;
-  const size_t elem = pi == 0 ? 16 : pi == 1 ? 8 : 4;
+  const size_t elem = (pi == 0 || pi == 3) ? 16 : pi == 1 ? 8 : 4;
   return reinterpret_cast<const char*>(clov[pi].ptr) + (size_t)parity * 36 * lat->Vh * elem;
 }
 

@@ -289,6 +289,16 @@ __global__ void k_links_recon8_error(int64_t nlinks, const double2* __restrict__
   if (threadIdx.x == 0) atomicMax(out, __float_as_uint(red[0]));
 }
 
+// FP64 complex elements -> FP32 pairs (re.h, re.l, im.h, im.l), the same
+// element order (links, self-coupling blocks, A_ee^-1)
+__global__ void k_split_pairs(int64_t n, const double2* __restrict__ in, float4* out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const double2 v = in[t];
+  const df re(v.x), im(v.y);
+  out[t] = make_float4(re.h, re.l, im.h, im.l);
+}
+
 __global__ void k_links_to_canonical(LexGeom g, const double2* __restrict__ U64, double2* Uc) {
   const int64_t V = 2 * g.Vh;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -833,6 +843,21 @@ int clover_build(dd_clover* op, cudaStream_t st) {
     k_group16<<<nblk(2 * 9 * Vh, 256), 256, 0, st>>>((const double2*)op->clov[0].ptr, (uint4*)op->clov[2].ptr, 2, Vh);
     k_group16<<<nblk(9 * Vh, 256), 256, 0, st>>>((const double2*)op->ainv[0].ptr, (uint4*)op->ainv[2].ptr, 1, Vh);
   }
+  if (op->prec_mask & PDF) {
+    DD_TRY(op->clov[3].alloc(nclov * sizeof(float4)));
+    DD_TRY(op->ainv[3].alloc(nainv * sizeof(float4)));
+    k_split_pairs<<<nblk(nclov, 256), 256, 0, st>>>(nclov, (const double2*)op->clov[0].ptr, (float4*)op->clov[3].ptr);
+    k_split_pairs<<<nblk(nainv, 256), 256, 0, st>>>(nainv, (const double2*)op->ainv[0].ptr, (float4*)op->ainv[3].ptr);
+  }
+  DD_CUDA(cudaGetLastError());
+  return DD_OK;
+}
+
+int links_to_pairs(dd_gauge* g, cudaStream_t st) {
+  const int64_t n = g->lat->V * 36;
+  DD_TRY(g->links[3].alloc((size_t)n * sizeof(float4)));
+  k_split_pairs<<<nblk(n, 256), 256, 0, st>>>(n, reinterpret_cast<const double2*>(g->links[0].ptr),
+                                              reinterpret_cast<float4*>(g->links[3].ptr));
   DD_CUDA(cudaGetLastError());
   return DD_OK;
 }
@@ -867,6 +892,8 @@ int pack(const dd_lattice* lat, int prec, int subset, const double* canon, const
   const int64_t n = a.ns * f.nrhs * a.npar;
   if (prec == P64)
     k_pack<P64><<<nblk(n, 128), 128, 0, st>>>(a, c);
+  else if (prec == PDF)
+    k_pack<PDF><<<nblk(n, 128), 128, 0, st>>>(a, c);
   else if (prec == P32)
     k_pack<P32><<<nblk(n, 128), 128, 0, st>>>(a, c);
   else
@@ -898,6 +925,8 @@ int unpack(const dd_lattice* lat, int prec, int subset, const Field& f, double* 
   const int64_t n = a.ns * f.nrhs * a.npar;
   if (prec == P64)
     k_unpack<P64><<<nblk(n, 128), 128, 0, st>>>(a, c);
+  else if (prec == PDF)
+    k_unpack<PDF><<<nblk(n, 128), 128, 0, st>>>(a, c);
   else if (prec == P32)
     k_unpack<P32><<<nblk(n, 128), 128, 0, st>>>(a, c);
   else

@@ -707,6 +707,7 @@ int solve(dd_clover* op, const dd_solve_params* prm, const double* b_canon, doub
   const int pv = pin == P64 ? P64 : P32;
   const int pg = pin;
   if (prec_index(pin) < 0) return fail(DD_ERR_ARG, "bad inner precision");
+  if (pin == PDF) return fail(DD_ERR_UNSUPPORTED, "inner precision: F64, F32 or F16");
   if (!op->clov[prec_index(pg)].ptr || !op->gauge->links[prec_index(pg)].ptr)
     return fail(DD_ERR_UNSUPPORTED, "inner precision not created in the handles");
   if (prm->restart < 1 || prm->restart > 32) return fail(DD_ERR_ARG, "restart must be in 1..32");

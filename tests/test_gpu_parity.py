@@ -246,6 +246,7 @@ def test_eight_real_fp32_links(eps):
         got = apply(op, which, dd.DD_PREC_F32, psi)
         assert rel(got[0], ref_fn(U, A, psi[0].reshape(-1, 12), dims)) < TOL[dd.DD_PREC_F32]
         assert rel(got, ref12[which]) < 1e-6
+        assert not np.array_equal(got, ref12[which])  # the rebuilt links differ in the last bits
     eo = oracle.EvenOdd(U, A, dims)
     v = psi[0].reshape(-1, 12)[eo.odd][None]
     for which, ref_fn in ((dd.DD_OP_DHAT, eo.Dhat), (dd.DD_OP_DHAT_H, eo.DhatH)):
