@@ -871,11 +871,16 @@ __global__ void __launch_bounds__(128, NB >= 4 ? 2 : 3) k_hop_rb(const HopArgs a
 // threads (at most 102 registers): measured on the 48^3 x 96 lattice this
 // beats the unconstrained 108-register build by about 5%.  The FP16-storage
 // stencil (half2 projection, mixed FMAs) asks for 7 (at most 72 registers):
-// 0.738 ms against 0.762 ms with 5 and 0.857 ms with 3 at 48^3 x 96.  FP64 is
-// bound by the FP64 pipe and keeps the unconstrained allocation.
+// 0.738 ms against 0.762 ms with 5 and 0.857 ms with 3 at 48^3 x 96 (with
+// two-row links 0.698 ms against 0.709 with 6 and 0.724 with 8).  FP16 links
+// with FP32 vectors (the FP16-inner solve) take 4: the solve 1.468 s against
+// 1.502 s with 5 and 1.513 s with 6.  The FP32-pair stencil takes 3 (at most
+// 168 registers: 7.6 ms against 11.3 ms with 4, which spills, and 15.2 ms
+// unconstrained at 188 registers).  FP64 is bound by the FP64 pipe and keeps
+// the unconstrained allocation.
 template <int PG, int PIN = PG>
 struct HopMinBlocks {
-  static constexpr int value = PG == P64 ? 1 : PG == PDF ? 3 : (PG == P16 && PIN == P16) ? 7 : 5;
+  static constexpr int value = PG == P64 ? 1 : PG == PDF ? 3 : (PG == P16 && PIN == P16) ? 7 : PG == P16 ? 4 : 5;
 };
 
 template <int PG, int PIN, int POUT, bool DAG, int EPI, int LF = 0>
