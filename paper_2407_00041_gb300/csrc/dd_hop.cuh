@@ -875,9 +875,8 @@ __global__ void __launch_bounds__(128, NB >= 4 ? 2 : 3) k_hop_rb(const HopArgs a
 // two-row links 0.698 ms against 0.709 with 6 and 0.724 with 8).  FP16 links
 // with FP32 vectors (the FP16-inner solve) take 4: the solve 1.468 s against
 // 1.502 s with 5 and 1.513 s with 6.  The FP32-pair stencil takes 3 (at most
-// 168 registers: 7.6 ms against 11.3 ms with 4, which spills, and 15.2 ms
-// unconstrained at 188 registers).  FP64 is bound by the FP64 pipe and keeps
-// the unconstrained allocation.
+// 168 registers: 7.6 ms against 11.3 ms with 4, which spills).  FP64 is
+// bound by the FP64 pipe and keeps the unconstrained allocation.
 template <int PG, int PIN = PG>
 struct HopMinBlocks {
   static constexpr int value = PG == P64 ? 1 : PG == PDF ? 3 : (PG == P16 && PIN == P16) ? 7 : PG == P16 ? 4 : 5;
