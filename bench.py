@@ -1028,6 +1028,8 @@ def main():
             legs.insert(1, ("mixed_f16", PREC["f16"], 8, 32, 1e-3, reals32))
         if args.solve_inner == "f32" and "f32_link8" in variants:
             legs.insert(1, ("mixed_link8", PREC["f32"], 8, 64, 1e-6, 8))
+        if "df64" in variants:  # the FP64-accuracy solve with the FP32-pair stencil (FP64 vectors)
+            legs.append(("df64", PREC["df64"], 8, 64, 1e-6, reals32))
         for name, inner, restart, cg, tol_in, reals in legs:
             x = torch.zeros_like(b)
             log(f"solve {name}")
@@ -1047,7 +1049,8 @@ def main():
                            "true_residual": st["true_residual"], "outer": st["outer_iterations"],
                            "inner_steps": st["inner_iterations"], "applies_inner": st["applies_inner"],
                            "applies_fp64": st["applies_fp64"],
-                           "inner_prec": {1: "f64", 2: "f32", 4: "f16 links/clover, f32 vectors"}[inner],
+                           "inner_prec": {1: "f64", 2: "f32", 4: "f16 links/clover, f32 vectors",
+                                          8: "f64 accuracy in FP32-pair arithmetic, f64 vectors"}[inner],
                            "f32_link_reals": reals,
                            "method": f"even-odd FGMRES({restart}), M_j = {cg} CG steps on Dhat^H Dhat, "
                                      f"inner tolerance {tol_in:g}, FP64 refinement"}
@@ -1058,6 +1061,10 @@ def main():
             solve["mixed_f16_vs_fp64_solution_rel_diff"] = \
                 (sols["mixed_f16"] - sols["fp64"]).norm().item() / sols["fp64"].norm().item()
             solve["speedup_mixed_f16_over_fp64"] = solve["fp64"]["seconds"] / solve["mixed_f16"]["seconds"]
+        if "df64" in solve:
+            solve["df64_vs_fp64_solution_rel_diff"] = \
+                (sols["df64"] - sols["fp64"]).norm().item() / sols["fp64"].norm().item()
+            solve["speedup_df64_over_fp64"] = solve["fp64"]["seconds"] / solve["df64"]["seconds"]
         if "mixed_link8" in solve:
             solve["mixed_link8_vs_fp64_solution_rel_diff"] = \
                 (sols["mixed_link8"] - sols["fp64"]).norm().item() / sols["fp64"].norm().item()

@@ -128,7 +128,9 @@ extern "C" {
  * fields of this precision have the FP64 byte count).  Accepted by
  * dd_gauge_create / dd_gauge_generate / dd_clover_create (precision masks),
  * dd_field_bytes, dd_pack, dd_unpack and dd_apply (all operators, native
- * and canonical layouts except the paired one); not by the solver, SAP,
+ * and canonical layouts except the paired one), and as dd_solve's
+ * inner_prec (FP64 Krylov vectors, split into pairs as the stencil loads
+ * them, 2^-46 relative; preconditioners none, normal and CGNR); not by SAP,
  * AMG, the batch, the domain decomposition or dd_force (DD_ERR_ARG or
  * DD_ERR_UNSUPPORTED).  Canonical inputs are split into pairs exactly to
  * about 2^-48 relative; results are rounded to FP64 by h + l. */
@@ -315,7 +317,8 @@ typedef struct {
   int restart;         /* Krylov dimension m of FGMRES(m), e.g. 30 */
   int max_restarts;    /* restart cycles allowed per inner solve */
   int max_outer;       /* refinement steps allowed (1 with inner_prec = F64 means a plain FP64 solve) */
-  int inner_prec;      /* DD_PREC_F64, DD_PREC_F32 or DD_PREC_F16 (FP16 links/clover, FP32 vectors) */
+  int inner_prec;      /* DD_PREC_F64, DD_PREC_F32, DD_PREC_F16 (FP16 links/clover, FP32 vectors) or
+                          DD_PREC_DF64 (FP32-pair arithmetic, FP64 vectors) */
   double inner_tol;    /* relative residual reduction asked of each inner solve, e.g. 1e-6 */
   int even_odd;        /* 1: inner solves use Dhat on odd sites; 0: D on the full lattice */
   int verbose;         /* 1: print progress lines to stderr */

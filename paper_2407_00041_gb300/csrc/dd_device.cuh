@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace dd {
 
 // ---------------------------------------------------------------- complex
@@ -153,6 +155,24 @@ __device__ __forceinline__ df df_fma(df a, df b, df c) {
   df r;
   fast_two_sum(s, t, r.h, r.l);
   return r;
+}
+
+// An FP64 value as a pair without FP64 instructions (the FP64 pipe of this
+// GPU runs at 1/64 of the FP32 rate): h = x truncated to 24 significant
+// bits, built from the sign, the rebased exponent and the top 23 fraction
+// bits; l = the next 23 fraction bits as an exact integer (the 2^23 magic
+// constant) times the power of two of their place.  |x - h - l| < 2^-46 |x|.
+// |x| < 2^-126 (and zero) gives (0, 0); |x| >= 2^128 is outside the range.
+__device__ __forceinline__ df df_split(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
+  const int e = (int)((hi >> 20) & 0x7FFu);
+  const unsigned sgn = hi & 0x80000000u;
+  const float h = __uint_as_float(sgn | ((unsigned)(e - 896) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
+  const float r = __fsub_rn(__uint_as_float(0x4B000000u | ((lo >> 6) & 0x7FFFFFu)), 8388608.f);
+  const int se = e - 942;  // FP32 exponent field of 2^(e - 1023 - 46)
+  const float l = __fmul_rn(r, __uint_as_float(sgn | ((unsigned)(se > 0 ? se : 0) << 23)));
+  return e > 896 ? df(h, l) : df(0.f, 0.f);
 }
 
 // Complex multiply-accumulate of FP32 pairs for the short sums of the stencil
@@ -349,7 +369,10 @@ __device__ __forceinline__ void load_spinor(const HalfField& f, int64_t gstride,
 #pragma unroll
     for (int c = 0; c < 12; ++c) {
       double2 t = __ldg(b + c * gstride);
-      v[c] = mk<R>(t.x, t.y);
+      if constexpr (std::is_same<R, df>::value)
+        v[c] = mk(df_split(t.x), df_split(t.y));
+      else
+        v[c] = mk<R>(t.x, t.y);
     }
   } else if constexpr (P == P32) {
     const float4* b = reinterpret_cast<const float4*>(f.base) + i;
@@ -415,7 +438,7 @@ __device__ __forceinline__ void store_spinor(const HalfField& f, int64_t gstride
     double2* b = reinterpret_cast<double2*>(f.base) + i;
 #pragma unroll
     for (int c = 0; c < 12; ++c) {
-      const double2 d = make_double2(v[c].re, v[c].im);
+      const double2 d = make_double2((double)v[c].re, (double)v[c].im);
       if (STREAM) __stcs(b + c * gstride, d); else b[c * gstride] = d;
     }
   } else if constexpr (P == P32) {

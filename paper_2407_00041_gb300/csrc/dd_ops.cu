@@ -150,6 +150,8 @@ int run_hop(int pg, int pv, const HopArgs& a, bool dag, int epi, cudaStream_t st
     e = launch_hop<P64, P64, P64>(a, dag, epi, st);
   else if (pg == PDF && pv == PDF)
     e = launch_hop<PDF, PDF, PDF>(a, dag, epi, st);
+  else if (pg == PDF && pv == P64)
+    e = launch_hop<PDF, P64, P64>(a, dag, epi, st);
   else if (pg == P32 && pv == P32)
     e = launch_hop<P32, P32, P32>(a, dag, epi, st);
   else if (pg == P16 && pv == P16)
@@ -236,6 +238,8 @@ int run_block(int pg, int pv, const BlockArgs& a, cudaStream_t st) {
     e = launch_block<P64, P64, P64>(a, st);
   else if (pg == PDF && pv == PDF)
     e = launch_block<PDF, PDF, PDF>(a, st);
+  else if (pg == PDF && pv == P64)
+    e = launch_block<PDF, P64, P64>(a, st);
   else if (pg == P32 && pv == P32)
     e = launch_block<P32, P32, P32>(a, st);
   else if (pg == P16 && pv == P16)

@@ -527,7 +527,7 @@ int schur_batch(dd_clover* op, const dd_solve_params* prm, const double* b_in, d
                 Inner& inner, cudaStream_t st, dd_stats& s, double& worst_out, bool& ok_out) {
   const dd_lattice* lat = op->lat;
   const int pin = prm->inner_prec;
-  const int pv = pin == P64 ? P64 : P32;
+  const int pv = (pin == P64 || pin == PDF) ? P64 : P32;  // FP32 pairs work on FP64 vectors
   const size_t h64 = field_bytes(lat, P64, 1, nb);
   const size_t canon = (size_t)lat->V * 12 * 16 * nb;
   DevBuf be, bo, bh, xo, ro, te, stage, red, partials, fv, ev;
@@ -663,7 +663,7 @@ int solve_schur(dd_clover* op, const dd_solve_params* prm, const double* b, doub
   const auto t0 = std::chrono::steady_clock::now();
   const dd_lattice* lat = op->lat;
   const int pin = prm->inner_prec;
-  const int pv = pin == P64 ? P64 : P32;
+  const int pv = (pin == P64 || pin == PDF) ? P64 : P32;  // FP32 pairs work on FP64 vectors
   if (prec_index(pin) < 0) return fail(DD_ERR_ARG, "bad inner precision");
   if (!op->clov[prec_index(pin)].ptr || !op->gauge->links[prec_index(pin)].ptr)
     return fail(DD_ERR_UNSUPPORTED, "inner precision not created in the handles");
@@ -704,10 +704,9 @@ int solve(dd_clover* op, const dd_solve_params* prm, const double* b_canon, doub
   const auto t0 = std::chrono::steady_clock::now();
   const dd_lattice* lat = op->lat;
   const int pin = prm->inner_prec;
-  const int pv = pin == P64 ? P64 : P32;
+  const int pv = (pin == P64 || pin == PDF) ? P64 : P32;  // FP32 pairs work on FP64 vectors
   const int pg = pin;
   if (prec_index(pin) < 0) return fail(DD_ERR_ARG, "bad inner precision");
-  if (pin == PDF) return fail(DD_ERR_UNSUPPORTED, "inner precision: F64, F32 or F16");
   if (!op->clov[prec_index(pg)].ptr || !op->gauge->links[prec_index(pg)].ptr)
     return fail(DD_ERR_UNSUPPORTED, "inner precision not created in the handles");
   if (prm->restart < 1 || prm->restart > 32) return fail(DD_ERR_ARG, "restart must be in 1..32");

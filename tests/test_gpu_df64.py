@@ -114,6 +114,32 @@ def test_precision_checks():
     b = torch.from_numpy(psi).cuda()
     x = torch.zeros_like(b)
     with pytest.raises(dd.DDError) as e:
-        op2.solve(b, x, 1, inner_prec=dd.DD_PREC_DF64)
+        op2.solve(b, x, 1, inner_prec=dd.DD_PREC_DF64, precond=dd.DD_PRECOND_SAP, sap_block=(2, 2, 2, 2))
     assert e.value.status == dd.DD_ERR_UNSUPPORTED
     assert g2.link_reals(dd.DD_PREC_DF64) == 18
+
+
+@pytest.mark.parametrize("even_odd", [1, 0])
+@pytest.mark.parametrize("precond", [dd.DD_PRECOND_NONE, dd.DD_PRECOND_CGNR])
+def test_solve_with_pair_inner(even_odd, precond):
+    """FGMRES with the FP32-pair stencil on FP64 vectors: one refinement
+    step reaches 1e-10 (the inner operator is accurate to ~1e-14), the oracle
+    recomputes the residual, and the solution matches the FP64 solve."""
+    dims = (8, 8, 4, 4)
+    U, lat, g, op = make_df(dims)
+    A = oracle.clover(U, dims, M0, CSW)
+    b = synthetic.spinor(dims, nrhs=1)
+    bt = torch.from_numpy(b).cuda()
+    xs = {}
+    for inner in (dd.DD_PREC_DF64, dd.DD_PREC_F64):
+        x = torch.zeros_like(bt)
+        status, st = op.solve(bt, x, 1, tol=1e-10, inner_prec=inner, even_odd=even_odd, restart=16, precond=precond,
+                              precond_iters=8)
+        assert status == 0, st
+        assert st["converged"] == 1 and st["true_residual"] < 1e-10
+        xs[inner] = x.cpu().numpy()[0]
+        res = b[0].reshape(-1, 12) - oracle.apply_D(U, A, xs[inner].reshape(-1, 12), dims)
+        assert np.linalg.norm(res) / np.linalg.norm(b[0]) < 1e-10
+        if inner == dd.DD_PREC_DF64:
+            assert st["outer_iterations"] == 1
+    assert rel(xs[dd.DD_PREC_DF64], xs[dd.DD_PREC_F64]) < 1e-8
