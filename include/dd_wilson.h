@@ -496,6 +496,13 @@ int dd_batch_create(dd_clover* const* ops, int count, int prec, const int* nrhs,
 int dd_batch_destroy(dd_batch* b);
 /* ins[i], outs[i]: native device fields of operator i (full lattice, nrhs[i] RHS). */
 int dd_apply_batched(dd_batch* b, const void* const* ins, void* const* outs, void* stream);
+/* Field layout of the batch: DD_LAYOUT_NATIVE (default) or
+ * DD_LAYOUT_NATIVE_PAIRED, under which the lattices with an even RHS count
+ * take paired-RHS fields (dd_pack_paired; their launches run the packed
+ * FP32x2 stencil) and the others native fields.  The paired layout runs one
+ * launch per lattice on forked streams (the persistent shapes take native
+ * fields only) and drops a captured graph.  DD_ERR_ARG for another layout. */
+int dd_batch_set_layout(dd_batch* b, int layout);
 /* Time candidate launch shapes on `stream` and keep the fastest; optional
  * report of the chosen shape (slots per tile, threads per block, CTAs per SM,
  * where 0 CTAs per SM means one CTA per work item instead of a persistent

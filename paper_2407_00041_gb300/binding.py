@@ -92,6 +92,7 @@ SIGNATURES = {
     "dd_amg_apply": (_I, [_P, _P, _P, _I, _I, _P]),
     "dd_batch_create": (_I, [_P, _I, _I, _P, _P]),
     "dd_batch_destroy": (_I, [_P]),
+    "dd_batch_set_layout": (_I, [_P, _I]),
     "dd_apply_batched": (_I, [_P, _P, _P, _P]),
     "dd_batch_tune": (_I, [_P, _P, _P, _P, _P]),
     "dd_apply_batched_graph": (_I, [_P, _P, _P, _P]),

@@ -29,6 +29,9 @@ struct dd_batch {
   int tile = 128;
   int ctas_per_sm = 4;
   int sms = 0;
+  // DD_LAYOUT_NATIVE_PAIRED: lattices with an even RHS count take paired-RHS
+  // fields (one launch per lattice only)
+  int layout = DD_LAYOUT_NATIVE;
   dd::DevBuf args, item_start;
   dd::HopArgs* h_args = nullptr;  // pinned staging
   std::vector<const void*> last_in;
@@ -148,8 +151,9 @@ int launch_per_lattice(dd_batch* b, cudaStream_t st) {
   for (int k = 0; k < b->count; ++k) {
     const int i = b->order[k];
     dd_clover* op = b->ops[i];
-    Field fi = field_view(op->lat, b->prec, 0, const_cast<void*>(b->last_in[i]), b->nrhs[i]);
-    Field fo = field_view(op->lat, b->prec, 0, b->last_out[i], b->nrhs[i]);
+    const int paired = b->layout == DD_LAYOUT_NATIVE_PAIRED && b->nrhs[i] % 2 == 0;
+    Field fi = field_view(op->lat, b->prec, 0, const_cast<void*>(b->last_in[i]), b->nrhs[i], paired);
+    Field fo = field_view(op->lat, b->prec, 0, b->last_out[i], b->nrhs[i], paired);
     DD_CUDA(cudaStreamWaitEvent(b->side[k], b->ev[b->count], 0));
     DD_TRY(op_D(op, b->prec, b->prec, false, fi, fo, b->side[k]));
     DD_CUDA(cudaEventRecord(b->ev[k], b->side[k]));
@@ -245,6 +249,17 @@ int dd_batch_create(dd_clover* const* ops, int count, int prec, const int* nrhs,
   return DD_OK;
 }
 
+int dd_batch_set_layout(dd_batch* b, int layout) {
+  if (!b) return fail(DD_ERR_ARG, "null batch");
+  if (layout != DD_LAYOUT_NATIVE && layout != DD_LAYOUT_NATIVE_PAIRED)
+    return fail(DD_ERR_ARG, "batch layout: DD_LAYOUT_NATIVE or DD_LAYOUT_NATIVE_PAIRED");
+  b->layout = layout;
+  if (layout == DD_LAYOUT_NATIVE_PAIRED) b->ctas_per_sm = -1;
+  drop_graph(b);
+  b->staged_tile = -1;
+  return DD_OK;
+}
+
 int dd_batch_destroy(dd_batch* b) {
   delete b;
   return DD_OK;
@@ -274,6 +289,7 @@ int dd_batch_tune(dd_batch* b, const void* const* ins, void* const* outs, void* 
     // (once) one launch per lattice
     const int shapes[5] = {cap, std::max(1, cap - 1), std::max(1, cap / 2), 0, -1};
     for (int ci = 0; ci < (ti == 0 ? 5 : 4); ++ci) {
+      if (b->layout == DD_LAYOUT_NATIVE_PAIRED && shapes[ci] != -1) continue;  // paired fields: per lattice only
       b->tile = tiles[ti];
       b->ctas_per_sm = shapes[ci];
       DD_TRY(stage(b, ins, outs, st));
