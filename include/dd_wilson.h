@@ -148,6 +148,13 @@ extern "C" {
 #define DD_LAYOUT_CANONICAL_HOST 1
 #define DD_LAYOUT_NATIVE 2
 #define DD_LAYOUT_NATIVE_PAIRED 3
+/* complex64 canonical fields [N][V or V/2][4][3] (float re, im), on the
+ * device or on the host: dd_apply only (native layout inside; FP32 / FP16
+ * applies read and write them without the complex128 round trip, so the
+ * host-buffer apply moves half the bytes; FP64 / FP32-pair applies take
+ * their inputs at FP32 precision). */
+#define DD_LAYOUT_CANONICAL_C64 4
+#define DD_LAYOUT_CANONICAL_HOST_C64 5
 
 typedef struct dd_lattice dd_lattice;
 typedef struct dd_gauge dd_gauge;

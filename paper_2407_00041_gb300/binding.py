@@ -18,6 +18,7 @@ DD_PREC_F64, DD_PREC_F32, DD_PREC_F16 = 1, 2, 4
 DD_PREC_DF64 = 8  # FP64-accurate arithmetic in FP32 pairs
 DD_OP_D, DD_OP_DH, DD_OP_DHAT, DD_OP_DHAT_H, DD_OP_SC = 0, 1, 2, 3, 4
 DD_LAYOUT_CANONICAL, DD_LAYOUT_CANONICAL_HOST, DD_LAYOUT_NATIVE, DD_LAYOUT_NATIVE_PAIRED = 0, 1, 2, 3
+DD_LAYOUT_CANONICAL_C64, DD_LAYOUT_CANONICAL_HOST_C64 = 4, 5  # complex64 canonical fields
 
 DD_PRECOND_NONE, DD_PRECOND_NORMAL, DD_PRECOND_CGNR, DD_PRECOND_SAP, DD_PRECOND_AMG = 0, 1, 2, 3, 4
 PREC = {"f64": DD_PREC_F64, "f32": DD_PREC_F32, "f16": DD_PREC_F16, "df64": DD_PREC_DF64}

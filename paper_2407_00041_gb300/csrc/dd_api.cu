@@ -30,9 +30,12 @@ bool valid_prec(int p) { return p == DD_PREC_F64 || p == DD_PREC_F32 || p == DD_
 // precisions of dd_apply, dd_pack, dd_unpack and dd_field_bytes
 bool valid_apply_prec(int p) { return valid_prec(p) || p == DD_PREC_DF64; }
 
+bool host_layout(int layout) { return layout == DD_LAYOUT_CANONICAL_HOST || layout == DD_LAYOUT_CANONICAL_HOST_C64; }
+bool c64_layout(int layout) { return layout == DD_LAYOUT_CANONICAL_C64 || layout == DD_LAYOUT_CANONICAL_HOST_C64; }
+
 // Copy a canonical field into device memory when it lives on the host.
 int stage_in(DevBuf& buf, const void* src, size_t bytes, int layout, const double** dev, cudaStream_t st) {
-  if (layout == DD_LAYOUT_CANONICAL_HOST) {
+  if (host_layout(layout)) {
     DD_TRY(buf.ensure(bytes));
     DD_CUDA(cudaMemcpyAsync(buf.ptr, src, bytes, cudaMemcpyHostToDevice, st));
     *dev = reinterpret_cast<const double*>(buf.ptr);
@@ -49,7 +52,8 @@ int stage_in(DevBuf& buf, const void* src, size_t bytes, int layout, const doubl
 // a chunk needs the input slices one beyond each end, so the last chunk is
 // copied first and chunk c is computed once chunk c + 1 is packed.
 int apply_host_pipelined(dd_clover* op, int prec, bool dagger, const void* hin, void* hout, int nrhs,
-                         cudaStream_t st) {
+                         cudaStream_t st, bool c64) {
+  const size_t esz = c64 ? 8 : 16;  // bytes per canonical complex element
   const dd_lattice* lat = op->lat;
   const int nT = lat->dims[0];
   static const int max_chunks = [] {
@@ -59,7 +63,7 @@ int apply_host_pipelined(dd_clover* op, int prec, bool dagger, const void* hin, 
   }();
   const int C = nT < max_chunks ? nT : max_chunks;
   const int64_t slice = (int64_t)lat->dims[1] * lat->dims[2] * lat->dims[3];
-  const size_t row = (size_t)lat->V * 12 * 16;  // one RHS of the canonical array
+  const size_t row = (size_t)lat->V * 12 * esz;  // one RHS of the canonical array
   const size_t cb = row * nrhs;
   const size_t nb = field_bytes(lat, prec, 0, nrhs);
   DD_TRY(op->ws_canon_in.ensure(cb));
@@ -71,8 +75,8 @@ int apply_host_pipelined(dd_clover* op, int prec, bool dagger, const void* hin, 
   cudaEvent_t start = hp.ev[2 * C];
   auto t0_of = [&](int c) { return (int)((int64_t)c * nT / C); };
   auto copy_rows = [&](void* dst, const void* src, int c, cudaMemcpyKind kind, cudaStream_t s) -> cudaError_t {
-    const size_t off = (size_t)t0_of(c) * slice * 12 * 16;
-    const size_t w = (size_t)(t0_of(c + 1) - t0_of(c)) * slice * 12 * 16;
+    const size_t off = (size_t)t0_of(c) * slice * 12 * esz;
+    const size_t w = (size_t)(t0_of(c + 1) - t0_of(c)) * slice * 12 * esz;
     return cudaMemcpy2DAsync(static_cast<char*>(dst) + off, row, static_cast<const char*>(src) + off, row, w, nrhs,
                              kind, s);
   };
@@ -91,12 +95,17 @@ int apply_host_pipelined(dd_clover* op, int prec, bool dagger, const void* hin, 
   }
   auto pack_chunk = [&](int c) -> int {
     DD_CUDA(cudaStreamWaitEvent(st, hp.ev[c], 0));
+    if (c64)
+      return pack_c64(lat, prec, 0, reinterpret_cast<const float*>(cin), fin, st, t0_of(c), t0_of(c + 1) - t0_of(c));
     return pack(lat, prec, 0, cin, fin, st, t0_of(c), t0_of(c + 1) - t0_of(c));
   };
   auto compute_chunk = [&](int c) -> int {
     const int t0 = t0_of(c), nt = t0_of(c + 1) - t0;
     DD_TRY(op_D_slices(op, prec, prec, dagger, fin, fout, t0, nt, st));
-    DD_TRY(unpack(lat, prec, 0, fout, cout, st, t0, nt));
+    if (c64)
+      DD_TRY(unpack_c64(lat, prec, 0, fout, reinterpret_cast<float*>(cout), st, t0, nt));
+    else
+      DD_TRY(unpack(lat, prec, 0, fout, cout, st, t0, nt));
     DD_CUDA(cudaEventRecord(hp.ev[C + c], st));
     DD_CUDA(cudaStreamWaitEvent(hp.s_out, hp.ev[C + c], 0));
     DD_CUDA(copy_rows(hout, cout, c, cudaMemcpyDeviceToHost, hp.s_out));
@@ -435,7 +444,7 @@ int dd_apply(dd_clover* op, int which, int prec, const void* in, void* out, int 
   if (!op || !in || !out || nrhs < 1) return fail(DD_ERR_ARG, "null argument or nrhs < 1");
   if (!valid_apply_prec(prec)) return fail(DD_ERR_ARG, "bad precision");
   if (which < DD_OP_D || which > DD_OP_SC) return fail(DD_ERR_ARG, "bad operator");
-  if (layout < DD_LAYOUT_CANONICAL || layout > DD_LAYOUT_NATIVE_PAIRED) return fail(DD_ERR_ARG, "bad layout");
+  if (layout < DD_LAYOUT_CANONICAL || layout > DD_LAYOUT_CANONICAL_HOST_C64) return fail(DD_ERR_ARG, "bad layout");
   if (layout == DD_LAYOUT_NATIVE_PAIRED) {
     if (nrhs % 2 != 0 || (prec != DD_PREC_F32 && prec != DD_PREC_F16))
       return fail(DD_ERR_ARG, "paired layout: precision F32 or F16 and an even nrhs");
@@ -449,16 +458,17 @@ int dd_apply(dd_clover* op, int which, int prec, const void* in, void* out, int 
   const bool half = which == DD_OP_DHAT || which == DD_OP_DHAT_H;
   const int subset = half ? 1 : 0;
   const size_t nb = field_bytes(lat, prec, subset, nrhs);
-  const size_t cb = (size_t)(half ? lat->Vh : lat->V) * 12 * 16 * nrhs;
-  if (layout == DD_LAYOUT_CANONICAL_HOST && (which == DD_OP_D || which == DD_OP_DH))
-    return apply_host_pipelined(op, prec, which == DD_OP_DH, in, out, nrhs, st);
+  const bool c64 = c64_layout(layout);
+  const size_t cb = (size_t)(half ? lat->Vh : lat->V) * 12 * (c64 ? 8 : 16) * nrhs;
+  if (host_layout(layout) && (which == DD_OP_D || which == DD_OP_DH))
+    return apply_host_pipelined(op, prec, which == DD_OP_DH, in, out, nrhs, st, c64);
   Field fin, fout;
   const double* cin = nullptr;
   // canonical fields with an even RHS count go through the paired-RHS stencil
   // (bit-identical to the RHS-blocked one; DD_RHS_BLOCK=1 keeps one thread
   // per site and RHS, DD_STAGE=1 the row-staged stencil)
   const int paired = layout == DD_LAYOUT_NATIVE_PAIRED ||
-                     (layout != DD_LAYOUT_NATIVE && nrhs % 2 == 0 && which != DD_OP_SC &&
+                     (layout != DD_LAYOUT_NATIVE && !c64 && nrhs % 2 == 0 && which != DD_OP_SC &&
                       (prec == DD_PREC_F32 || prec == DD_PREC_F16) && rhs_block_limit() >= 2 && !stage_opted_in());
   if (layout == DD_LAYOUT_NATIVE || layout == DD_LAYOUT_NATIVE_PAIRED) {
     fin = field_view(lat, prec, subset, const_cast<void*>(in), nrhs, paired);
@@ -469,7 +479,10 @@ int dd_apply(dd_clover* op, int which, int prec, const void* in, void* out, int 
     DD_TRY(op->ws_out.ensure(nb));
     fin = field_view(lat, prec, subset, op->ws_in.ptr, nrhs, paired);
     fout = field_view(lat, prec, subset, op->ws_out.ptr, nrhs, paired);
-    DD_TRY(pack(lat, prec, subset, cin, fin, st));
+    if (c64)
+      DD_TRY(pack_c64(lat, prec, subset, reinterpret_cast<const float*>(cin), fin, st));
+    else
+      DD_TRY(pack(lat, prec, subset, cin, fin, st));
   }
   switch (which) {
     case DD_OP_D:
@@ -487,12 +500,15 @@ int dd_apply(dd_clover* op, int which, int prec, const void* in, void* out, int 
   }
   if (layout != DD_LAYOUT_NATIVE && layout != DD_LAYOUT_NATIVE_PAIRED) {
     double* cout = reinterpret_cast<double*>(out);
-    if (layout == DD_LAYOUT_CANONICAL_HOST) {
+    if (host_layout(layout)) {
       DD_TRY(op->ws_canon_out.ensure(cb));
       cout = reinterpret_cast<double*>(op->ws_canon_out.ptr);
     }
-    DD_TRY(unpack(lat, prec, subset, fout, cout, st));
-    if (layout == DD_LAYOUT_CANONICAL_HOST) {
+    if (c64)
+      DD_TRY(unpack_c64(lat, prec, subset, fout, reinterpret_cast<float*>(cout), st));
+    else
+      DD_TRY(unpack(lat, prec, subset, fout, cout, st));
+    if (host_layout(layout)) {
       DD_CUDA(cudaMemcpyAsync(out, cout, cb, cudaMemcpyDeviceToHost, st));
       DD_CUDA(cudaStreamSynchronize(st));
     }

@@ -182,5 +182,10 @@ int pack(const dd_lattice* lat, int prec, int subset, const double* canon, const
          int t0 = 0, int nt = 0);
 int unpack(const dd_lattice* lat, int prec, int subset, const Field& f, double* canon, cudaStream_t st, int t0 = 0,
            int nt = 0);
+// the same for complex64 canonical fields [N][V][12] (native layout only)
+int pack_c64(const dd_lattice* lat, int prec, int subset, const float* canon, const Field& f, cudaStream_t st,
+             int t0 = 0, int nt = 0);
+int unpack_c64(const dd_lattice* lat, int prec, int subset, const Field& f, float* canon, cudaStream_t st,
+               int t0 = 0, int nt = 0);
 
 }  // namespace dd

@@ -602,8 +602,9 @@ __device__ __forceinline__ int64_t canon_offset(const PackArgs& a, int p, int64_
   return ((int64_t)r * a.g.Vh + s) * 12;
 }
 
-template <int P>
-__global__ void k_pack(PackArgs a, const double2* __restrict__ canon) {
+// CT: the canonical element, double2 (complex128) or float2 (complex64)
+template <int P, typename CT = double2>
+__global__ void k_pack(PackArgs a, const CT* __restrict__ canon) {
   using R = typename SpinorStore<P>::real;
   const int64_t nper = a.ns * a.nrhs;
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -616,18 +617,18 @@ __global__ void k_pack(PackArgs a, const double2* __restrict__ canon) {
   t += a.s0 * a.nrhs;
   const int64_t s = t / a.nrhs;
   const int r = (int)(t - s * a.nrhs);
-  const double2* src = canon + canon_offset(a, p, s, r);
+  const CT* src = canon + canon_offset(a, p, s, r);
   cx<R> v[12];
 #pragma unroll
   for (int c = 0; c < 12; ++c) {
-    double2 d = src[c];
+    const CT d = src[c];
     v[c] = mk<R>((R)d.x, (R)d.y);
   }
   store_spinor<P, R>(a.h[p], a.gstride, t, v);
 }
 
-template <int P>
-__global__ void k_unpack(PackArgs a, double2* canon) {
+template <int P, typename CT = double2>
+__global__ void k_unpack(PackArgs a, CT* canon) {
   using R = typename SpinorStore<P>::real;
   const int64_t nper = a.ns * a.nrhs;
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -642,9 +643,14 @@ __global__ void k_unpack(PackArgs a, double2* canon) {
   const int r = (int)(t - s * a.nrhs);
   cx<R> v[12];
   load_spinor<P, R>(a.h[p], a.gstride, t, v);
-  double2* dst = canon + canon_offset(a, p, s, r);
+  CT* dst = canon + canon_offset(a, p, s, r);
 #pragma unroll
-  for (int c = 0; c < 12; ++c) dst[c] = make_double2((double)v[c].re, (double)v[c].im);
+  for (int c = 0; c < 12; ++c) {
+    if constexpr (std::is_same<CT, float2>::value)
+      dst[c] = make_float2((float)v[c].re, (float)v[c].im);
+    else
+      dst[c] = make_double2((double)v[c].re, (double)v[c].im);
+  }
 }
 
 // The paired-RHS layouts (dd_pair.cuh): one thread per (site, RHS pair j),
@@ -869,6 +875,36 @@ int clover_to_dense(const dd_clover* op, double* A_dev, cudaStream_t st) {
   return DD_OK;
 }
 
+template <typename CT>
+int pack_native(const PackArgs& a, int prec, int nrhs, const CT* c, cudaStream_t st) {
+  const int64_t n = a.ns * nrhs * a.npar;
+  if (prec == P64)
+    k_pack<P64, CT><<<nblk(n, 128), 128, 0, st>>>(a, c);
+  else if (prec == PDF)
+    k_pack<PDF, CT><<<nblk(n, 128), 128, 0, st>>>(a, c);
+  else if (prec == P32)
+    k_pack<P32, CT><<<nblk(n, 128), 128, 0, st>>>(a, c);
+  else
+    k_pack<P16, CT><<<nblk(n, 128), 128, 0, st>>>(a, c);
+  DD_CUDA(cudaGetLastError());
+  return DD_OK;
+}
+
+template <typename CT>
+int unpack_native(const PackArgs& a, int prec, int nrhs, CT* c, cudaStream_t st) {
+  const int64_t n = a.ns * nrhs * a.npar;
+  if (prec == P64)
+    k_unpack<P64, CT><<<nblk(n, 128), 128, 0, st>>>(a, c);
+  else if (prec == PDF)
+    k_unpack<PDF, CT><<<nblk(n, 128), 128, 0, st>>>(a, c);
+  else if (prec == P32)
+    k_unpack<P32, CT><<<nblk(n, 128), 128, 0, st>>>(a, c);
+  else
+    k_unpack<P16, CT><<<nblk(n, 128), 128, 0, st>>>(a, c);
+  DD_CUDA(cudaGetLastError());
+  return DD_OK;
+}
+
 int pack(const dd_lattice* lat, int prec, int subset, const double* canon, const Field& f, cudaStream_t st, int t0,
          int nt) {
   PackArgs a = pack_args(lat, subset, f);
@@ -889,17 +925,20 @@ int pack(const dd_lattice* lat, int prec, int subset, const double* canon, const
     DD_CUDA(cudaGetLastError());
     return DD_OK;
   }
-  const int64_t n = a.ns * f.nrhs * a.npar;
-  if (prec == P64)
-    k_pack<P64><<<nblk(n, 128), 128, 0, st>>>(a, c);
-  else if (prec == PDF)
-    k_pack<PDF><<<nblk(n, 128), 128, 0, st>>>(a, c);
-  else if (prec == P32)
-    k_pack<P32><<<nblk(n, 128), 128, 0, st>>>(a, c);
-  else
-    k_pack<P16><<<nblk(n, 128), 128, 0, st>>>(a, c);
-  DD_CUDA(cudaGetLastError());
-  return DD_OK;
+  return pack_native(a, prec, f.nrhs, c, st);
+}
+
+// complex64 canonical fields (native layout only)
+int pack_c64(const dd_lattice* lat, int prec, int subset, const float* canon, const Field& f, cudaStream_t st,
+             int t0, int nt) {
+  if (f.paired) return fail(DD_ERR_ARG, "complex64 fields take the native layout");
+  PackArgs a = pack_args(lat, subset, f);
+  if (nt > 0) {
+    const int64_t slice = (int64_t)lat->dims[1] * lat->dims[2] * lat->dims[3];
+    a.s0 = t0 * slice / 2;
+    a.ns = nt * slice / 2;
+  }
+  return pack_native(a, prec, f.nrhs, reinterpret_cast<const float2*>(canon), st);
 }
 
 int unpack(const dd_lattice* lat, int prec, int subset, const Field& f, double* canon, cudaStream_t st, int t0,
@@ -922,17 +961,19 @@ int unpack(const dd_lattice* lat, int prec, int subset, const Field& f, double* 
     DD_CUDA(cudaGetLastError());
     return DD_OK;
   }
-  const int64_t n = a.ns * f.nrhs * a.npar;
-  if (prec == P64)
-    k_unpack<P64><<<nblk(n, 128), 128, 0, st>>>(a, c);
-  else if (prec == PDF)
-    k_unpack<PDF><<<nblk(n, 128), 128, 0, st>>>(a, c);
-  else if (prec == P32)
-    k_unpack<P32><<<nblk(n, 128), 128, 0, st>>>(a, c);
-  else
-    k_unpack<P16><<<nblk(n, 128), 128, 0, st>>>(a, c);
-  DD_CUDA(cudaGetLastError());
-  return DD_OK;
+  return unpack_native(a, prec, f.nrhs, c, st);
+}
+
+int unpack_c64(const dd_lattice* lat, int prec, int subset, const Field& f, float* canon, cudaStream_t st, int t0,
+               int nt) {
+  if (f.paired) return fail(DD_ERR_ARG, "complex64 fields take the native layout");
+  PackArgs a = pack_args(lat, subset, f);
+  if (nt > 0) {
+    const int64_t slice = (int64_t)lat->dims[1] * lat->dims[2] * lat->dims[3];
+    a.s0 = t0 * slice / 2;
+    a.ns = nt * slice / 2;
+  }
+  return unpack_native(a, prec, f.nrhs, reinterpret_cast<float2*>(canon), st);
 }
 
 }  // namespace dd

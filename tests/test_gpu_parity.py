@@ -285,3 +285,28 @@ def test_eight_real_needs_su3_links_and_valid_forms():
     with pytest.raises(dd.DDError) as e:
         g64.compress_links(8)
     assert e.value.status == dd.DD_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("prec", [dd.DD_PREC_F32, dd.DD_PREC_F16])
+def test_complex64_canonical_layouts(prec):
+    """complex64 canonical fields on the device and on the host (pipelined
+    for D and D^H): the results equal the complex128 applies of the same
+    (complex64-representable) input, rounded to complex64, bit for bit."""
+    dims = (6, 4, 2, 8)
+    U, lat, g, op = make(dims)
+    A = oracle.clover(U, dims, M0, CSW)
+    eo = oracle.EvenOdd(U, A, dims)
+    for nrhs in (1, 2):
+        psi = synthetic.spinor(dims, nrhs=nrhs).astype(np.complex64)
+        half = np.ascontiguousarray(np.stack([psi[r].reshape(-1, 12)[eo.odd] for r in range(nrhs)]))
+        for which in (dd.DD_OP_D, dd.DD_OP_DH, dd.DD_OP_DHAT, dd.DD_OP_DHAT_H, dd.DD_OP_SC):
+            x = half if which in (dd.DD_OP_DHAT, dd.DD_OP_DHAT_H) else psi
+            ref = apply(op, which, prec, x.astype(np.complex128)).astype(np.complex64)
+            xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+            od = torch.empty_like(xd)
+            op.apply(which, prec, xd, od, nrhs, dd.DD_LAYOUT_CANONICAL_C64)
+            oh = np.empty_like(x)
+            op.apply(which, prec, np.ascontiguousarray(x), oh, nrhs, dd.DD_LAYOUT_CANONICAL_HOST_C64)
+            torch.cuda.synchronize()
+            assert np.array_equal(od.cpu().numpy(), ref.reshape(od.shape))
+            assert np.array_equal(oh, ref.reshape(oh.shape))
