@@ -56,6 +56,9 @@ METRIC = "D.psi HBM GB/s (algorithmic) at 48^3x96; mixed vs FP64 FGMRES time-to-
 BYTES = {"f64": (1152, 384), "f32": (576, 192), "f16": (288, 104), "df64": (1152, 384)}
 PREC = {"f64": 1, "f32": 2, "f16": 4, "df64": 8}  # df64: FP64-accurate FP32-pair arithmetic
 FLOPS_PER_SITE = 1848  # nominal: hopping 1320 + self coupling 504 + combine 24
+# FP64-pipe instructions of the FP64 stencil per site and RHS (ncu; an FMA and
+# an addition each take one slot, so the pipe roof is half the FMA FLOP peak)
+F64_PIPE_INSTR_PER_SITE = 1153
 # link force with the clover term, one RHS, as the kernels compute it (an FMA
 # counts 2): hopping outer products 4 x 336, clover leaf derivatives 6 planes x
 # (T 720 + T' 36 + 4 leaves x 8 products x 216), su(3) projection 4 x 242
@@ -936,6 +939,8 @@ def main():
                 variants[prec]["speedup_over_f64"] = variants["f64"]["ms_per_apply"] / ms
                 out_f64 = None
             del o
+        if prec == "f64":  # FP64-pipe instructions per site (ncu, profiles/dslash_f64_48x48x48x96.md)
+            variants[prec]["fp64_pipe_frac"] = F64_PIPE_INSTR_PER_SITE * N * V / kern / (f64_peak / 2)
         rooflines[prec] = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": frac,
                            "traffic": (profile_traffic(prec) if N == 1 and dims == DIMS and
                                        (prec != "f32" or LINK_REALS_F32[0] == 12) and
