@@ -18,8 +18,9 @@ def _free_port():
 
 
 def _worker(rank, world, port, q):
+    # CPU ranks even where a GPU is present (init_dist takes NCCL on GPUs)
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
-                      LOCAL_RANK=str(rank))
+                      LOCAL_RANK=str(rank), CUDA_VISIBLE_DEVICES="")
     import bench
     r, w, local = bench.dist_env()
     tdist = bench.init_dist(w, local)
