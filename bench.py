@@ -1078,6 +1078,8 @@ def main():
         legs = [("mixed", PREC[args.solve_inner], 8, 64, 1e-6, reals32), ("fp64", PREC["f64"], 8, 64, 1e-6, reals32)]
         if args.solve_inner != "f16":
             legs.insert(1, ("mixed_f16", PREC["f16"], 8, 32, 1e-3, reals32))
+            # the same with the CG vectors in FP16 (DD_PRECOND_CGNR16)
+            legs.insert(2, ("mixed_f16_cg16", PREC["f16"], 8, 32, 1e-3, reals32))
         if args.solve_inner == "f32" and "f32_link8" in variants:
             legs.insert(1, ("mixed_link8", PREC["f32"], 8, 64, 1e-6, 8))
         if "df64" in variants:  # the FP64-accuracy solve with the FP32-pair stencil (FP64 vectors)
@@ -1089,8 +1091,9 @@ def main():
                 gauge.compress_links(reals)
             barrier(tdist)
             w0 = time.time()
+            pc = dd.DD_PRECOND_CGNR16 if name.endswith("_cg16") else dd.DD_PRECOND_CGNR
             status, st = op.solve(b, x, 1, tol=1e-10, inner_prec=inner, restart=restart, max_restarts=100,
-                                  max_outer=20, precond=dd.DD_PRECOND_CGNR, precond_iters=cg, inner_tol=tol_in)
+                                  max_outer=20, precond=pc, precond_iters=cg, inner_tol=tol_in)
             w1 = time.time()
             clocks.window(w0, w1)
             if reals != reals32:
@@ -1104,7 +1107,8 @@ def main():
                            "inner_prec": {1: "f64", 2: "f32", 4: "f16 links/clover, f32 vectors",
                                           8: "f64 accuracy in FP32-pair arithmetic, f64 vectors"}[inner],
                            "f32_link_reals": reals,
-                           "method": f"even-odd FGMRES({restart}), M_j = {cg} CG steps on Dhat^H Dhat, "
+                           "method": f"even-odd FGMRES({restart}), M_j = {cg} CG steps on Dhat^H Dhat"
+                                     f"{' (FP16 CG vectors)' if name.endswith('_cg16') else ''}, "
                                      f"inner tolerance {tol_in:g}, FP64 refinement"}
         d = (sols["mixed"] - sols["fp64"]).norm().item() / sols["fp64"].norm().item()
         solve["mixed_vs_fp64_solution_rel_diff"] = d
@@ -1113,6 +1117,10 @@ def main():
             solve["mixed_f16_vs_fp64_solution_rel_diff"] = \
                 (sols["mixed_f16"] - sols["fp64"]).norm().item() / sols["fp64"].norm().item()
             solve["speedup_mixed_f16_over_fp64"] = solve["fp64"]["seconds"] / solve["mixed_f16"]["seconds"]
+        if "mixed_f16_cg16" in solve:
+            solve["mixed_f16_cg16_vs_fp64_solution_rel_diff"] = \
+                (sols["mixed_f16_cg16"] - sols["fp64"]).norm().item() / sols["fp64"].norm().item()
+            solve["speedup_mixed_f16_cg16_over_fp64"] = solve["fp64"]["seconds"] / solve["mixed_f16_cg16"]["seconds"]
         if "df64" in solve:
             solve["df64_vs_fp64_solution_rel_diff"] = \
                 (sols["df64"] - sols["fp64"]).norm().item() / sols["fp64"].norm().item()

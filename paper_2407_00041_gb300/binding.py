@@ -21,6 +21,7 @@ DD_LAYOUT_CANONICAL, DD_LAYOUT_CANONICAL_HOST, DD_LAYOUT_NATIVE, DD_LAYOUT_NATIV
 DD_LAYOUT_CANONICAL_C64, DD_LAYOUT_CANONICAL_HOST_C64 = 4, 5  # complex64 canonical fields
 
 DD_PRECOND_NONE, DD_PRECOND_NORMAL, DD_PRECOND_CGNR, DD_PRECOND_SAP, DD_PRECOND_AMG = 0, 1, 2, 3, 4
+DD_PRECOND_CGNR16 = 5  # CGNR with FP16-stored CG vectors (inner_prec F16)
 PREC = {"f64": DD_PREC_F64, "f32": DD_PREC_F32, "f16": DD_PREC_F16, "df64": DD_PREC_DF64}
 OPS = {"D": DD_OP_D, "DH": DD_OP_DH, "DHAT": DD_OP_DHAT, "DHAT_H": DD_OP_DHAT_H, "SC": DD_OP_SC}
 

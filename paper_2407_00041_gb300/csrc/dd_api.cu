@@ -542,8 +542,10 @@ int dd_solve(dd_clover* op, const dd_solve_params* params, const void* b, void* 
   if (!op || !params || !b || !x || nrhs < 1) return fail(DD_ERR_ARG, "null argument or nrhs < 1");
   if (layout != DD_LAYOUT_CANONICAL && layout != DD_LAYOUT_CANONICAL_HOST)
     return fail(DD_ERR_ARG, "dd_solve takes canonical fields");
-  if (params->precond < DD_PRECOND_NONE || params->precond > DD_PRECOND_AMG)
+  if (params->precond < DD_PRECOND_NONE || params->precond > DD_PRECOND_CGNR16)
     return fail(DD_ERR_ARG, "unknown preconditioner");
+  if (params->precond == DD_PRECOND_CGNR16 && params->inner_prec != DD_PREC_F16)
+    return fail(DD_ERR_UNSUPPORTED, "DD_PRECOND_CGNR16 takes inner precision F16");
   if (!valid_apply_prec(params->inner_prec)) return fail(DD_ERR_ARG, "bad inner precision");
   if (params->inner_prec == DD_PREC_DF64 && (params->precond == DD_PRECOND_SAP || params->precond == DD_PRECOND_AMG))
     return fail(DD_ERR_UNSUPPORTED, "SAP and AMG take inner precision F64, F32 or F16");
@@ -557,7 +559,7 @@ int dd_solve(dd_clover* op, const dd_solve_params* params, const void* b, void* 
     DD_TRY(sap_check_blocks(op->lat, params->sap_block, params->inner_prec == DD_PREC_F64 ? P64 : P32));
     if (params->sap_cycles < 1 || params->sap_mr_steps < 1) return fail(DD_ERR_ARG, "SAP cycles and MR steps >= 1");
   }
-  if (params->precond == DD_PRECOND_CGNR && params->precond_iters < 1)
+  if ((params->precond == DD_PRECOND_CGNR || params->precond == DD_PRECOND_CGNR16) && params->precond_iters < 1)
     return fail(DD_ERR_ARG, "precond_iters must be >= 1");
   if (!(params->tol > 0) || params->max_restarts < 1 || params->max_outer < 0)
     return fail(DD_ERR_ARG, "bad solver parameters");

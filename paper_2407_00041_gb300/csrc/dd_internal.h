@@ -182,6 +182,15 @@ int pack(const dd_lattice* lat, int prec, int subset, const double* canon, const
          int t0 = 0, int nt = 0);
 int unpack(const dd_lattice* lat, int prec, int subset, const Field& f, double* canon, cudaStream_t st, int t0 = 0,
            int nt = 0);
+// Vector kernels of the CG preconditioner with FP16-stored vectors
+// (dd_cg16.cu): npar = 1 (odd half) or 2 (full field); x32 FP32, the others
+// FP16 native fields.
+int cg16_convert(const Field& in32, const Field& out16, int64_t Vh, int npar, cudaStream_t st);
+int cg16_norm(const Field& x16, int64_t Vh, int npar, double2* partials, double2* out, cudaStream_t st);
+int cg16_r(const Field& r16, const Field& w16, int64_t Vh, int npar, const double2* g, const double2* n,
+           cudaStream_t st);
+int cg16_xp(const Field& x32, const Field& p16, const Field* z16, int64_t Vh, int npar, const double2* g,
+            const double2* n, const double2* gn, cudaStream_t st);
 // the same for complex64 canonical fields [N][V][12] (native layout only)
 int pack_c64(const dd_lattice* lat, int prec, int subset, const float* canon, const Field& f, cudaStream_t st,
              int t0 = 0, int nt = 0);

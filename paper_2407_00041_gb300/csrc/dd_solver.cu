@@ -25,6 +25,9 @@
 //           method on the normal equations A^H A z = A^H v_j (from z = 0), run
 //           on the device with step sizes kept in device memory; Z_m is stored
 //           and x += Z_m y.
+//   cgnr16  the same CG with its vectors r, A^H r, p and A p stored in FP16
+//           (per-site scales) and read by the FP16 stencil; z accumulates in
+//           FP32 (FP16 links and blocks, inner_prec F16)
 //   amg     the flexible two-level preconditioner of dd_amg.cu (coarse-grid
 //           correction and SAP post-smoothing), for the even-odd system
 //           applied to (0, v_j) like sap;
@@ -83,6 +86,9 @@ struct Inner {
   int verbose = 0;
   int gs_passes = 1;    // classical Gram-Schmidt passes per Arnoldi step
   DevBuf basis, w, rvec, tmp, red, partials, coef, zt, ut, zbasis, cr, cz, cp, cgs;
+  // cgnr16: the CG vectors in FP16 (r, A^H r, p, A p) and Dhat's intermediate
+  DevBuf cr16, cz16, cp16, cw16, tmp16;
+  size_t vbytes16 = 0;
   // sap: block extents, cycles and MR steps per block solve; full fields v, z, r
   int sap_block[4] = {4, 4, 4, 4};
   int sap_cycles = 1, sap_mr = 4;
@@ -161,6 +167,16 @@ struct Inner {
         npart_len = nb + blas_reduce_scratch((int)std::min<int64_t>(nb, INT32_MAX), 1);
         DD_TRY(npart.ensure((size_t)npart_len * sizeof(double2)));
       }
+    }
+    if (mode == DD_PRECOND_CGNR16) {
+      DD_TRY(zbasis.ensure(vbytes * m));
+      DD_TRY(cgs.ensure((size_t)3 * N * sizeof(double2)));
+      vbytes16 = field_bytes(lat, P16, eo ? 1 : 0, N);
+      DD_TRY(cr16.ensure(vbytes16));
+      DD_TRY(cz16.ensure(vbytes16));
+      DD_TRY(cp16.ensure(vbytes16));
+      DD_TRY(cw16.ensure(vbytes16));
+      if (eo) DD_TRY(tmp16.ensure(field_bytes(lat, P16, 2, N)));
     }
     if (eo) DD_TRY(tmp.ensure(field_bytes(lat, pv, 2, N)));
     const size_t nred = (size_t)(2 * (m + 1) + 1) * N;
@@ -244,6 +260,45 @@ struct Inner {
     DD_CUDA(cudaMemcpyAsync(V.h[1].base, v, hb, cudaMemcpyDeviceToDevice, st));
     DD_TRY(amg_apply(amg, V, Z, st));
     DD_CUDA(cudaMemcpyAsync(z, Z.h[1].base, hb, cudaMemcpyDeviceToDevice, st));
+    return DD_OK;
+  }
+
+  // the cgnr16 preconditioner: the same CG with r, A^H r, p and A p stored in
+  // FP16 (dd_cg16.cu), z accumulated in FP32
+  Field fv16(void* p) { return field_view(op->lat, P16, eo ? 1 : 0, p, N); }
+  int apply16(void* in, void* out, bool dagger, cudaStream_t st) {
+    ++applies;
+    if (eo) return op_Dhat(op, pg, P16, dagger, fv16(in), fv16(out), field_view(op->lat, P16, 2, tmp16.ptr, N), st);
+    return op_D(op, pg, P16, dagger, fv16(in), fv16(out), st);
+  }
+  int norm16(void* x, double2* out, cudaStream_t st) {
+    return cg16_norm(fv16(x), op->lat->Vh, eo ? 1 : 2, (double2*)partials.ptr, out, st);
+  }
+  int cgnr16(const void* v, void* z, cudaStream_t st) {
+    double2* g0 = reinterpret_cast<double2*>(cgs.ptr);
+    double2* g1 = g0 + N;
+    double2* nw = g0 + 2 * N;
+    double2* g[2] = {g0, g1};
+    const int npar = eo ? 1 : 2;
+    const int64_t Vh = op->lat->Vh;
+    DD_CUDA(cudaMemsetAsync(z, 0, vbytes, st));
+    DD_TRY(cg16_convert(fv(const_cast<void*>(v)), fv16(cr16.ptr), Vh, npar, st));
+    DD_TRY(apply16(cr16.ptr, cz16.ptr, true, st));  // A^H r
+    DD_TRY(norm16(cz16.ptr, g[0], st));
+    DD_CUDA(cudaMemcpyAsync(cp16.ptr, cz16.ptr, vbytes16, cudaMemcpyDeviceToDevice, st));
+    const Field Z = fv(z), P = fv16(cp16.ptr), W = fv16(cw16.ptr), Rr = fv16(cr16.ptr), Zz = fv16(cz16.ptr);
+    for (int i = 0; i < cg_iters; ++i) {
+      DD_TRY(apply16(cp16.ptr, cw16.ptr, false, st));  // w = A p
+      DD_TRY(norm16(cw16.ptr, nw, st));
+      if (i + 1 == cg_iters) {
+        DD_TRY(cg16_xp(Z, P, nullptr, Vh, npar, g[i & 1], nw, nullptr, st));
+        break;
+      }
+      DD_TRY(cg16_r(Rr, W, Vh, npar, g[i & 1], nw, st));
+      DD_TRY(apply16(cr16.ptr, cz16.ptr, true, st));  // z' = A^H r
+      DD_TRY(norm16(cz16.ptr, g[(i + 1) & 1], st));
+      DD_TRY(cg16_xp(Z, P, &Zz, Vh, npar, g[i & 1], nw, g[(i + 1) & 1], st));
+    }
     return DD_OK;
   }
 
@@ -360,9 +415,12 @@ struct Inner {
       int jmax = 0;
       for (int j = 0; j < m; ++j) {
         ++steps;
-        if (mode == DD_PRECOND_CGNR || mode == DD_PRECOND_SAP || mode == DD_PRECOND_AMG) {
+        if (mode == DD_PRECOND_CGNR || mode == DD_PRECOND_CGNR16 || mode == DD_PRECOND_SAP ||
+            mode == DD_PRECOND_AMG) {
           if (mode == DD_PRECOND_CGNR)
             DD_TRY(cgnr(V(j), Zb(j), st));  // z_j = M_j^{-1} v_j
+          else if (mode == DD_PRECOND_CGNR16)
+            DD_TRY(cgnr16(V(j), Zb(j), st));
           else if (mode == DD_PRECOND_SAP)
             DD_TRY(sap(V(j), Zb(j), st));
           else
@@ -460,7 +518,10 @@ struct Inner {
       DD_CUDA(cudaMemcpyAsync(dcoef, hc, (size_t)jmax * N * sizeof(double2), cudaMemcpyHostToDevice, st));
       VecList vs;
       for (int i = 0; i < jmax; ++i)
-        vs.p[i] = (mode == DD_PRECOND_CGNR || mode == DD_PRECOND_SAP || mode == DD_PRECOND_AMG) ? Zb(i) : V(i);
+        vs.p[i] = (mode == DD_PRECOND_CGNR || mode == DD_PRECOND_CGNR16 || mode == DD_PRECOND_SAP ||
+                   mode == DD_PRECOND_AMG)
+                      ? Zb(i)
+                      : V(i);
       if (!normal) {
         DD_TRY(axpys(vs, jmax, dcoef, 1.0, e, st));  // e += Z_m y (Z_m = V_m without preconditioner)
       } else {

@@ -130,3 +130,34 @@ def test_nan_rhs_is_rejected(sys44):
     with pytest.raises(dd.DDError) as e:
         op.solve(bt, x, 1)
     assert e.value.status == dd.DD_ERR_ARG
+
+
+@pytest.mark.parametrize("even_odd", [1, 0])
+@pytest.mark.parametrize("nrhs", [1, 2])
+def test_solve_with_fp16_cg_vectors(even_odd, nrhs):
+    """DD_PRECOND_CGNR16: the CG preconditioner with its vectors in FP16
+    (per-site scales) inside the FP16-inner solve reaches 1e-10, certified by
+    the oracle, with FP64 refinement."""
+    dims = (8, 8, 4, 4)
+    U, lat, g, op = make(dims)
+    A = oracle.clover(U, dims, M0, CSW)
+    b = synthetic.spinor(dims, nrhs=nrhs)
+    bt = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bt)
+    status, st = op.solve(bt, x, nrhs, tol=1e-10, inner_prec=dd.DD_PREC_F16, even_odd=even_odd, restart=8,
+                          precond=dd.DD_PRECOND_CGNR16, precond_iters=16, inner_tol=1e-3)
+    assert status == 0, st
+    assert st["converged"] == 1 and st["true_residual"] < 1e-10
+    xn = x.cpu().numpy()
+    for r in range(nrhs):
+        assert oracle_residual(U, A, dims, b[r], xn[r]) < 1e-10
+
+
+def test_fp16_cg_vectors_need_fp16_inner():
+    dims = (4, 4, 4, 4)
+    U, lat, g, op = make(dims)
+    b = torch.from_numpy(synthetic.spinor(dims, nrhs=1)).cuda()
+    x = torch.zeros_like(b)
+    with pytest.raises(dd.DDError) as e:
+        op.solve(b, x, 1, inner_prec=dd.DD_PREC_F32, precond=dd.DD_PRECOND_CGNR16)
+    assert e.value.status == dd.DD_ERR_UNSUPPORTED
