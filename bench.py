@@ -574,9 +574,12 @@ def extra_measurements(dd, torch, stream, op48, psi48, V48, tdist, clocks, alu_p
 
 # ---------------------------------------------------------------- 64^3 x 128, 8 RHS
 def run_solve_only(args):
-    """One mixed-precision solve of the 48^3 x 96 workload (the bench's
-    `solve.mixed` leg: even-odd FGMRES(8), M_j = 64 CG steps on Dhat^H Dhat,
-    FP32 inner, FP64 refinement), for profiling its kernels."""
+    """One mixed-precision solve of the 48^3 x 96 workload, for profiling its
+    kernels: the bench's `solve.mixed` leg (even-odd FGMRES(8), M_j = 64 CG
+    steps on Dhat^H Dhat, inner tolerance 1e-6, FP32 inner, FP64 refinement),
+    or with --solve-inner f16 its `solve.mixed_f16` leg (32 CG steps, inner
+    tolerance 1e-3), and with --solve-precond cgnr16 the same with the CG
+    vectors in FP16 (`solve.mixed_f16_cg16`)."""
     import torch
     import synthetic
     import paper_2407_00041_gb300 as dd
@@ -586,8 +589,10 @@ def run_solve_only(args):
     op = dd.Operator(gauge, M0, CSW)
     b = torch.from_numpy(synthetic.spinor(dims, nrhs=1)).cuda()
     x = torch.zeros_like(b)
+    cg, tol_in = (64, 1e-6) if args.solve_inner == "f32" else (32, 1e-3)
+    pc = dd.DD_PRECOND_CGNR16 if args.solve_precond == "cgnr16" else dd.DD_PRECOND_CGNR
     status, st = op.solve(b, x, 1, tol=1e-10, inner_prec=PREC[args.solve_inner], restart=8, max_restarts=100,
-                          max_outer=20, precond=dd.DD_PRECOND_CGNR, precond_iters=64)
+                          max_outer=20, precond=pc, precond_iters=cg, inner_tol=tol_in)
     print(json.dumps({"metric": "time to ||b-Dx|| < 1e-10 ||b||, 48^3x96, mixed precision", "value": st["seconds"],
                       "unit": "s", "higher_is_better": False, "status": status, "stats": st}), flush=True)
     return 0 if status == dd.DD_OK else 1
@@ -821,6 +826,8 @@ def main():
                     help="field layout of the timed FP32 / FP16 D psi (paired: even --nrhs; profiling)")
     ap.add_argument("--solve-64x128-8rhs", action="store_true", help="run the 64^3x128, 8-RHS memory-fitted solve instead")
     ap.add_argument("--solve-only", action="store_true", help="run only the mixed 48^3x96 solve (for profiling)")
+    ap.add_argument("--solve-precond", default="cgnr", choices=["cgnr", "cgnr16"],
+                    help="--solve-only: CG vectors of the preconditioner in FP32 (cgnr) or FP16 (cgnr16, FP16 inner)")
     ap.add_argument("--rhs-batch", type=int, default=2, help="64^3x128 solve: right-hand sides per batch")
     ap.add_argument("--restart", type=int, default=8, help="64^3x128 solve: FGMRES restart length")
     ap.add_argument("--cg-steps", type=int, default=64, help="64^3x128 solve: CG steps per preconditioner application")

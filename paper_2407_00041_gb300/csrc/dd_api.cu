@@ -465,8 +465,9 @@ int dd_apply(dd_clover* op, int which, int prec, const void* in, void* out, int 
   Field fin, fout;
   const double* cin = nullptr;
   // canonical fields with an even RHS count go through the paired-RHS stencil
-  // (bit-identical to the RHS-blocked one; DD_RHS_BLOCK=1 keeps one thread
-  // per site and RHS, DD_STAGE=1 the row-staged stencil)
+  // (FP32: bit-identical to the RHS-blocked one; FP16: half2 colour products;
+  // DD_RHS_BLOCK=1 keeps one thread per site and RHS, DD_STAGE=1 the
+  // row-staged stencil)
   const int paired = layout == DD_LAYOUT_NATIVE_PAIRED ||
                      (layout != DD_LAYOUT_NATIVE && !c64 && nrhs % 2 == 0 && which != DD_OP_SC &&
                       (prec == DD_PREC_F32 || prec == DD_PREC_F16) && rhs_block_limit() >= 2 && !stage_opted_in());

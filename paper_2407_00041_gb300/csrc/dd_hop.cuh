@@ -607,7 +607,9 @@ __device__ __forceinline__ float hop_epilogue(const HopArgs& a, int p, int s, in
   store_spinor<POUT, R, true>(a.out[p], a.gstride, i, res);
   float n2 = 0.f;
   if constexpr (NORM) {
-    static_assert(POUT == P32, "the fused norm reads the FP32 result");
+    // the FP32 result before it is stored (for FP16 output: before the
+    // rounding to halves, within 2^-11 of the stored vector's norm)
+    static_assert(POUT == P32 || POUT == P16, "the fused norm reads an FP32 result");
 #pragma unroll
     for (int c = 0; c < 12; ++c) {
       n2 = __fmaf_rn((float)res[c].re, (float)res[c].re, n2);
@@ -1022,7 +1024,7 @@ cudaError_t launch_hop(const HopArgs& args, bool dagger, int epi, cudaStream_t s
   }
 }
 
-// One right-hand side, EPI_D, out written in FP32: the stencil plus
+// One right-hand side, EPI_D, out written in FP32 or FP16: the stencil plus
 // norm_out[0] = (|out|^2, 0), reduced in a fixed order (deterministic).
 // `partials` holds at least hop_norm_blocks(launch sites) complex doubles
 // plus the reduction's own scratch (blas_reduce_scratch(blocks, 1)).

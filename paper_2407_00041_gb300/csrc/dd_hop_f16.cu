@@ -2,4 +2,5 @@
 #include "dd_hop.cuh"
 namespace dd {
 DD_INSTANTIATE_HOP(P16, P16, P16)
+DD_INSTANTIATE_HOP_NORM(P16, P16, P16)
 }  // namespace dd

@@ -4,9 +4,19 @@
 //
 // The operator is the one of dd_hop.cuh (the hopping sum of Eq. 1.13 formed
 // through the two-spin projection that the back-substitution after
-// Algorithm 3 uses, plus the self coupling of Eq. 2.5): every arithmetic step
-// of one right-hand side is the same FP32 operation, in the same order, as in
-// the RHS-blocked kernel k_hop_rb, so results are bit-identical to it.
+// Algorithm 3 uses, plus the self coupling of Eq. 2.5).  With FP32 vectors
+// every arithmetic step of one right-hand side is the same FP32 operation, in
+// the same order, as in the RHS-blocked kernel k_hop_rb, so results are
+// bit-identical to it.  With FP16 vectors (and FP16 links) each hop works in
+// half2 arithmetic on the stored values, the two lanes of a half2 being the
+// two right-hand sides: spin projection by add.f16x2 and the colour product
+// by fma.rn.f16x2 (FP16 sums of the six products of a component), then
+// widened once per component for the reconstruction; the sum over the hops,
+// the site scales and the self coupling stay FP32.  A packed FP32x2 FMA
+// occupies the FMA pipe for two cycles and an FP16x2 FMA for one, so this
+// halves the pipe time of the colour products, which bound the FP16-storage
+// kernel at many right-hand sides; the FP16 sums add about 3e-4 relative
+// error per product to the 2.4e-4 of the FP16 storage itself.
 // What changes is the data layout, which puts the same component of two
 // right-hand sides side by side so that one packed instruction serves both:
 //
@@ -32,8 +42,8 @@ namespace dd {
 // with (u0, u1) the upper and (l0, l1) the lower spin pair and
 //   B_T = I, B_Z = -i sigma_3, B_Y = -i sigma_2, B_X = -i sigma_1
 // (-i z = (z.im, -z.re), i z = (-z.im, z.re)).
-template <int MU, int T>
-__device__ __forceinline__ void proj2(cx2 u0, cx2 u1, cx2 l0, cx2 l1, cx2& h0, cx2& h1) {
+template <int MU, int T, typename C>
+__device__ __forceinline__ void proj2(C u0, C u1, C l0, C l1, C& h0, C& h1) {
   if constexpr (MU == 0) {  // b0 = l0, b1 = l1
     if constexpr (T > 0) {
       h0.re = add2(u0.re, l0.re), h0.im = add2(u0.im, l0.im);
@@ -145,6 +155,73 @@ __device__ __forceinline__ void hop_pair(cx2 acc[12], const cx2 psi[12], const c
   }
 }
 
+// The same hop for FP16 pairs: projection and colour product in half2
+// arithmetic on the stored values (u: the nine FP16 link elements, re in the
+// low and im in the high half), reconstruction in FP32 with sg the boundary
+// sign times the two site scales.
+template <int MU, int T, bool ADJ>
+__device__ __forceinline__ void hop_pair_h(cx2 acc[12], const hx2 psi[12], const __half2 u[9], float2 sg) {
+  hx2 h0[3], h1[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) proj2<MU, T>(psi[c], psi[3 + c], psi[6 + c], psi[9 + c], h0[c], h1[c]);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    hx2 q0, q1;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const __half2 w = ADJ ? u[3 * b + a] : u[3 * a + b];
+      const __half2 wr = __low2half2(w), wi = __high2half2(w);
+      // U:   re += w.re h.re - w.im h.im,  im += w.re h.im + w.im h.re
+      // U^H: re += w.re h.re + w.im h.im,  im += w.re h.im - w.im h.re
+      const __half2 wi_im = ADJ ? wi : __hneg2(wi);
+      const __half2 wi_re = ADJ ? __hneg2(wi) : wi;
+      if (b == 0) {
+        q0.re = __hmul2(wr, h0[b].re);
+        q1.re = __hmul2(wr, h1[b].re);
+        q0.im = __hmul2(wr, h0[b].im);
+        q1.im = __hmul2(wr, h1[b].im);
+      } else {
+        q0.re = __hfma2(wr, h0[b].re, q0.re);
+        q1.re = __hfma2(wr, h1[b].re, q1.re);
+        q0.im = __hfma2(wr, h0[b].im, q0.im);
+        q1.im = __hfma2(wr, h1[b].im, q1.im);
+      }
+      q0.re = __hfma2(wi_im, h0[b].im, q0.re);
+      q1.re = __hfma2(wi_im, h1[b].im, q1.re);
+      q0.im = __hfma2(wi_re, h0[b].re, q0.im);
+      q1.im = __hfma2(wi_re, h1[b].re, q1.im);
+    }
+    cx2 g0, g1;
+    g0.re = __half22float2(q0.re);
+    g0.im = __half22float2(q0.im);
+    g1.re = __half22float2(q1.re);
+    g1.im = __half22float2(q1.im);
+    recon2<MU, T>(acc, a, g0, g1, sg);
+  }
+}
+
+// One hop from the stored neighbour pair i of field f with link mu of site ls
+// of Ubase: FP16 vectors take the half2 hop above, FP32 vectors widen the
+// links to FP32 and use the packed FP32x2 hop.
+template <int PG, int PV, int MU, int T, bool ADJ>
+__device__ __forceinline__ void pair_hop_from(cx2 acc[12], const HalfField& f, int64_t gstride, int64_t i,
+                                              const void* Ubase, int64_t ls, int64_t Vh, float sg) {
+  if constexpr (PV == P16) {
+    static_assert(PG == P16, "FP16 paired vectors come with FP16 links");
+    __half2 u[9];
+    load_link_h(Ubase, ls, Vh, MU, u);
+    hx2 psi[12];
+    const float2 ps = load_pair_h(f, gstride, i, psi);
+    hop_pair_h<MU, T, ADJ>(acc, psi, u, mul2(bc2(sg), ps));
+  } else {
+    cx<float> u[9];
+    load_link<PG, float>(Ubase, ls, Vh, MU, u);
+    cx2 psi[12];
+    load_pair<PV>(f, gstride, i, psi);
+    hop_pair<MU, T, ADJ>(acc, psi, u, bc2(sg));
+  }
+}
+
 // out (+)= M x for the two Hermitian 6x6 blocks of site s (storage as in
 // block_apply_g), on a pair; the same operation order as block_apply_g.
 template <int PG, bool ADD>
@@ -233,16 +310,14 @@ __device__ __forceinline__ void hop_thread_pair(const HopArgs& a, int64_t tid) {
   }
   const float hop_scale = EPI == EPI_D ? beta : 1.f;
 
-#define DD_PAIR_HOP(MU, FWD)                                                                        \
-  {                                                                                                 \
-    const int nl = FWD ? nb_fwd(a.g, sc, MU) : nb_bwd(a.g, sc, MU);                                 \
-    float sg = hop_scale;                                                                           \
-    if (MU == 0 && sc.c[0] == (FWD ? a.g.n[0] - 1 : 0)) sg = sg * a.g.t_bc;                         \
-    cx<float> u[9];                                                                                 \
-    load_link<PG, float>(FWD ? a.U[p] : a.U[q], FWD ? (int64_t)s : (int64_t)(nl >> 1), Vh, MU, u);  \
-    cx2 psi[12];                                                                                    \
-    const float2 ps = load_pair<PV>(a.in[q], a.gstride, (int64_t)(nl >> 1) * NP + j, psi);          \
-    hop_pair<MU, FWD ? TF : TB, !FWD>(acc, psi, u, PV == P16 ? mul2(bc2(sg), ps) : bc2(sg));        \
+#define DD_PAIR_HOP(MU, FWD)                                                                          \
+  {                                                                                                   \
+    const int nl = FWD ? nb_fwd(a.g, sc, MU) : nb_bwd(a.g, sc, MU);                                   \
+    float sg = hop_scale;                                                                             \
+    if (MU == 0 && sc.c[0] == (FWD ? a.g.n[0] - 1 : 0)) sg = sg * a.g.t_bc;                           \
+    pair_hop_from<PG, PV, MU, FWD ? TF : TB, !FWD>(acc, a.in[q], a.gstride, (int64_t)(nl >> 1) * NP + j, \
+                                                   FWD ? a.U[p] : a.U[q],                             \
+                                                   FWD ? (int64_t)s : (int64_t)(nl >> 1), Vh, sg);    \
   }
   DD_PAIR_HOP(0, true)
   DD_PAIR_HOP(0, false)

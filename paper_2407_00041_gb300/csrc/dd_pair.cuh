@@ -28,6 +28,16 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 
+// one complex component of two right-hand sides as stored in the paired FP16
+// layout: re and im as half2 (RHS a in .x, RHS b in .y), in units of each
+// RHS's site scale
+struct hx2 {
+  __half2 re, im;
+};
+
+__device__ __forceinline__ __half2 add2(__half2 a, __half2 b) { return __hadd2(a, b); }
+__device__ __forceinline__ __half2 sub2(__half2 a, __half2 b) { return __hsub2(a, b); }
+
 // ---- paired field access ----
 // Load the 12 components of RHS pair index i (= site * NP + j); FP16 values
 // come without their site scales, which are returned (FP32: (1, 1)).
@@ -56,6 +66,21 @@ __device__ __forceinline__ float2 load_pair(const HalfField& f, int64_t gstride,
     // scales of RHS 2j and 2j + 1 of the site: floats site * N + 2j = 2 i
     return __ldg(reinterpret_cast<const float2*>(f.scale) + i);
   }
+}
+
+// The 12 stored FP16 components of RHS pair index i without widening; returns
+// the site scales of the two RHS.
+__device__ __forceinline__ float2 load_pair_h(const HalfField& f, int64_t gstride, int64_t i, hx2 v[12]) {
+  const uint4* b = reinterpret_cast<const uint4*>(f.base) + i;
+#pragma unroll
+  for (int g = 0; g < 6; ++g) {
+    const uint4 t = __ldg(b + g * gstride);
+    v[2 * g].re = *reinterpret_cast<const __half2*>(&t.x);
+    v[2 * g].im = *reinterpret_cast<const __half2*>(&t.y);
+    v[2 * g + 1].re = *reinterpret_cast<const __half2*>(&t.z);
+    v[2 * g + 1].im = *reinterpret_cast<const __half2*>(&t.w);
+  }
+  return __ldg(reinterpret_cast<const float2*>(f.scale) + i);
 }
 
 // Store RHS pair index i; FP16 divides each RHS by its own site scale

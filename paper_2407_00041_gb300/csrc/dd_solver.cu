@@ -94,8 +94,9 @@ struct Inner {
   int sap_cycles = 1, sap_mr = 4;
   DevBuf sv, sz, sr;
   dd_amg* amg = nullptr;  // DD_PRECOND_AMG
-  // CG norms formed by the second stencil launch of Dhat (one RHS, FP32
-  // vectors; DD_FUSED_NORM=0 turns it off): per-block partial sums
+  // CG norms formed by the second stencil launch of Dhat (one RHS; FP32
+  // vectors, or the FP16 CG vectors of cgnr16; DD_FUSED_NORM=0 turns it
+  // off): per-block partial sums
   bool fuse_norm = false;
   DevBuf npart;
   int64_t npart_len = 0;
@@ -131,6 +132,7 @@ struct Inner {
   int init(const dd_clover* op_, int pg_, int pv_, bool eo_, int N_, int m_, int mode_) {
     mode = mode_;
     normal = mode == DD_PRECOND_NORMAL;
+    fuse_norm = false;
     op = op_;
     pg = pg_;
     pv = pv_;
@@ -177,6 +179,13 @@ struct Inner {
       DD_TRY(cp16.ensure(vbytes16));
       DD_TRY(cw16.ensure(vbytes16));
       if (eo) DD_TRY(tmp16.ensure(field_bytes(lat, P16, 2, N)));
+      const char* fe = getenv("DD_FUSED_NORM");
+      fuse_norm = eo && dhat_norm_fused(pg, P16, N) && !(fe && atoi(fe) == 0);
+      if (fuse_norm) {
+        const int64_t nb = hop_norm_blocks(lat->Vh);
+        npart_len = nb + blas_reduce_scratch((int)std::min<int64_t>(nb, INT32_MAX), 1);
+        DD_TRY(npart.ensure((size_t)npart_len * sizeof(double2)));
+      }
     }
     if (eo) DD_TRY(tmp.ensure(field_bytes(lat, pv, 2, N)));
     const size_t nred = (size_t)(2 * (m + 1) + 1) * N;
@@ -274,6 +283,18 @@ struct Inner {
   int norm16(void* x, double2* out, cudaStream_t st) {
     return cg16_norm(fv16(x), op->lat->Vh, eo ? 1 : 2, (double2*)partials.ptr, out, st);
   }
+  // out = A in and nrm[0] = (|out|^2, 0): the norm formed by the stencil
+  // launch (of the FP32 result before its rounding to FP16) where supported,
+  // else a pass over the stored FP16 vector
+  int apply16_norm(void* in, void* out, bool dagger, double2* nrm, cudaStream_t st) {
+    if (!fuse_norm) {
+      DD_TRY(apply16(in, out, dagger, st));
+      return norm16(out, nrm, st);
+    }
+    ++applies;
+    return op_Dhat_norm(op, pg, P16, dagger, fv16(in), fv16(out), field_view(op->lat, P16, 2, tmp16.ptr, N), nrm,
+                        (double2*)npart.ptr, npart_len, st);
+  }
   int cgnr16(const void* v, void* z, cudaStream_t st) {
     double2* g0 = reinterpret_cast<double2*>(cgs.ptr);
     double2* g1 = g0 + N;
@@ -283,20 +304,17 @@ struct Inner {
     const int64_t Vh = op->lat->Vh;
     DD_CUDA(cudaMemsetAsync(z, 0, vbytes, st));
     DD_TRY(cg16_convert(fv(const_cast<void*>(v)), fv16(cr16.ptr), Vh, npar, st));
-    DD_TRY(apply16(cr16.ptr, cz16.ptr, true, st));  // A^H r
-    DD_TRY(norm16(cz16.ptr, g[0], st));
+    DD_TRY(apply16_norm(cr16.ptr, cz16.ptr, true, g[0], st));  // A^H r
     DD_CUDA(cudaMemcpyAsync(cp16.ptr, cz16.ptr, vbytes16, cudaMemcpyDeviceToDevice, st));
     const Field Z = fv(z), P = fv16(cp16.ptr), W = fv16(cw16.ptr), Rr = fv16(cr16.ptr), Zz = fv16(cz16.ptr);
     for (int i = 0; i < cg_iters; ++i) {
-      DD_TRY(apply16(cp16.ptr, cw16.ptr, false, st));  // w = A p
-      DD_TRY(norm16(cw16.ptr, nw, st));
+      DD_TRY(apply16_norm(cp16.ptr, cw16.ptr, false, nw, st));  // w = A p
       if (i + 1 == cg_iters) {
         DD_TRY(cg16_xp(Z, P, nullptr, Vh, npar, g[i & 1], nw, nullptr, st));
         break;
       }
       DD_TRY(cg16_r(Rr, W, Vh, npar, g[i & 1], nw, st));
-      DD_TRY(apply16(cr16.ptr, cz16.ptr, true, st));  // z' = A^H r
-      DD_TRY(norm16(cz16.ptr, g[(i + 1) & 1], st));
+      DD_TRY(apply16_norm(cr16.ptr, cz16.ptr, true, g[(i + 1) & 1], st));  // z' = A^H r
       DD_TRY(cg16_xp(Z, P, &Zz, Vh, npar, g[i & 1], nw, g[(i + 1) & 1], st));
     }
     return DD_OK;

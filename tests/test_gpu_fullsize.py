@@ -101,8 +101,9 @@ def test_32c4_twelve_rhs_sampled():
 
 def test_32c4_twelve_rhs_paired_layout_sampled():
     """The bench's multi-RHS launch: the paired-RHS layout at 32^4 x 12 (FP32,
-    FP16 storage), D and D^H, sampled against the oracle, and bit-identical to
-    the native-layout apply on every site."""
+    FP16 storage), D and D^H, sampled against the oracle; FP32 bit-identical
+    to the native-layout apply on every site, FP16 (half2 colour products)
+    within 2e-3 of it for every RHS."""
     dims = (32, 32, 32, 32)
     n = 12
     U = synthetic.gauge(dims, eps=EPS)
@@ -122,7 +123,11 @@ def test_32c4_twelve_rhs_paired_layout_sampled():
             op.apply(which, prec, xi, xo, n, dd.DD_LAYOUT_NATIVE_PAIRED)
             op.unpack_paired(prec, 0, xo, out, n)
             ref = _native_apply(op, prec, psi_dev, n, which)
-            assert torch.equal(out, ref)
+            if prec == dd.DD_PREC_F32:
+                assert torch.equal(out, ref)
+            else:
+                for r in range(n):
+                    assert ((out[r] - ref[r]).norm() / ref[r].norm()).item() < 2e-3
             del ref
             if which == dd.DD_OP_D:
                 _check_sites(U, dims, psi, out, sites, (0, 5, n - 1), TOL[prec])

@@ -1,12 +1,15 @@
-"""The paired-RHS layout and its packed FP32x2 stencil, through the C ABI.
+"""The paired-RHS layout and its packed stencil, through the C ABI.
 
-Every arithmetic step of one right-hand side in the paired stencil is the FP32
-operation of the native-layout RHS-blocked stencil, in the same order, so the
-two layouts must give bit-identical results (compared here exactly, after
-unpacking both to the canonical layout); the oracle checks the values to the
-stated tolerances (FP32 1e-6, FP16 storage 5e-3).  Shapes span several
-128-thread tiles with a ragged tail (6x4x2x8: 192 sites per parity; with 6
-pairs per site, 1152 threads per parity)."""
+With FP32 vectors every arithmetic step of one right-hand side in the paired
+stencil is the FP32 operation of the native-layout RHS-blocked stencil, in the
+same order, so the two layouts must give bit-identical results (compared here
+exactly, after unpacking both to the canonical layout).  With FP16 vectors the
+paired stencil forms the spin projection and colour products in half2
+arithmetic (FP16 sums) where the native one widens to FP32 first: the two
+agree to PAIR16_TOL.  The oracle checks the values to the stated tolerances
+(FP32 1e-6, FP16 storage 5e-3).  Shapes span several 128-thread tiles with a
+ragged tail (6x4x2x8: 192 sites per parity; with 6 pairs per site, 1152
+threads per parity)."""
 import numpy as np
 import pytest
 import torch
@@ -21,6 +24,10 @@ pytestmark = pytest.mark.gpu
 SHAPES = [(4, 4, 4, 4), (6, 4, 2, 8), (2, 2, 2, 2), (8, 6, 4, 2)]
 PRECS = [dd.DD_PREC_F32, dd.DD_PREC_F16]
 OPS = [dd.DD_OP_D, dd.DD_OP_DH, dd.DD_OP_DHAT, dd.DD_OP_DHAT_H]
+# FP16 paired (half2 colour products) against FP16 native (FP32 colour
+# products), relative L2 distance: both round their output to FP16 (2.4e-4),
+# the FP16 sums add about 3e-4 per colour product
+PAIR16_TOL = 2e-3
 
 
 @pytest.fixture(scope="module", params=SHAPES, ids=lambda d: "x".join(map(str, d)))
@@ -52,7 +59,7 @@ def _run(op, which, prec, psi_dev, nrhs, paired):
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("nrhs", [2, 4, 12])
 @pytest.mark.parametrize("which", OPS)
-def test_paired_equals_native_bit_for_bit(system, prec, nrhs, which):
+def test_paired_equals_native(system, prec, nrhs, which):
     dims, U, A, op, _ = system
     full = synthetic.spinor(dims, nrhs=nrhs).reshape(nrhs, -1, 12)
     if which in (dd.DD_OP_DHAT, dd.DD_OP_DHAT_H):
@@ -64,7 +71,12 @@ def test_paired_equals_native_bit_for_bit(system, prec, nrhs, which):
     got = _run(op, which, prec, x, nrhs, True)
     ref = _run(op, which, prec, x, nrhs, False)
     assert np.isfinite(got).all()
-    assert np.array_equal(got, ref)
+    if prec == dd.DD_PREC_F32:
+        assert np.array_equal(got, ref)
+    else:
+        for r in range(nrhs):
+            assert rel(got[r], ref[r]) < PAIR16_TOL
+        assert not np.array_equal(got, ref)  # the half2 path ran
 
 
 @pytest.mark.parametrize("prec", PRECS)

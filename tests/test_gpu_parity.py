@@ -101,7 +101,10 @@ def test_pack_unpack_roundtrip(system, prec):
 
 
 def test_native_layout_matches_canonical(system):
-    """The native-layout entry point (what the bench times) gives the same result."""
+    """The native-layout entry point (what the bench times) gives the same
+    result as the canonical one, which takes the paired stencil for two RHS:
+    exactly in FP64 and FP32, and within 2e-3 for FP16 storage (the paired FP16
+    stencil forms its colour products in half2 arithmetic)."""
     dims, U, A, op, _ = system
     nrhs = 2
     psi = torch.from_numpy(synthetic.spinor(dims, nrhs=nrhs)).cuda()
@@ -114,7 +117,7 @@ def test_native_layout_matches_canonical(system):
         op.unpack(prec, 0, nat_out, out, nrhs)
         torch.cuda.synchronize()
         ref = apply(op, dd.DD_OP_D, prec, psi.cpu().numpy())
-        assert rel(out.cpu().numpy(), ref) == 0.0
+        assert rel(out.cpu().numpy(), ref) <= (2e-3 if prec == dd.DD_PREC_F16 else 0.0)
 
 
 def test_periodic_time_boundary():
@@ -287,11 +290,30 @@ def test_eight_real_needs_su3_links_and_valid_forms():
     assert e.value.status == dd.DD_ERR_UNSUPPORTED
 
 
+def native_apply(op, which, prec, psi):
+    """The apply on the native layout (pack, apply, unpack)."""
+    nrhs = psi.shape[0]
+    subset = 1 if which in (dd.DD_OP_DHAT, dd.DD_OP_DHAT_H) else 0
+    x = torch.from_numpy(np.ascontiguousarray(psi)).cuda()
+    nb = op.field_bytes(prec, subset, nrhs)
+    fi = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    fo = torch.empty_like(fi)
+    op.pack(prec, subset, x, fi, nrhs)
+    op.apply(which, prec, fi, fo, nrhs, dd.DD_LAYOUT_NATIVE)
+    out = torch.empty_like(x)
+    op.unpack(prec, subset, fo, out, nrhs)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
 @pytest.mark.parametrize("prec", [dd.DD_PREC_F32, dd.DD_PREC_F16])
 def test_complex64_canonical_layouts(prec):
     """complex64 canonical fields on the device and on the host (pipelined
-    for D and D^H): the results equal the complex128 applies of the same
-    (complex64-representable) input, rounded to complex64, bit for bit."""
+    for D and D^H): the results equal the native-layout applies of the same
+    (complex64-representable) input, rounded to complex64, bit for bit.
+    (complex128 canonical fields with an even RHS count take the paired
+    stencil, whose FP16 form rounds differently, so the reference is the
+    native layout.)"""
     dims = (6, 4, 2, 8)
     U, lat, g, op = make(dims)
     A = oracle.clover(U, dims, M0, CSW)
@@ -301,7 +323,7 @@ def test_complex64_canonical_layouts(prec):
         half = np.ascontiguousarray(np.stack([psi[r].reshape(-1, 12)[eo.odd] for r in range(nrhs)]))
         for which in (dd.DD_OP_D, dd.DD_OP_DH, dd.DD_OP_DHAT, dd.DD_OP_DHAT_H, dd.DD_OP_SC):
             x = half if which in (dd.DD_OP_DHAT, dd.DD_OP_DHAT_H) else psi
-            ref = apply(op, which, prec, x.astype(np.complex128)).astype(np.complex64)
+            ref = native_apply(op, which, prec, x.astype(np.complex128)).astype(np.complex64)
             xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
             od = torch.empty_like(xd)
             op.apply(which, prec, xd, od, nrhs, dd.DD_LAYOUT_CANONICAL_C64)

@@ -54,18 +54,21 @@ def test_solve_to_1e10(sys44, inner, even_odd, precond):
         assert st["outer_iterations"] >= 2  # refinement did the last digits
 
 
-@pytest.mark.parametrize("inner", [dd.DD_PREC_F32, dd.DD_PREC_F16])
-def test_cg_norms_fused_into_the_stencil(inner, monkeypatch):
+@pytest.mark.parametrize("inner,precond", [(dd.DD_PREC_F32, dd.DD_PRECOND_CGNR), (dd.DD_PREC_F16, dd.DD_PRECOND_CGNR),
+                                           (dd.DD_PREC_F16, dd.DD_PRECOND_CGNR16)])
+def test_cg_norms_fused_into_the_stencil(inner, precond, monkeypatch):
     """The CG preconditioner takes |Dhat p|^2 and |Dhat^H r|^2 from the
     second stencil launch of Dhat (per-block partial sums; 1080 odd sites =
     eight blocks of 128 and a ragged block of 56) and, with DD_FUSED_NORM=0,
-    from a separate reduction of the stored vector.  Both solves meet the
-    tolerance against the oracle and agree."""
+    from a separate reduction of the stored vector (with FP16 CG vectors:
+    the fused norm is that of the FP32 result before its rounding to FP16).
+    Both solves meet the tolerance against the oracle, agree, and take the
+    same number of Arnoldi steps to within one."""
     dims = (10, 6, 6, 6)
     U, lat, g, op = make(dims)
     A = oracle.clover(U, dims, M0, CSW)
     b = synthetic.spinor(dims, nrhs=1)
-    xs = []
+    xs, steps = [], []
     for fused in (True, False):
         if fused:
             monkeypatch.delenv("DD_FUSED_NORM", raising=False)
@@ -73,13 +76,15 @@ def test_cg_norms_fused_into_the_stencil(inner, monkeypatch):
             monkeypatch.setenv("DD_FUSED_NORM", "0")
         bt = torch.from_numpy(b).cuda()
         x = torch.zeros_like(bt)
-        status, st = op.solve(bt, x, 1, tol=1e-10, inner_prec=inner, restart=8, precond=dd.DD_PRECOND_CGNR,
+        status, st = op.solve(bt, x, 1, tol=1e-10, inner_prec=inner, restart=8, precond=precond,
                               precond_iters=16)
         assert status == 0 and st["true_residual"] < 1e-10, st
         xn = x.cpu().numpy()[0]
         assert oracle_residual(U, A, dims, b[0], xn) < 1e-10
         xs.append(xn)
+        steps.append(st["inner_iterations"])
     assert rel(xs[0], xs[1]) < 1e-8
+    assert abs(steps[0] - steps[1]) <= 1, steps
 
 
 def test_multi_rhs_solve(sys44):
