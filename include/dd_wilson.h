@@ -37,7 +37,7 @@
  *   DD_LAYOUT_NATIVE_PAIRED   device memory in the paired-RHS layout (FP32 and
  *                             FP16 only, nrhs even; same bytes as native):
  *                             the same component of RHS 2j and 2j + 1 side by
- *                             side, for the packed FP32x2 stencil.
+ *                             side, for the packed paired stencil.
  *   For the full-lattice operators (DD_OP_D, DD_OP_DH) nsites = V.  For the
  *   even-odd operators (DD_OP_DHAT, DD_OP_DHAT_H) fields live on odd sites
  *   only: nsites = V/2, in increasing lexicographic order.
@@ -309,11 +309,15 @@ int dd_unpack_paired(const dd_clover* op, int prec, int subset, const void* pair
  * to and from the native layout inside the call, using workspace owned by the
  * operator handle (allocated on first use and kept).
  * DD_LAYOUT_NATIVE_PAIRED (DD_OP_D, DD_OP_DH, DD_OP_DHAT, DD_OP_DHAT_H with
- * prec DD_PREC_F32 or DD_PREC_F16 and an even nrhs) runs the packed FP32x2
- * stencil: one thread per output site and pair of right-hand sides, each
- * arithmetic step the FP32 operation of the native-layout kernel (results are
- * bit-identical); DD_ERR_ARG for an odd nrhs or another precision,
- * DD_ERR_UNSUPPORTED for DD_OP_SC.
+ * prec DD_PREC_F32 or DD_PREC_F16 and an even nrhs) runs the packed paired
+ * stencil: one thread per output site and pair of right-hand sides.  FP32:
+ * each arithmetic step the FP32 operation of the native-layout kernel
+ * (results are bit-identical).  FP16: spin projection and colour products in
+ * half2 arithmetic on the stored values (FP16 sums; results within about
+ * 1e-3 relative of the native-layout kernel, which widens to FP32 first), the
+ * hop sums and the self coupling in FP32.  Canonical layouts with an even
+ * nrhs take this stencil too.  DD_ERR_ARG for an odd nrhs or another
+ * precision, DD_ERR_UNSUPPORTED for DD_OP_SC.
  * Enqueued on `stream`; DD_LAYOUT_CANONICAL_HOST synchronises it.
  */
 int dd_apply(dd_clover* op, int which, int prec, const void* in, void* out, int nrhs, int layout, void* stream);
