@@ -1091,6 +1091,12 @@ def main():
             legs.insert(1, ("mixed_link8", PREC["f32"], 8, 64, 1e-6, 8))
         if "df64" in variants:  # the FP64-accuracy solve with the FP32-pair stencil (FP64 vectors)
             legs.append(("df64", PREC["df64"], 8, 64, 1e-6, reals32))
+            # the refinement's operator applications (r = b - D x, preparation,
+            # reconstruction) in FP32-pair arithmetic on the FP64 iterate
+            legs.append(("mixed_dfref", PREC[args.solve_inner], 8, 64 if args.solve_inner == "f32" else 32,
+                         1e-6 if args.solve_inner == "f32" else 1e-3, reals32))
+            if args.solve_inner != "f16":
+                legs.append(("mixed_f16_cg16_dfref", PREC["f16"], 8, 32, 1e-3, reals32))
         for name, inner, restart, cg, tol_in, reals in legs:
             x = torch.zeros_like(b)
             log(f"solve {name}")
@@ -1098,9 +1104,10 @@ def main():
                 gauge.compress_links(reals)
             barrier(tdist)
             w0 = time.time()
-            pc = dd.DD_PRECOND_CGNR16 if name.endswith("_cg16") else dd.DD_PRECOND_CGNR
+            pc = dd.DD_PRECOND_CGNR16 if "_cg16" in name else dd.DD_PRECOND_CGNR
+            rp = dd.DD_PREC_DF64 if name.endswith("_dfref") else dd.DD_PREC_F64
             status, st = op.solve(b, x, 1, tol=1e-10, inner_prec=inner, restart=restart, max_restarts=100,
-                                  max_outer=20, precond=pc, precond_iters=cg, inner_tol=tol_in)
+                                  max_outer=20, precond=pc, precond_iters=cg, inner_tol=tol_in, refine_prec=rp)
             w1 = time.time()
             clocks.window(w0, w1)
             if reals != reals32:
@@ -1115,8 +1122,10 @@ def main():
                                           8: "f64 accuracy in FP32-pair arithmetic, f64 vectors"}[inner],
                            "f32_link_reals": reals,
                            "method": f"even-odd FGMRES({restart}), M_j = {cg} CG steps on Dhat^H Dhat"
-                                     f"{' (FP16 CG vectors)' if name.endswith('_cg16') else ''}, "
-                                     f"inner tolerance {tol_in:g}, FP64 refinement"}
+                                     f"{' (FP16 CG vectors)' if '_cg16' in name else ''}, "
+                                     f"inner tolerance {tol_in:g}, "
+                                     + ("refinement on FP64 vectors with the FP32-pair (FP64-accurate) stencil"
+                                        if rp == dd.DD_PREC_DF64 else "FP64 refinement")}
         d = (sols["mixed"] - sols["fp64"]).norm().item() / sols["fp64"].norm().item()
         solve["mixed_vs_fp64_solution_rel_diff"] = d
         solve["speedup_mixed_over_fp64"] = solve["fp64"]["seconds"] / solve["mixed"]["seconds"]
@@ -1132,6 +1141,11 @@ def main():
             solve["df64_vs_fp64_solution_rel_diff"] = \
                 (sols["df64"] - sols["fp64"]).norm().item() / sols["fp64"].norm().item()
             solve["speedup_df64_over_fp64"] = solve["fp64"]["seconds"] / solve["df64"]["seconds"]
+        for name in ("mixed_dfref", "mixed_f16_cg16_dfref"):
+            if name in solve:
+                solve[f"{name}_vs_fp64_solution_rel_diff"] = \
+                    (sols[name] - sols["fp64"]).norm().item() / sols["fp64"].norm().item()
+                solve[f"speedup_{name}_over_fp64"] = solve["fp64"]["seconds"] / solve[name]["seconds"]
         if "mixed_link8" in solve:
             solve["mixed_link8_vs_fp64_solution_rel_diff"] = \
                 (sols["mixed_link8"] - sols["fp64"]).norm().item() / sols["fp64"].norm().item()

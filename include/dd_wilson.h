@@ -348,6 +348,12 @@ typedef struct {
   dd_amg* amg;         /* DD_PRECOND_AMG: the two-level preconditioner (dd_amg_create); its fine
                           precision must be that of the inner vectors (F64 for inner_prec F64,
                           F32 otherwise) and it must belong to the same operator */
+  int refine_prec;     /* arithmetic of the refinement's operator applications on the FP64
+                          iterate (r = b - D x, the even-odd preparation and reconstruction):
+                          DD_PREC_F64 (default) or DD_PREC_DF64 (the FP32-pair stencil on the
+                          same FP64 vectors, about 1e-14 relative, needs the DF64 copies in the
+                          gauge and operator handles; DD_ERR_UNSUPPORTED without them).  The
+                          reported true_residual is computed the same way. */
 } dd_solve_params;
 
 #define DD_PRECOND_NONE 0

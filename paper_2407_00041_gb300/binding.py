@@ -39,7 +39,7 @@ class SolveParams(ctypes.Structure):
                 ("even_odd", ctypes.c_int), ("verbose", ctypes.c_int), ("precond", ctypes.c_int),
                 ("gs_passes", ctypes.c_int), ("rhs_batch", ctypes.c_int), ("precond_iters", ctypes.c_int),
                 ("sap_block", ctypes.c_int * 4), ("sap_cycles", ctypes.c_int), ("sap_mr_steps", ctypes.c_int),
-                ("amg", ctypes.c_void_p)]
+                ("amg", ctypes.c_void_p), ("refine_prec", ctypes.c_int)]
 
 
 class AmgParams(ctypes.Structure):

@@ -536,6 +536,7 @@ void dd_solve_params_default(dd_solve_params* p) {
   p->sap_cycles = 1;
   p->sap_mr_steps = 4;
   p->amg = nullptr;
+  p->refine_prec = DD_PREC_F64;
 }
 
 int dd_solve(dd_clover* op, const dd_solve_params* params, const void* b, void* x, int nrhs, int layout,
@@ -565,6 +566,11 @@ int dd_solve(dd_clover* op, const dd_solve_params* params, const void* b, void* 
   if (!(params->tol > 0) || params->max_restarts < 1 || params->max_outer < 0)
     return fail(DD_ERR_ARG, "bad solver parameters");
   if (params->rhs_batch < 0) return fail(DD_ERR_ARG, "rhs_batch must be >= 0");
+  if (params->refine_prec != DD_PREC_F64 && params->refine_prec != DD_PREC_DF64)
+    return fail(DD_ERR_ARG, "refine_prec: DD_PREC_F64 or DD_PREC_DF64");
+  if (params->refine_prec == DD_PREC_DF64 &&
+      (!op->gauge->links[prec_index(PDF)].ptr || !op->clov[prec_index(PDF)].ptr))
+    return fail(DD_ERR_UNSUPPORTED, "refine_prec DD_PREC_DF64: no FP32-pair copies in the gauge/operator handles");
   cudaStream_t st = as_stream(stream);
   if (params->even_odd)
     return solve_schur(op, params, (const double*)b, (double*)x, nrhs, layout == DD_LAYOUT_CANONICAL_HOST, st, stats);

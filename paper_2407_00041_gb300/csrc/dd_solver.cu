@@ -607,6 +607,8 @@ int schur_batch(dd_clover* op, const dd_solve_params* prm, const double* b_in, d
   const dd_lattice* lat = op->lat;
   const int pin = prm->inner_prec;
   const int pv = (pin == P64 || pin == PDF) ? P64 : P32;  // FP32 pairs work on FP64 vectors
+  // the refinement's operator on the FP64 vectors: FP64 or FP32-pair arithmetic
+  const int rp = prm->refine_prec == DD_PREC_DF64 ? PDF : P64;
   const size_t h64 = field_bytes(lat, P64, 1, nb);
   const size_t canon = (size_t)lat->V * 12 * 16 * nb;
   DevBuf be, bo, bh, xo, ro, te, stage, red, partials, fv, ev;
@@ -645,7 +647,7 @@ int schur_batch(dd_clover* op, const dd_solve_params* prm, const double* b_in, d
     bnorm[r] = std::sqrt(n_e[r] + n_o[r]);
     if (!std::isfinite(bnorm[r])) return fail(DD_ERR_ARG, "right-hand side contains NaN or Inf");
   }
-  DD_TRY(op_prepare(op, P64, P64, B, BH, TE, st));
+  DD_TRY(op_prepare(op, rp, P64, B, BH, TE, st));
   if (pv == P32) {
     DD_TRY(fv.alloc(field_bytes(lat, P32, 1, nb)));
     DD_TRY(ev.alloc(field_bytes(lat, P32, 1, nb)));
@@ -656,7 +658,7 @@ int schur_batch(dd_clover* op, const dd_solve_params* prm, const double* b_in, d
   bool ok = false;
   double worst = 0.0;
   for (int outer = 0;; ++outer) {
-    DD_TRY(op_dhat_residual(op, P64, P64, BH, XO, RO, TE, st));
+    DD_TRY(op_dhat_residual(op, rp, P64, BH, XO, RO, TE, st));
     ++s.applies_fp64;
     DD_TRY(half_norms64(lat, ro.ptr, nb, (double2*)red.ptr, (double2*)partials.ptr, hbuf, rn, st));
     bool reached = true;
@@ -669,13 +671,13 @@ int schur_batch(dd_clover* op, const dd_solve_params* prm, const double* b_in, d
       X.nrhs = nb;
       X.h[0] = TE.h[0];
       X.h[1] = XO.h[1];
-      DD_TRY(op_reconstruct(op, P64, P64, B, X, st));
+      DD_TRY(op_reconstruct(op, rp, P64, B, X, st));
       Field R;
       R.prec = P64;
       R.nrhs = nb;
       R.h[0] = field_view(lat, P64, 2, bh.ptr, nb).h[0];
       R.h[1] = RO.h[1];
-      DD_TRY(op_residual(op, P64, P64, B, X, R, st));
+      DD_TRY(op_residual(op, rp, P64, B, X, R, st));
       ++s.applies_fp64;
       DD_TRY(half_norms64(lat, bh.ptr, nb, (double2*)red.ptr, (double2*)partials.ptr, hbuf, n_e, st));
       DD_TRY(half_norms64(lat, ro.ptr, nb, (double2*)red.ptr, (double2*)partials.ptr, hbuf, n_o, st));
@@ -700,7 +702,7 @@ int schur_batch(dd_clover* op, const dd_solve_params* prm, const double* b_in, d
         break;
       }
       target *= 0.1;  // the Schur residual understated the full one: tighten and go on
-      DD_TRY(op_prepare(op, P64, P64, B, BH, TE, st));  // bh held r_e
+      DD_TRY(op_prepare(op, rp, P64, B, BH, TE, st));  // bh held r_e
       continue;
     }
     if (prm->verbose) {
@@ -785,6 +787,7 @@ int solve(dd_clover* op, const dd_solve_params* prm, const double* b_canon, doub
   const int pin = prm->inner_prec;
   const int pv = (pin == P64 || pin == PDF) ? P64 : P32;  // FP32 pairs work on FP64 vectors
   const int pg = pin;
+  const int rp = prm->refine_prec == DD_PREC_DF64 ? PDF : P64;  // the refinement operator
   if (prec_index(pin) < 0) return fail(DD_ERR_ARG, "bad inner precision");
   if (!op->clov[prec_index(pg)].ptr || !op->gauge->links[prec_index(pg)].ptr)
     return fail(DD_ERR_UNSUPPORTED, "inner precision not created in the handles");
@@ -824,7 +827,7 @@ int solve(dd_clover* op, const dd_solve_params* prm, const double* b_canon, doub
   dd_stats s{};
   int status = DD_ERR_NOT_CONVERGED;
   for (int outer = 0;; ++outer) {
-    DD_TRY(op_residual(op, P64, P64, B, X, Rr, st));  // r = b - D x in FP64
+    DD_TRY(op_residual(op, rp, P64, B, X, Rr, st));  // r = b - D x in FP64
     ++s.applies_fp64;
     DD_TRY(dot_norms64(lat, r64.ptr, N, (double2*)red.ptr, (double2*)partials.ptr, hbuf, rnorm, st));
     double worst = 0.0;

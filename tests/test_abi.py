@@ -42,6 +42,7 @@ def test_host_side_argument_checks_without_gpu():
     p = binding.SolveParams()
     lib.dd_solve_params_default(ctypes.byref(p))
     assert p.tol == 1e-10 and p.restart == 30 and p.even_odd == 1
+    assert p.refine_prec == binding.DD_PREC_F64 and p.amg is None
 
 
 def test_no_cpu_fallback_in_package():

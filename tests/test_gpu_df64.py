@@ -143,3 +143,46 @@ def test_solve_with_pair_inner(even_odd, precond):
         if inner == dd.DD_PREC_DF64:
             assert st["outer_iterations"] == 1
     assert rel(xs[dd.DD_PREC_DF64], xs[dd.DD_PREC_F64]) < 1e-8
+
+
+@pytest.mark.parametrize("inner,precond,even_odd", [(dd.DD_PREC_F32, dd.DD_PRECOND_CGNR, 1),
+                                                    (dd.DD_PREC_F16, dd.DD_PRECOND_CGNR16, 1),
+                                                    (dd.DD_PREC_F32, dd.DD_PRECOND_CGNR, 0)])
+def test_refinement_in_pair_arithmetic(inner, precond, even_odd):
+    """refine_prec = DD_PREC_DF64: the refinement's r = b - D x (and the
+    even-odd preparation and reconstruction) in FP32-pair arithmetic on the
+    FP64 iterate.  The solve reaches 1e-10, certified by the oracle, and
+    agrees with the FP64-refined solve."""
+    dims = (8, 8, 4, 4)
+    U, lat, g, op = make_df(dims)
+    A = oracle.clover(U, dims, M0, CSW)
+    b = synthetic.spinor(dims, nrhs=1)
+    bt = torch.from_numpy(b).cuda()
+    xs = {}
+    for rp in (dd.DD_PREC_F64, dd.DD_PREC_DF64):
+        x = torch.zeros_like(bt)
+        status, st = op.solve(bt, x, 1, tol=1e-10, inner_prec=inner, even_odd=even_odd, restart=8, precond=precond,
+                              precond_iters=16, inner_tol=1e-3 if inner == dd.DD_PREC_F16 else 1e-6,
+                              refine_prec=rp)
+        assert status == 0, st
+        assert st["converged"] == 1 and st["true_residual"] < 1e-10
+        xs[rp] = x.cpu().numpy()[0]
+        res = b[0].reshape(-1, 12) - oracle.apply_D(U, A, xs[rp].reshape(-1, 12), dims)
+        assert np.linalg.norm(res) / np.linalg.norm(b[0]) < 1e-10
+    assert rel(xs[dd.DD_PREC_DF64], xs[dd.DD_PREC_F64]) < 1e-8
+
+
+def test_refinement_precision_checks():
+    dims = (4, 4, 4, 4)
+    U = synthetic.gauge(dims)
+    lat = dd.Lattice(dims, -1)
+    g = dd.Gauge(lat, U)  # no FP32-pair copies
+    op = dd.Operator(g, M0, CSW)
+    b = torch.from_numpy(synthetic.spinor(dims, nrhs=1)).cuda()
+    x = torch.zeros_like(b)
+    with pytest.raises(dd.DDError) as e:
+        op.solve(b, x, 1, refine_prec=dd.DD_PREC_DF64)
+    assert e.value.status == dd.DD_ERR_UNSUPPORTED
+    with pytest.raises(dd.DDError) as e:
+        op.solve(b, x, 1, refine_prec=dd.DD_PREC_F32)
+    assert e.value.status == dd.DD_ERR_ARG
