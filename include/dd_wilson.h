@@ -86,7 +86,7 @@
  *   DD_ZBLOCK=d         Z-slab depth of the traversal (a divisor of nZ; 0 =
  *                       nZ); default: the deepest slab within 30 MB.
  *   DD_HOST_CHUNKS=c    time-slice chunks of the pipelined host-buffer
- *                       apply (default 24).
+ *                       apply (default 48, at most nT).
  *   DD_FUSED_NORM=0     the CG preconditioner of dd_solve takes its norms
  *                       from separate reductions instead of the stencil
  *                       launch (read at each dd_solve).

@@ -58,7 +58,7 @@ int apply_host_pipelined(dd_clover* op, int prec, bool dagger, const void* hin, 
   const int nT = lat->dims[0];
   static const int max_chunks = [] {
     const char* e = getenv("DD_HOST_CHUNKS");  // tuning override
-    const int v = e ? atoi(e) : 24;
+    const int v = e ? atoi(e) : 48;
     return v < 2 ? 2 : v;
   }();
   const int C = nT < max_chunks ? nT : max_chunks;
