@@ -935,7 +935,8 @@ def main():
             achieved = gflops / 1e3
         variants[prec] = {"gbs": gbs, "ms_per_apply": ms, "hbm_frac": bytes_per_site(prec, N) * V / kern / 1e9 /
                           peaks["hbm_gbs"], "gflops_nominal": gflops, "bound": bound,
-                          "roof_frac": frac, "bytes_per_site": bytes_per_site(prec, N)}
+                          "roof_frac": frac, "bytes_per_site": bytes_per_site(prec, N),
+                          "ms_min": min(per) * 1e3, "ms_median": statistics.median(per) * 1e3}
         if prec in ("f64", "df64") and not paired:  # the FP32-pair result against the FP64 one
             o = torch.empty_like(psi_dev)
             op.unpack(p, 0, xout, o, N)
@@ -956,6 +957,9 @@ def main():
                            "peak_source": f"{peak_kind} MEASURED_PEAKS.json hbm_gbs" if bound == "hbm"
                            else "FMA-chain probe dd_probe_flops on this GPU (FP64 pipe)" if prec == "f64"
                            else "FMA-chain probe dd_probe_flops on this GPU (FP32 pipe)"}
+        if rooflines[prec]["traffic"]:  # DRAM bytes of the ncu capture over this run's launch time
+            rooflines[prec]["dram_gbs"] = rooflines[prec]["traffic"] / kern / 1e9
+            rooflines[prec]["dram_frac"] = rooflines[prec]["dram_gbs"] / peaks["hbm_gbs"]
         if prec == args.prec:
             traffic = (profile_traffic(prec) if N == 1 and dims == DIMS and (prec != "f32" or LINK_REALS_F32[0] == 12) and
                        (prec != "f16" or LINK_REALS_F16[0] == 12)
@@ -963,6 +967,8 @@ def main():
             head = {"value": gbs, "ms": ms, "kernel_s": kern,
                     "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": frac,
                                  "traffic": traffic,
+                                 **({"dram_gbs": traffic / kern / 1e9,
+                                     "dram_frac": traffic / kern / 1e9 / peaks["hbm_gbs"]} if traffic else {}),
                                  "peak_source": f"{peak_kind} MEASURED_PEAKS.json hbm_gbs" if bound == "hbm"
                                  else "FMA-chain probe dd_probe_flops on this GPU"}}
             # parity of the timed launch configuration on a sample of sites
