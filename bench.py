@@ -34,7 +34,6 @@ from __future__ import annotations
 
 import argparse
 import hashlib
-import glob
 import json
 import os
 import re
@@ -239,13 +238,22 @@ def time_steps(fn, steps, warmup, stream, tdist, clocks):
 
 
 # ---------------------------------------------------------------- profiles
-def kernel_source_hash():
+def kernel_source_hash(units=("dd_hop_f32.cu", "dd_hop_f16.cu")):
+    """sha256 (16 hex digits) of the sources the single-RHS FP32 and FP16
+    stencils are compiled from: their instantiation units and every local
+    header those include, transitively."""
+    csrc = os.path.join(ROOT, "paper_2407_00041_gb300", "csrc")
+    seen, todo = set(), list(units)
+    while todo:
+        f = todo.pop()
+        if f in seen or not os.path.exists(os.path.join(csrc, f)):
+            continue
+        seen.add(f)
+        with open(os.path.join(csrc, f)) as fh:
+            todo += re.findall(r'^\s*#\s*include\s+"([^"]+)"', fh.read(), flags=re.M)
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2407_00041_gb300", "csrc", "dd_hop*")) +
-                    [os.path.join(ROOT, "paper_2407_00041_gb300", "csrc", "dd_device.cuh"),
-                     os.path.join(ROOT, "paper_2407_00041_gb300", "csrc", "dd_ops.h"),
-                     os.path.join(ROOT, "paper_2407_00041_gb300", "csrc", "dd_link8.cuh")]):
-        with open(f, "rb") as fh:
+    for f in sorted(seen):
+        with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
@@ -726,6 +734,64 @@ def run_solve_64c128_8rhs(args):
     return 0 if status == 0 else 1
 
 
+def run_context_64x32(args):
+    """Context run on the lattice shape of the thesis' two-node solves
+    (64 x 32^3) at its mass m0 = -0.332, with the synthetic eps = 0.3 links
+    instead of its gauge configurations (not in this container), so the
+    numbers are not comparable to its tables.  Three solves to
+    ||b - D x|| < 1e-10 ||b||: plain FP64 GMRES(30) on the full lattice with
+    M = I (the thesis' unpreconditioned solver), the mixed FP32-inner
+    even-odd FGMRES(8) with 64 CG steps per M_j and FP64 refinement, and the
+    FP16-inner solve with FP16 CG vectors and FP32-pair refinement.  The
+    oracle recomputes the residual on the sites of two time slices."""
+    import torch
+    import oracle
+    import synthetic
+    import paper_2407_00041_gb300 as dd
+    dims = (64, 32, 32, 32)
+    m0 = -0.332
+    V = int(np.prod(dims))
+    log("64x32^3 context run: generating links")
+    U = synthetic.gauge(dims, eps=EPS)
+    b = synthetic.spinor(dims, nrhs=1)
+    lat = dd.Lattice(dims, -1)
+    precs = dd.DD_PREC_F64 | dd.DD_PREC_F32 | dd.DD_PREC_F16 | dd.DD_PREC_DF64
+    gauge = dd.Gauge(lat, U, precisions=precs)
+    op = dd.Operator(gauge, m0, CSW, precisions=precs)
+    bt = torch.from_numpy(b).cuda()
+    per = dims[1] * dims[2] * dims[3]
+    sites = np.arange(2 * per, dtype=np.int64)
+    A = oracle.clover_sites(U, dims, m0, CSW, sites)
+    legs = [("gmres_fp64_no_precond", dict(inner_prec=dd.DD_PREC_F64, even_odd=0, restart=30, max_outer=1,
+                                           precond=dd.DD_PRECOND_NONE, max_restarts=100)),
+            ("mixed", dict(inner_prec=dd.DD_PREC_F32, restart=8, precond=dd.DD_PRECOND_CGNR, precond_iters=64,
+                           inner_tol=1e-6, max_outer=20, max_restarts=100)),
+            ("mixed_f16_cg16_dfref", dict(inner_prec=dd.DD_PREC_F16, restart=8, precond=dd.DD_PRECOND_CGNR16,
+                                          precond_iters=32, inner_tol=1e-3, max_outer=20, max_restarts=100,
+                                          refine_prec=dd.DD_PREC_DF64))]
+    out = {}
+    for name, kw in legs:
+        x = torch.zeros_like(bt)
+        log(f"context solve {name}")
+        status, st = op.solve(bt, x, 1, tol=1e-10, **kw)
+        xn = x.cpu().numpy()[0]
+        Dx = oracle.apply_D_sites(U, A, xn, dims, sites)
+        bb = b[0].reshape(-1, 12)[sites]
+        out[name] = {"seconds": st["seconds"], "status": status, "true_residual": st["true_residual"],
+                     "applies": st["applies_inner"] + st["applies_fp64"], "outer": st["outer_iterations"],
+                     "oracle_residual_two_slices": float(np.linalg.norm(bb - Dx) / np.linalg.norm(bb))}
+        log(f"  {name}: {out[name]}")
+    line = {"metric": "context: time to ||b-Dx|| < 1e-10 ||b|| on the 64x32^3 lattice shape at m0=-0.332",
+            "unit": "s", "n_gpus": 1, "higher_is_better": False, "data": "synthetic (eps=0.3 links)",
+            "config": {"workload": "64x32^3 Wilson-clover, eps=0.3 synthetic links, m0=-0.332, c_sw=1.0, "
+                                   "antiperiodic T, 1 Gaussian RHS",
+                       "note": "the thesis' two-node lattice shape and mass on synthetic links: "
+                               "not comparable to its gauge-configuration solves"},
+            "solves": out}
+    print(json.dumps(line), flush=True)
+    return 0 if all(v["status"] == 0 for k, v in out.items() if k != "gmres_fp64_no_precond") else 1
+
+
 def run_cpu_solve(args):
     """The CPU oracle solving D x = b to ||b - D x|| < 1e-10 ||b|| in FP64 on
     the host cores, with the settings of the GPU solves: the oracle's
@@ -835,6 +901,8 @@ def main():
     ap.add_argument("--cpu-dhat-only", action="store_true",
                     help="with --cpu-solve: time one oracle Dhat and Dhat^H application instead of the full solve")
     ap.add_argument("--amg-solve", action="store_true", help="run the 48^3x96 solve with the AMG preconditioner")
+    ap.add_argument("--context-64x32", action="store_true",
+                    help="context solves on the 64x32^3 lattice shape at m0=-0.332 (synthetic links)")
     ap.add_argument("--amg-settings", default="8:4.4.4.4:1:2,16:4.4.4.4:1:4",
                     help="AMG settings n_tv:aT.aZ.aY.aX:init_sap:setup_iters, comma separated")
     ap.add_argument("--amg-rhs", type=int, default=1, help="right-hand sides of the AMG solves")
@@ -845,6 +913,8 @@ def main():
         return run_solve_64c128_8rhs(args)
     if args.solve_only:
         return run_solve_only(args)
+    if args.context_64x32:
+        return run_context_64x32(args)
     if args.cpu_solve:
         return run_cpu_solve(args)
     if args.amg_solve:
