@@ -332,3 +332,33 @@ def test_complex64_canonical_layouts(prec):
             torch.cuda.synchronize()
             assert np.array_equal(od.cpu().numpy(), ref.reshape(od.shape))
             assert np.array_equal(oh, ref.reshape(oh.shape))
+
+
+def test_singular_self_coupling_and_empty_calls():
+    """Degenerate cases.  Unit links make the clover term of Eq. 1.11 vanish
+    (every plaquette is 1), so each 6x6 block is (4 + m0) 1: at m0 = -4 the
+    blocks are zero and creating the operator reports DD_ERR_SINGULAR (no
+    inverse is formed); at m0 = -3.5 the self coupling is 0.5 psi exactly.
+    An apply or solve of zero right-hand sides is an argument error."""
+    dims = (4, 4, 2, 2)
+    V = int(np.prod(dims))
+    U = np.zeros((V, 4, 3, 3), dtype=np.complex128)
+    U[:] = np.eye(3)
+    lat = dd.Lattice(dims, -1)
+    g = dd.Gauge(lat, U)
+    with pytest.raises(dd.DDError) as e:
+        dd.Operator(g, -4.0, CSW)
+    assert e.value.status == dd.DD_ERR_SINGULAR
+    op = dd.Operator(g, -3.5, CSW)
+    psi = synthetic.spinor(dims, nrhs=1)
+    for prec in (dd.DD_PREC_F64, dd.DD_PREC_F32):
+        sc = apply(op, dd.DD_OP_SC, prec, psi)
+        assert rel(sc, 0.5 * psi.reshape(sc.shape)) < TOL[prec]
+    x = torch.from_numpy(psi).cuda()
+    y = torch.empty_like(x)
+    with pytest.raises(dd.DDError) as e:
+        op.apply(dd.DD_OP_D, dd.DD_PREC_F64, x, y, 0)
+    assert e.value.status == dd.DD_ERR_ARG
+    with pytest.raises(dd.DDError) as e:
+        op.solve(x, y, 0)
+    assert e.value.status == dd.DD_ERR_ARG

@@ -65,7 +65,9 @@ def test_staged_D_and_DH_match_oracle(dims, nrhs, prec):
 
 def test_staged_matches_unstaged_kernels(tmp_path):
     """Same inputs through the staged kernel and (DD_STAGE=0) the per-thread
-    load kernels: FP32 results agree to rounding."""
+    load kernels: FP32 results agree to rounding.  The FP16 D^H with 12 RHS
+    runs the paired stencil (half2 colour products) without DD_STAGE and the
+    native one with it, so those two agree to the FP16 paired tolerance."""
     script = tmp_path / "run.py"
     script.write_text(
         "import sys, numpy as np\n"
@@ -89,7 +91,7 @@ def test_staged_matches_unstaged_kernels(tmp_path):
         res[flag] = np.load(path)
     for k in res["1"].files:
         a, b = res["1"][k], res["0"][k]
-        assert rel(a, b) < 1e-6, k
+        assert rel(a, b) < (2e-3 if k == "arr_1" else 1e-6), k
 
 
 def test_expired_wait_is_reported_and_context_stays_usable(tmp_path):
