@@ -336,12 +336,15 @@ typedef struct {
   int precond;         /* preconditioner M_j of Algorithm 2: DD_PRECOND_NONE (M = I),
                           DD_PRECOND_NORMAL (M^{-1} = A^H, so A M^{-1} = A A^H is Hermitian
                           positive definite and restarted FGMRES cannot stagnate),
-                          DD_PRECOND_CGNR (flexible: CG steps on the normal equations) or
-                          DD_PRECOND_SAP (flexible: Schwarz cycles, see dd_sap) */
+                          DD_PRECOND_CGNR (flexible: CG steps on the normal equations),
+                          DD_PRECOND_SAP (flexible: Schwarz cycles, see dd_sap),
+                          DD_PRECOND_AMG (flexible: the two-level preconditioner `amg`) or
+                          DD_PRECOND_CGNR16 (DD_PRECOND_CGNR with FP16 CG vectors) */
   int gs_passes;       /* classical Gram-Schmidt passes per Arnoldi step: 1, or 2 (re-orthogonalised) */
   int rhs_batch;       /* even-odd solves: right-hand sides solved together (0 = all); smaller
                           batches need proportionally less device memory */
-  int precond_iters;   /* DD_PRECOND_CGNR: conjugate-gradient steps per preconditioner application */
+  int precond_iters;   /* DD_PRECOND_CGNR / CGNR16: conjugate-gradient steps per preconditioner
+                          application */
   int sap_block[4];    /* DD_PRECOND_SAP: block extents (T, Z, Y, X), as for dd_sap */
   int sap_cycles;      /* DD_PRECOND_SAP: red-black cycles per preconditioner application */
   int sap_mr_steps;    /* DD_PRECOND_SAP: minimal-residual steps per block solve */
