@@ -367,7 +367,8 @@ typedef struct {
 #define DD_PRECOND_AMG 4   /* flexible M_j: the two-level AMG preconditioner `amg` (even-odd: the odd
                               half of M^{-1} (0, v_j)) */
 #define DD_PRECOND_CGNR16 5 /* DD_PRECOND_CGNR with the CG vectors r, p, A p and A^H r stored in FP16
-                              (per-site scales; the iterate z_j in FP32): inner_prec DD_PREC_F16 only */
+                              (per-site scales; the iterate z_j in FP32): inner_prec DD_PREC_F16 (FP16
+                              links and self coupling) or DD_PREC_F32 (FP32 ones) */
 
 typedef struct {
   int converged;             /* 1 if every right-hand side met tol */

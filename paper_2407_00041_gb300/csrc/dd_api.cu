@@ -546,8 +546,8 @@ int dd_solve(dd_clover* op, const dd_solve_params* params, const void* b, void* 
     return fail(DD_ERR_ARG, "dd_solve takes canonical fields");
   if (params->precond < DD_PRECOND_NONE || params->precond > DD_PRECOND_CGNR16)
     return fail(DD_ERR_ARG, "unknown preconditioner");
-  if (params->precond == DD_PRECOND_CGNR16 && params->inner_prec != DD_PREC_F16)
-    return fail(DD_ERR_UNSUPPORTED, "DD_PRECOND_CGNR16 takes inner precision F16");
+  if (params->precond == DD_PRECOND_CGNR16 && params->inner_prec != DD_PREC_F16 && params->inner_prec != DD_PREC_F32)
+    return fail(DD_ERR_UNSUPPORTED, "DD_PRECOND_CGNR16 takes inner precision F16 or F32");
   if (!valid_apply_prec(params->inner_prec)) return fail(DD_ERR_ARG, "bad inner precision");
   if (params->inner_prec == DD_PREC_DF64 && (params->precond == DD_PRECOND_SAP || params->precond == DD_PRECOND_AMG))
     return fail(DD_ERR_UNSUPPORTED, "SAP and AMG take inner precision F64, F32 or F16");

@@ -158,6 +158,8 @@ int run_hop(int pg, int pv, const HopArgs& a, bool dag, int epi, cudaStream_t st
     e = launch_hop<P16, P16, P16>(a, dag, epi, st);
   else if (pg == P16 && pv == P32)
     e = launch_hop<P16, P32, P32>(a, dag, epi, st);
+  else if (pg == P32 && pv == P16)
+    e = launch_hop<P32, P16, P16>(a, dag, epi, st);
   else
     return fail(DD_ERR_UNSUPPORTED, "unsupported precision pair");
   if (e != cudaSuccess) return cuda_fail(e, "stencil launch");
@@ -246,6 +248,8 @@ int run_block(int pg, int pv, const BlockArgs& a, cudaStream_t st) {
     e = launch_block<P16, P16, P16>(a, st);
   else if (pg == P16 && pv == P32)
     e = launch_block<P16, P32, P32>(a, st);
+  else if (pg == P32 && pv == P16)
+    e = launch_block<P32, P16, P16>(a, st);
   else
     return fail(DD_ERR_UNSUPPORTED, "unsupported precision pair");
   if (e != cudaSuccess) return cuda_fail(e, "self-coupling launch");
@@ -303,20 +307,22 @@ int op_Dhat(const dd_clover* op, int pg, int pv, bool dagger, const Field& in, c
 }
 
 bool dhat_norm_fused(int pg, int pv, int nrhs) {
-  return nrhs == 1 && ((pv == P32 && (pg == P32 || pg == P16)) || (pv == P16 && pg == P16));
+  return nrhs == 1 && (pv == P32 || pv == P16) && (pg == P32 || pg == P16);
 }
 
 int op_Dhat_norm(const dd_clover* op, int pg, int pv, bool dagger, const Field& in, const Field& out, const Field& tmp,
                  double2* norm_out, double2* partials, int64_t npartials, cudaStream_t st) {
   if (!dhat_norm_fused(pg, pv, in.nrhs))
-    return fail(DD_ERR_UNSUPPORTED, "fused norm: one RHS, FP32 vectors or FP16 vectors with FP16 links");
+    return fail(DD_ERR_UNSUPPORTED, "fused norm: one RHS, FP32 or FP16 vectors and links");
   DD_TRY(check_prec(op, pg));
   HopArgs a, b;
   dhat_args(op, pg, in, out, tmp, a, b);
   DD_TRY(run_hop(pg, pv, a, dagger, EPI_AINV, st));
-  const cudaError_t e = pg == P32   ? launch_hop_norm<P32, P32, P32>(b, dagger, partials, npartials, norm_out, st)
-                        : pv == P32 ? launch_hop_norm<P16, P32, P32>(b, dagger, partials, npartials, norm_out, st)
-                                    : launch_hop_norm<P16, P16, P16>(b, dagger, partials, npartials, norm_out, st);
+  const cudaError_t e =
+      pg == P32 ? (pv == P32 ? launch_hop_norm<P32, P32, P32>(b, dagger, partials, npartials, norm_out, st)
+                             : launch_hop_norm<P32, P16, P16>(b, dagger, partials, npartials, norm_out, st))
+                : (pv == P32 ? launch_hop_norm<P16, P32, P32>(b, dagger, partials, npartials, norm_out, st)
+                             : launch_hop_norm<P16, P16, P16>(b, dagger, partials, npartials, norm_out, st));
   if (e != cudaSuccess) return cuda_fail(e, "stencil launch with norm");
   return DD_OK;
 }

@@ -26,8 +26,9 @@
 //           on the device with step sizes kept in device memory; Z_m is stored
 //           and x += Z_m y.
 //   cgnr16  the same CG with its vectors r, A^H r, p and A p stored in FP16
-//           (per-site scales) and read by the FP16 stencil; z accumulates in
-//           FP32 (FP16 links and blocks, inner_prec F16)
+//           (per-site scales) and read by the stencil with FP16 vectors and
+//           the inner precision's links and blocks (FP16 for inner_prec F16,
+//           FP32 for F32); z accumulates in FP32
 //   amg     the flexible two-level preconditioner of dd_amg.cu (coarse-grid
 //           correction and SAP post-smoothing), for the even-odd system
 //           applied to (0, v_j) like sap;

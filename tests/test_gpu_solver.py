@@ -55,7 +55,8 @@ def test_solve_to_1e10(sys44, inner, even_odd, precond):
 
 
 @pytest.mark.parametrize("inner,precond", [(dd.DD_PREC_F32, dd.DD_PRECOND_CGNR), (dd.DD_PREC_F16, dd.DD_PRECOND_CGNR),
-                                           (dd.DD_PREC_F16, dd.DD_PRECOND_CGNR16)])
+                                           (dd.DD_PREC_F16, dd.DD_PRECOND_CGNR16),
+                                           (dd.DD_PREC_F32, dd.DD_PRECOND_CGNR16)])
 def test_cg_norms_fused_into_the_stencil(inner, precond, monkeypatch):
     """The CG preconditioner takes |Dhat p|^2 and |Dhat^H r|^2 from the
     second stencil launch of Dhat (per-block partial sums; 1080 odd sites =
@@ -158,11 +159,32 @@ def test_solve_with_fp16_cg_vectors(even_odd, nrhs):
         assert oracle_residual(U, A, dims, b[r], xn[r]) < 1e-10
 
 
-def test_fp16_cg_vectors_need_fp16_inner():
+def test_fp16_cg_vectors_need_a_reduced_precision_inner_solve():
     dims = (4, 4, 4, 4)
     U, lat, g, op = make(dims)
     b = torch.from_numpy(synthetic.spinor(dims, nrhs=1)).cuda()
     x = torch.zeros_like(b)
     with pytest.raises(dd.DDError) as e:
-        op.solve(b, x, 1, inner_prec=dd.DD_PREC_F32, precond=dd.DD_PRECOND_CGNR16)
+        op.solve(b, x, 1, inner_prec=dd.DD_PREC_F64, precond=dd.DD_PRECOND_CGNR16)
     assert e.value.status == dd.DD_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("even_odd", [1, 0])
+@pytest.mark.parametrize("nrhs", [1, 2])
+def test_solve_with_fp16_cg_vectors_fp32_operator(even_odd, nrhs):
+    """DD_PRECOND_CGNR16 inside the FP32-inner solve: the CG vectors in FP16
+    read by the FP32-link stencil; 1e-10 reached and certified by the oracle,
+    with FP64 refinement."""
+    dims = (8, 8, 4, 4)
+    U, lat, g, op = make(dims)
+    A = oracle.clover(U, dims, M0, CSW)
+    b = synthetic.spinor(dims, nrhs=nrhs)
+    bt = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bt)
+    status, st = op.solve(bt, x, nrhs, tol=1e-10, inner_prec=dd.DD_PREC_F32, even_odd=even_odd, restart=8,
+                          precond=dd.DD_PRECOND_CGNR16, precond_iters=16, inner_tol=1e-6)
+    assert status == 0, st
+    assert st["converged"] == 1 and st["true_residual"] < 1e-10
+    xn = x.cpu().numpy()
+    for r in range(nrhs):
+        assert oracle_residual(U, A, dims, b[r], xn[r]) < 1e-10
