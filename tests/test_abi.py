@@ -86,3 +86,32 @@ def test_binding_argument_and_return_types_match_the_header():
         assert kinds[res] == _ctype_of(ret.strip() + " x"), (name, ret)
         for i, (p, a) in enumerate(zip(plist, args)):
             assert kinds[a] == _ctype_of(p), (name, i, p)
+
+
+def test_binding_structs_match_the_header():
+    """The ctypes mirrors of dd_solve_params, dd_stats and dd_amg_params have
+    the C structs' fields in the same order, with the same types and array
+    lengths, so that their layouts agree."""
+    from paper_2407_00041_gb300 import binding
+    src = open(os.path.join(ROOT, "include", "dd_wilson.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    ctype = {"int": ctypes.c_int, "double": ctypes.c_double, "dd_amg*": ctypes.c_void_p}
+    for cname, pyclass in (("dd_solve_params", binding.SolveParams), ("dd_stats", binding.Stats),
+                           ("dd_amg_params", binding.AmgParams)):
+        body = re.search(r"typedef\s+struct\s*\{([^}]*)\}\s*" + cname + r"\s*;", src, flags=re.S)
+        assert body, cname
+        fields = []
+        for decl in body.group(1).split(";"):
+            decl = " ".join(decl.split())
+            if not decl:
+                continue
+            m = re.match(r"^([A-Za-z_]\w*\s*\*?)\s*([A-Za-z_]\w*)\s*(?:\[(\d+)\])?$", decl)
+            assert m, (cname, decl)
+            typ = m.group(1).replace(" ", "")
+            t = ctype[typ]
+            fields.append((m.group(2), t * int(m.group(3)) if m.group(3) else t))
+        py = [(n, t) for n, t in pyclass._fields_]
+        assert [n for n, _ in py] == [n for n, _ in fields], cname
+        for (n, t), (_, u) in zip(py, fields):
+            assert ctypes.sizeof(t) == ctypes.sizeof(u) and getattr(t, "_type_", t) == getattr(u, "_type_", u), (cname, n)
