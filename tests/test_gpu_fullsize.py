@@ -206,6 +206,33 @@ def test_48c96_mixed_solve_oracle_residual_sampled(inner):
     assert rel(Dx, bs) < 1e-10  # the solve's own tolerance, recomputed by the oracle on the sample
 
 
+def test_48c96_fp16_cg_vectors_pair_refinement_oracle_residual_sampled():
+    """The bench's fastest solve at full size: FP16 links and blocks inside,
+    the CG vectors of M_j in FP16 (32 steps, inner tolerance 1e-3), the
+    refinement's applications in FP32-pair arithmetic; the oracle
+    recomputes b - D x on sampled sites from the downloaded solution."""
+    dims = (96, 48, 48, 48)
+    U = synthetic.gauge(dims, eps=EPS)
+    b = synthetic.spinor(dims, nrhs=1)
+    lat = dd.Lattice(dims, -1)
+    precs = dd.DD_PREC_F64 | dd.DD_PREC_F32 | dd.DD_PREC_F16 | dd.DD_PREC_DF64
+    g = dd.Gauge(lat, U, precisions=precs)
+    op = dd.Operator(g, M0, CSW, precisions=precs)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    status, st = op.solve(bd, x, 1, tol=1e-10, inner_prec=dd.DD_PREC_F16, restart=8, max_restarts=100,
+                          max_outer=20, precond=dd.DD_PRECOND_CGNR16, precond_iters=32, inner_tol=1e-3,
+                          refine_prec=dd.DD_PREC_DF64)
+    assert status == dd.DD_OK and st["true_residual"] < 1e-10, st
+    xh = x.cpu().numpy()
+    del op, g
+    sites = _sample(dims, 20000, 5)
+    A = oracle.clover_sites(U, dims, M0, CSW, sites)
+    Dx = oracle.apply_D_sites(U, A, xh[0], dims, sites)
+    bs = b[0].reshape(-1, 12)[sites]
+    assert rel(Dx, bs) < 1e-10
+
+
 def test_64c128_8rhs_mixed_solve_oracle_residual():
     """The 64^3 x 128 lattice with 8 Gaussian right-hand sides fitted in one
     GPU: FP64 and FP16 copies of links and self coupling only, b and x in host
