@@ -660,7 +660,7 @@ int dd_amg_create(dd_clover* op, int prec, const dd_amg_params* prm, const doubl
   if (s == DD_OK) s = A->Dc.alloc((size_t)A->nagg * 9 * A->K * A->K * sizeof(double2));
   if (s == DD_OK) s = A->flag.alloc(sizeof(int));
   if (s != DD_OK) return fin(s);
-  Field W = field_view(lat, pv, 0, A->Vw.ptr, NT), P = field_view(lat, pv, 0, A->P.ptr, NT);
+  Field W = field_view(lat, pv, 0, A->Vw.ptr, NT);
   s = pack(lat, pv, 0, w0, W, st);
   if (s != DD_OK) return fin(s);
   // norms and scaling of the N test vectors
